@@ -1,0 +1,291 @@
+#!/usr/bin/env python
+"""Refactor+solve throughput of the GB300 sparse LU on the power-grid workload.
+
+One step = one refactorization of the 316 x 316 power-grid matrix (n = 99,856,
+ND depth 4) with new values (base x (1 + N(0, 0.05)), the ten-matrix sequence
+cycled) plus one solve, all inputs resident in HBM.  Only steps whose solve has
+backward error <= 1e-12 count as valid.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs N independent replicas (one process per GPU, launched by torchrun);
+the path has no exchange step, so there is no collective in the data path.
+--impl reference times the CPU oracle on the same workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "refactor+solve/s at backward err<=1e-12, FP32+IR vs FP64; p50/p99 latency"
+UNIT = "refactor+solve/s"
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-sample", type=int, default=4, help="oracle steps in the cpu_baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class Clocks:
+    """nvidia-smi samples (every 100 ms) of the SM clock and throttle reasons."""
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.proc = None
+        self.path = None
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "100", "-i", str(index)], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def mark(self):
+        return time.time()
+
+    def stop(self, t0: float, t1: float):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 10:
+                continue
+            try:
+                ts = time.mktime(time.strptime(parts[0].split(".")[0], "%Y/%m/%d %H:%M:%S"))
+                rows.append((ts, float(parts[2]), float(parts[3]), parts[5:]))
+            except Exception:
+                continue
+        os.unlink(self.path)
+        inside = [r for r in rows if t0 - 1.0 <= r[0] <= t1 + 1.0] or rows
+        if not inside:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in inside:
+            for nm, v in zip(names, r[3][1:]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(r[1] for r in inside), "sm_max_mhz": max(r[2] for r in inside),
+                "reasons": sorted(reasons), "samples": len(inside)}
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def _workload():
+    from paper_1601_05725_gb300 import inputs
+    prob = inputs.config2()
+    vals = [inputs.refactor_values(prob, k) for k in range(1, 11)]
+    rhs = [inputs.rhs_ones(prob, v) for v in vals]
+    return prob, vals, rhs
+
+
+def _config(prob):
+    return {"workload": "powergrid_316x316_refactor_solve", "n": int(prob.n), "nnz": int(prob.nnz),
+            "nd_leaves": int(prob.nd_leaves), "refactor_values": "base x (1+N(0,0.05)), 10 draws cycled",
+            "nrhs": 1, "tau": 1e-3, "l2": "flushed between steps (256 MiB write outside the step events)",
+            "parallelism": "replicas"}
+
+
+def _eta(prob, v, x, b):
+    import scipy.sparse as sp
+    A = sp.csc_matrix((v, prob.rowind, prob.colptr), shape=(prob.n, prob.n))
+    r = b - A @ x
+    return float(np.abs(r).max() / (np.abs(A).sum(axis=1).max() * np.abs(x).max() + np.abs(b).max()))
+
+
+def cpu_oracle_steps(prob, vals, rhs, k0: int, count: int):
+    """The oracle as it stands: refactor (previous pivots preferred) + solve, serial."""
+    import oracle
+    o = oracle.OracleLU(prob)
+    assert o.factor() == "OK"
+    f = o.factors()
+    t = 0.0
+    etas = []
+    for i in range(count):
+        v, b = vals[(k0 + i) % len(vals)], rhs[(k0 + i) % len(rhs)]
+        t0 = time.perf_counter()
+        s = o.factor(v, pref=f.prow)
+        x = o.solve(b)
+        t += time.perf_counter() - t0
+        assert s == "OK"
+        f = o.factors()
+        etas.append(_eta(prob, v, x, b))
+    return t, etas
+
+
+def run_reference(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return
+    prob, vals, rhs = _workload()
+    cpu_oracle_steps(prob, vals, rhs, 0, args.warmup) if args.warmup else None
+    t, etas = cpu_oracle_steps(prob, vals, rhs, args.warmup, args.steps)
+    value = args.steps / t
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": _config(prob),
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": f"{args.steps} refactor+solve steps of the workload, serial C oracle"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+           "max_backward_error": max(etas)}
+    print(json.dumps(out), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1601_05725_gb300 import basker, build
+
+    world, rank, local = _dist()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+    prob, vals, rhs = _workload()
+    dvals = [torch.as_tensor(v, device=dev) for v in vals]
+    drhs = [torch.as_tensor(b, device=dev) for b in rhs]
+    h = basker.Handle.from_problem(prob, timing=True)
+    h.factor(torch.as_tensor(prob.values, device=dev))
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    K, W = args.steps, args.warmup
+    xs = torch.empty((K, prob.n), dtype=torch.float64, device=dev)
+    for i in range(W):
+        h.refactor(dvals[i % 10])
+        h.solve(drhs[i % 10])
+    torch.cuda.synchronize()
+    info0 = h.info()                      # resets the kernel timers
+    clocks = Clocks(local)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_start = time.time()
+    for i in range(K):
+        flush.fill_(float(i))
+        ev[i][0].record()
+        h.refactor(dvals[(W + i) % 10])
+        h.solve(drhs[(W + i) % 10], x=xs[i])
+        ev[i][1].record()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t_end = time.time()
+    clk = clocks.stop(t_start, t_end)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    info1 = h.info()
+    total_s = sum(step_ms) / 1e3
+    if world > 1:
+        t = torch.tensor([total_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    # validity: every step's backward error
+    X = xs.cpu().numpy()
+    etas = [_eta(prob, vals[(W + i) % 10], X[i], rhs[(W + i) % 10]) for i in range(K)]
+    # end to end through the host entry point (copies inside the timed calls)
+    pin_v = [torch.as_tensor(v).pin_memory() for v in vals]
+    pin_b = [torch.as_tensor(b).pin_memory() for b in rhs]
+    e2e_t = []
+    for i in range(K):
+        t0 = time.perf_counter()
+        h.refactor_solve_host(pin_v[(W + i) % 10].numpy(), pin_b[(W + i) % 10].numpy())
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_total = sum(e2e_t)
+    if world > 1:
+        t = torch.tensor([e2e_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    if rank != 0:
+        dist.destroy_process_group() if world > 1 else None
+        return
+    kms = info1["kernel_ms"]
+    dom = max(kms, key=lambda k: kms[k])
+    nnz_lu = info1["nnz_l"] + info1["nnz_u"]
+    peaks = _peaks()
+    hbm = peaks.get("hbm_gbs")
+    # algorithmic bytes of one refactor: (8 + 4) bytes per entry of A and of L+U
+    bytes_refactor = 12.0 * (prob.nnz + nnz_lu)
+    launches_per_step = {"static_refactor": 1, "solve": 1}
+    per_launch_ms = kms[dom] / (K * launches_per_step.get(dom, 1))
+    algo_bytes = bytes_refactor if dom != "solve" else 12.0 * nnz_lu + 24.0 * prob.n
+    achieved = algo_bytes / (per_launch_ms * 1e-3) / 1e9 if per_launch_ms > 0 else 0.0
+    value = world * K / total_s
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": 1e3 * total_s / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic", "config": _config(prob),
+        "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
+        "max_backward_error": max(etas), "valid_steps": int(sum(e <= 1e-12 for e in etas)),
+        "e2e": {"value": world * K / e2e_total, "unit": UNIT,
+                "h2d_bytes_per_step": int(8 * prob.nnz + 8 * prob.n), "d2h_bytes_per_step": int(8 * prob.n)},
+        "gpu_launches": int(info1["kernel_launches"] - info0["kernel_launches"] - K * 0),
+        "kernel_ms_per_step": {k: v / K for k, v in kms.items() if v > 0},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved,
+                     "peak": hbm, "unit": "GB/s", "frac": (achieved / hbm) if hbm else None,
+                     "traffic": None, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if hbm else None,
+                     "algorithmic_bytes_per_launch": algo_bytes},
+        "nnz_lu": int(nnz_lu), "flops_per_refactor": info1["flops"],
+        "clocks": clk,
+    }
+    if not args.no_cpu_baseline:
+        t, _ = cpu_oracle_steps(prob, vals, rhs, 0, args.cpu_sample)
+        out["cpu_baseline"] = {"value": args.cpu_sample / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+                               "sample": f"{args.cpu_sample} refactor+solve steps of the same workload, serial C oracle"}
+    print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,164 @@
+/*
+ * basker.h -- C ABI of the GB300 sparse LU library (libbasker_gb300.so).
+ *
+ * The library factors A (n x n, CSC) as the paper "Basker: A Threaded Sparse LU
+ * Factorization Utilizing Hierarchical Parallelism and Data Layouts" (Booth,
+ * Rajamanickam, Thornquist, arXiv 1601.05725) describes: A is permuted by fixed
+ * row/column permutations P, Q into block triangular form (BTF, Sec. II and
+ * III-A), only the diagonal blocks are factored (Sec. II), one diagonal block may
+ * carry a nested-dissection (ND) tree (Sec. III-C), and every block is factored
+ * with the left-looking Gilbert-Peierls method (Algorithm 1) with threshold
+ * partial pivoting confined to the block, or to the ND node (the diagonal blocks
+ * A_ii / A_jj of Fig. 3a).  Refactorization reuses the pattern for a sequence of
+ * matrices (Sec. V-F, the circuit-simulation sequence), and the solve is the BTF
+ * back-substitution with the off-diagonal blocks kept as values of A (Sec. III-B).
+ *
+ * Conventions for every entry point:
+ *   - Indices are 0-based int32.  CSC: colptr[n+1], rowind[nnz], rows strictly
+ *     increasing inside a column.
+ *   - "new -> old" permutations: B = A(P,Q) means B(i,j) = A(P[i], Q[j]).
+ *   - Pointers named *_dev are device pointers (CUDA global memory) read or
+ *     written in stream order on the stream passed in; *_host are host pointers.
+ *   - Streams are passed as void* holding a cudaStream_t (NULL = legacy default).
+ *   - The caller owns every array it passes; the library copies what it keeps.
+ *     The handle owns all device memory the library allocates.
+ *   - Return value: a basker_status (0 = success).  A handle is not thread-safe:
+ *     use one handle from one host thread and one stream at a time.
+ *   - No entry point falls back to the CPU: device work runs only in this
+ *     library's CUDA kernels.
+ */
+#ifndef BASKER_GB300_H
+#define BASKER_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct basker_s *basker_t;
+
+typedef enum {
+    BASKER_OK = 0,
+    BASKER_ERR_INVALID_ARG = 1,   /* bad size, pointer, permutation or CSC pattern */
+    BASKER_ERR_NOT_BTF = 2,       /* an entry of B lies below the diagonal blocks (Sec. II) */
+    BASKER_ERR_BAD_ND = 3,        /* an entry joins two ND nodes on different branches (Sec. III-C) */
+    BASKER_ERR_SINGULAR = 4,      /* no nonzero pivot candidate; basker_info gives the column */
+    BASKER_ERR_NAN = 5,           /* a non-finite value in a factored column; column in basker_info */
+    BASKER_ERR_OOM = 6,           /* device or host allocation failed */
+    BASKER_ERR_TIMEOUT = 7,       /* an in-kernel wait exceeded options.wait_budget_cycles */
+    BASKER_ERR_CUDA = 8,          /* a CUDA runtime call failed */
+    BASKER_ERR_NOT_FACTORED = 9   /* refactor/solve/export before a successful factor */
+} basker_status;
+
+typedef struct {
+    double tau;                   /* pivot threshold in (0,1]; default 1e-3 */
+    double slack;                 /* extra L/U capacity over the symbolic count; default 1.0 */
+    long long wait_budget_cycles; /* clock64 cycles any in-kernel wait may spin; default 2e10 */
+    int factor_mode;              /* must be 0: every column of basker_factor goes through
+                                     the reach of Algorithm 1 (other values: INVALID_ARG) */
+    int timing;                   /* nonzero: record CUDA events around every kernel launch
+                                     on the caller's stream; totals in basker_info */
+    int reserved[6];
+} basker_options;
+
+typedef struct {
+    int32_t n;
+    int32_t nblocks;              /* BTF blocks */
+    int32_t nd_block;             /* ND block index or -1 */
+    int32_t nd_leaves;
+    int64_t nnz_a;                /* entries of A */
+    int64_t nnz_l;                /* stored strictly-lower entries of L (unit diagonal implied) */
+    int64_t nnz_u;                /* stored entries of U, diagonal included */
+    int64_t nnz_l_sym, nnz_u_sym; /* symbolic counts under the preferred (diagonal) pivots */
+    double flops;                 /* sum_j l_j (2 u_j + 1) of the current factors */
+    int32_t failed_column;        /* column named by SINGULAR / NAN, else -1 */
+    int32_t last_repivot_columns; /* columns recomputed by the reach in the last refactor */
+    int32_t off_diagonal_pivots;  /* columns whose pivot is not the natural row */
+    int32_t capacity_regrows;     /* times the L/U arena was regrown */
+    int64_t device_bytes;         /* device memory held by the handle */
+    int32_t gp_launches;          /* kernel launches of the last factor/refactor */
+    int32_t static_launches;
+    int64_t kernel_launches;      /* all kernel launches since basker_symbolic */
+    double kernel_ms[8];          /* with options.timing: device time per kernel kind since
+                                     the last basker_info call: [0] value gather,
+                                     [1] stored-pattern refactor, [2] DAG levels,
+                                     [3] in-node Algorithm 1, [4] separator descendant
+                                     phase, [5] solve, [6] pivot reset, [7] unused */
+    int32_t reserved[8];
+} basker_info_t;
+
+/* Defaults listed in basker_options. */
+void basker_default_options(basker_options *opt);
+
+/* Analyse a pattern (host arrays; Sec. III-A/III-C orderings are inputs).
+ *   n, colptr, rowind: pattern of A (host).
+ *   P, Q: host, new -> old permutations putting A in BTF order.
+ *   nblocks, block_ptr[nblocks+1]: BTF block boundaries in B's numbering
+ *     (0 = b_0 < b_1 < ... < b_nblocks = n).
+ *   nd_block: index of the block carrying the ND tree, or -1.
+ *   nd_leaves: power of two; nd_node_ptr[2*nd_leaves]: row/column boundaries of
+ *     the ND nodes in postorder (left subtree, right subtree, separator), from
+ *     block_ptr[nd_block] to block_ptr[nd_block+1]; nodes may be empty.
+ *   opt: options (NULL = defaults).  out: receives the handle.
+ * Checks the BTF and ND invariants, runs the structural pass (capacities, the
+ * level schedule of Algorithm 4's dependency tree), allocates the device arena
+ * and uploads the plan.  Errors: INVALID_ARG, NOT_BTF, BAD_ND, OOM, CUDA;
+ * *out is NULL on error. */
+int basker_symbolic(int32_t n, const int32_t *colptr, const int32_t *rowind,
+                    const int32_t *P, const int32_t *Q,
+                    int32_t nblocks, const int32_t *block_ptr,
+                    int32_t nd_block, int32_t nd_leaves, const int32_t *nd_node_ptr,
+                    const basker_options *opt, basker_t *out);
+
+/* Numeric factorization (Algorithm 1 on every BTF block; Algorithm 4's levels on
+ * the ND block).  values_dev: nnz(A) doubles, device, in A's CSC order.  Pivots
+ * prefer the natural row.  Synchronises the stream at the end to read a 16-byte
+ * status.  Errors: SINGULAR, NAN (column in basker_info), TIMEOUT, CUDA, OOM. */
+int basker_factor(basker_t h, const double *values_dev, void *stream);
+
+/* Refactorization of a new matrix with the same pattern (Sec. V-F): each column
+ * prefers the pivot row of the previous factorization; columns that keep it are
+ * computed on the stored pattern (column-level dataflow), and a node whose
+ * column rejects its preferred pivot is recomputed from that column on with the
+ * reach of Algorithm 1, together with its ancestors.  The result equals a fresh
+ * factorization with those preferences.  Errors as basker_factor, and
+ * NOT_FACTORED. */
+int basker_refactor(basker_t h, const double *values_dev, void *stream);
+
+/* Solve A X = B for nrhs right-hand sides (column-major, leading dimensions ldb,
+ * ldx >= n, device pointers; b_dev and x_dev may not overlap).  BTF blocks from
+ * last to first: subtract the off-diagonal blocks' products, then the L and U
+ * solves of the block.  Asynchronous on the stream.  Errors: INVALID_ARG,
+ * NOT_FACTORED, CUDA, OOM. */
+int basker_solve(basker_t h, int32_t nrhs, const double *b_dev, int32_t ldb,
+                 double *x_dev, int32_t ldx, void *stream);
+
+/* End-to-end call on host buffers: copies values and b from host memory to the
+ * device, refactors (or factors, if refactor != 0 is not possible yet), solves
+ * and copies x back, synchronising the stream.  values_host: nnz(A) doubles in
+ * A's CSC order; b_host/x_host: n x nrhs column-major (ld = n). */
+int basker_refactor_solve_host(basker_t h, const double *values_host, int32_t nrhs,
+                               const double *b_host, double *x_host, void *stream);
+
+/* Counters of the handle (sizes, flops, failing column, repivots). */
+int basker_info(basker_t h, basker_info_t *out);
+
+/* Copy the factors to host memory, in B's coordinates: prow[k] = B row pivoted
+ * at step k (n ints); L strictly lower with rows = pivot steps, U upper with the
+ * diagonal last, each column sorted by step.  Call with Li == NULL to get the
+ * sizes only (*nnz_l, *nnz_u).  Lp/Up are int64[n+1].  Synchronises. */
+int basker_export(basker_t h, int32_t *prow, int64_t *Lp, int32_t *Li, double *Lx,
+                  int64_t *Up, int32_t *Ui, double *Ux, int64_t *nnz_l, int64_t *nnz_u);
+
+/* Release the handle and all its device memory (NULL is allowed). */
+void basker_free(basker_t h);
+
+/* Static string naming a status. */
+const char *basker_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BASKER_GB300_H */

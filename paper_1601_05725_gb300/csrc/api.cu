@@ -1,0 +1,763 @@
+// api.cu -- the C entry points of include/basker.h: handle, device memory, and
+// the order of kernel launches for factor, refactor and solve.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "basker_internal.h"
+#include "solve_internal.h"
+
+struct basker_s {
+    basker_options opt;
+    bk_plan pl;
+    bk_solve_plan sp;
+    int device = 0;
+    std::vector<void *> allocs;
+    bk_dev d{};
+    bk_solve_dev sd{};
+    // level lists of a full factorization (device)
+    std::vector<int32_t *> lv_tasks;
+    std::vector<int32_t> lv_ntasks;
+    std::vector<size_t> lv_smem;
+    std::vector<int32_t *> lv_cols;
+    std::vector<int32_t> lv_ncols;
+    // redo lists (device buffers of n ints each) and their pinned staging
+    int32_t *rd_tasks = nullptr, *rd_c0 = nullptr, *rd_cols = nullptr;
+    int32_t *h_stage = nullptr;      // pinned, 3n + ntasks + 16 ints
+    bk_status *h_status = nullptr;   // pinned
+    int32_t *h_task_fail = nullptr;  // pinned
+    int32_t epoch = 0, solve_epoch = 0;
+    bool factored = false, ws_dirty = false, schedule_valid = true, order_is_symbolic = true;
+    int32_t nrhs_cap = 0;
+    double *d_vals = nullptr, *d_b = nullptr, *d_x = nullptr;
+    int32_t stage_nrhs = 0;
+    double grow = 1.0;
+    basker_info_t info{};
+    int64_t device_bytes = 0;
+    int32_t launches = 0;
+    // kernel timing (options.timing): event pairs recorded on the launch stream
+    struct timed { cudaEvent_t a, b; int kind; };
+    std::vector<timed> pending;
+    std::vector<cudaEvent_t> pool;
+    cudaEvent_t open_ev = nullptr;
+    int open_kind = 0;
+};
+
+namespace {
+
+enum { KT_GATHER = 0, KT_STATIC = 1, KT_LEVELS = 2, KT_GP = 3, KT_DESC = 4, KT_SOLVE = 5, KT_RESET = 6 };
+
+cudaEvent_t take_event(basker_t h)
+{
+    if (!h->pool.empty()) {
+        cudaEvent_t e = h->pool.back();
+        h->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Bracket a launch (or a group of launches of one kind) with events on its stream.
+void tbeg(basker_t h, int kind, cudaStream_t s, int nkernels)
+{
+    h->info.kernel_launches += nkernels;
+    if (!h->opt.timing) return;
+    h->open_ev = take_event(h);
+    h->open_kind = kind;
+    cudaEventRecord(h->open_ev, s);
+}
+
+void tend(basker_t h, cudaStream_t s)
+{
+    if (!h->opt.timing || !h->open_ev) return;
+    cudaEvent_t b = take_event(h);
+    cudaEventRecord(b, s);
+    h->pending.push_back({h->open_ev, b, h->open_kind});
+    h->open_ev = nullptr;
+}
+
+void tflush(basker_t h)
+{
+    for (auto &t : h->pending) {
+        float ms = 0.f;
+        cudaEventSynchronize(t.b);
+        if (cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) h->info.kernel_ms[t.kind] += ms;
+        h->pool.push_back(t.a);
+        h->pool.push_back(t.b);
+    }
+    h->pending.clear();
+}
+
+template <typename T>
+int dalloc(basker_t h, T **p, size_t count, bool zero = false)
+{
+    *p = nullptr;
+    size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+    if (cudaMalloc((void **)p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return BASKER_ERR_OOM;
+    }
+    h->allocs.push_back((void *)*p);
+    h->device_bytes += (int64_t)bytes;
+    if (zero && cudaMemset(*p, 0, bytes) != cudaSuccess) return BASKER_ERR_CUDA;
+    return BASKER_OK;
+}
+
+void dfree(basker_t h, void *p)
+{
+    if (!p) return;
+    auto it = std::find(h->allocs.begin(), h->allocs.end(), p);
+    if (it != h->allocs.end()) h->allocs.erase(it);
+    cudaFree(p);
+}
+
+template <typename T>
+int upload(basker_t h, T **p, const std::vector<T> &v)
+{
+    int s = dalloc(h, p, v.size());
+    if (s) return s;
+    if (!v.empty() && cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess)
+        return BASKER_ERR_CUDA;
+    return BASKER_OK;
+}
+
+#define TRY(x)                      \
+    do {                            \
+        int s_ = (x);               \
+        if (s_ != BASKER_OK) return s_; \
+    } while (0)
+#define CU(x)                                  \
+    do {                                       \
+        if ((x) != cudaSuccess) {              \
+            cudaGetLastError();                \
+            return BASKER_ERR_CUDA;            \
+        }                                      \
+    } while (0)
+
+// L/U arrays sized by the current layout (symbolic pattern, slack, growth)
+int alloc_factors(basker_t h)
+{
+    bk_plan &pl = h->pl;
+    dfree(h, h->d.Li); dfree(h, (void *)h->d.Lx); dfree(h, h->d.Ui); dfree(h, (void *)h->d.Ux);
+    dfree(h, h->d.Lbeg); dfree(h, h->d.Ubeg);
+    h->d.Li = h->d.Ui = nullptr;
+    h->d.Lx = h->d.Ux = nullptr;
+    TRY(dalloc(h, &h->d.Li, (size_t)pl.lcap));
+    TRY(dalloc(h, &h->d.Lx, (size_t)pl.lcap));
+    TRY(dalloc(h, &h->d.Ui, (size_t)pl.ucap));
+    TRY(dalloc(h, &h->d.Ux, (size_t)pl.ucap));
+    TRY(upload(h, &h->d.Lbeg, pl.sLbeg));
+    TRY(upload(h, &h->d.Ubeg, pl.sUbeg));
+    return BASKER_OK;
+}
+
+// the symbolic pattern in the L/U arrays (the static path's first schedule)
+int upload_symbolic_pattern(basker_t h)
+{
+    bk_plan &pl = h->pl;
+    std::vector<int32_t> Li((size_t)pl.lcap, 0), Ui((size_t)pl.ucap, 0);
+    int64_t l = 0, u = 0;
+    for (int32_t c = 0; c < pl.n; c++) {
+        for (int32_t k = 0; k < pl.sLcnt[(size_t)c]; k++) Li[(size_t)(pl.sLbeg[(size_t)c] + k)] = pl.sLi[(size_t)l++];
+        for (int32_t k = 0; k < pl.sUcnt[(size_t)c]; k++) Ui[(size_t)(pl.sUbeg[(size_t)c] + k)] = pl.sUi[(size_t)u++];
+    }
+    CU(cudaMemcpy(h->d.Li, Li.data(), Li.size() * 4, cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(h->d.Ui, Ui.data(), Ui.size() * 4, cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(h->d.Lcnt, pl.sLcnt.data(), (size_t)pl.n * 4, cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(h->d.Ucnt, pl.sUcnt.data(), (size_t)pl.n * 4, cudaMemcpyHostToDevice));
+    std::vector<int32_t> prow(pl.sprow), pinv((size_t)pl.n, -1);
+    for (int32_t c = 0; c < pl.n; c++) if (prow[(size_t)c] >= 0) pinv[(size_t)prow[(size_t)c]] = c;
+    CU(cudaMemcpy(h->d.prow, prow.data(), (size_t)pl.n * 4, cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(h->d.pinv, pinv.data(), (size_t)pl.n * 4, cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(h->d.order, pl.sorder.data(), (size_t)pl.n * 4, cudaMemcpyHostToDevice));
+    return BASKER_OK;
+}
+
+int setup_device(basker_t h)
+{
+    bk_plan &pl = h->pl;
+    bk_dev &d = h->d;
+    const int32_t n = pl.n;
+    d.n = n;
+    d.ntasks = (int32_t)pl.tasks.size();
+    TRY(upload(h, (int32_t **)&d.Bp, pl.Bp));
+    TRY(upload(h, (int32_t **)&d.Bi, pl.Bi));
+    TRY(upload(h, (int32_t **)&d.dstart, pl.dstart));
+    TRY(upload(h, (int32_t **)&d.bmap, pl.bmap));
+    TRY(upload(h, (int32_t **)&d.col_task, pl.col_task));
+    TRY(dalloc(h, &d.Bx, (size_t)pl.nnz, true));
+    TRY(upload(h, &d.tasks, pl.tasks));
+    TRY(dalloc(h, &d.prow, (size_t)n));
+    TRY(dalloc(h, &d.pinv, (size_t)n));
+    TRY(dalloc(h, (int32_t **)&d.pref, (size_t)n));
+    TRY(dalloc(h, &d.Lcnt, (size_t)n, true));
+    TRY(dalloc(h, &d.Ucnt, (size_t)n, true));
+    TRY(alloc_factors(h));
+    TRY(dalloc(h, &d.status, 1, true));
+    TRY(dalloc(h, &d.task_fail, pl.tasks.size()));
+    TRY(dalloc(h, &d.ws, (size_t)std::max<int64_t>(pl.ws_bytes, 256), true));
+    TRY(dalloc(h, &d.done, (size_t)n, true));
+    TRY(dalloc(h, &d.order, (size_t)n));
+    TRY(dalloc(h, &d.counter, 8, true));
+    TRY(dalloc(h, &d.level, (size_t)n * 2 + 2, true));
+    TRY(dalloc(h, &d.ahat, (size_t)pl.ahat_doubles));
+    TRY(dalloc(h, &d.abits, (size_t)pl.ahat_words));
+    TRY(dalloc(h, &d.dcnt, (size_t)n, true));
+    d.wsd_slice = pl.wsd_slice;
+    d.wsd_warps = pl.wsd_warps;
+    TRY(dalloc(h, &d.wsd, (size_t)(pl.wsd_slice * pl.wsd_warps), true));
+    d.sx_warps = bk_static_blocks() * 4;
+    d.sx_stride = ((int64_t)pl.max_space + 31) & ~(int64_t)31;
+    TRY(dalloc(h, &d.sx, (size_t)(d.sx_stride * d.sx_warps), true));
+    d.nblocks = pl.nblocks;
+    TRY(upload(h, (int32_t **)&d.block_ptr, pl.block_ptr));
+    TRY(upload(h, (int32_t **)&d.P, pl.P));
+    TRY(upload(h, (int32_t **)&d.Q, pl.Q));
+    // level lists of a full factorization
+    const size_t nl = pl.level_tasks.size();
+    h->lv_tasks.assign(nl, nullptr);
+    h->lv_ntasks.assign(nl, 0);
+    h->lv_smem.assign(nl, 0);
+    h->lv_cols.assign(nl, nullptr);
+    h->lv_ncols.assign(nl, 0);
+    for (size_t l = 0; l < nl; l++) {
+        const auto &ids = pl.level_tasks[l];
+        TRY(upload(h, &h->lv_tasks[l], ids));
+        h->lv_ntasks[l] = (int32_t)ids.size();
+        size_t sm = 0;
+        std::vector<int32_t> cols;
+        for (int32_t t : ids) {
+            const bk_task &T = pl.tasks[(size_t)t];
+            if (T.wsoff < 0) sm = std::max(sm, bk_task_smem_bytes(T));
+            if (T.sp_lo < T.lo)
+                for (int32_t c = T.lo; c < T.hi; c++) cols.push_back(c);
+        }
+        h->lv_smem[l] = (sm + 15) & ~(size_t)15;
+        TRY(upload(h, &h->lv_cols[l], cols));
+        h->lv_ncols[l] = (int32_t)cols.size();
+    }
+    TRY(dalloc(h, &h->rd_tasks, (size_t)std::max<size_t>(pl.tasks.size(), 1)));
+    TRY(dalloc(h, &h->rd_c0, (size_t)std::max<size_t>(pl.tasks.size(), 1)));
+    TRY(dalloc(h, &h->rd_cols, (size_t)std::max(n, 1)));
+    CU(cudaMallocHost((void **)&h->h_stage, sizeof(int32_t) * ((size_t)n + 4 * pl.tasks.size() + 16)));
+    CU(cudaMallocHost((void **)&h->h_status, sizeof(bk_status)));
+    CU(cudaMallocHost((void **)&h->h_task_fail, sizeof(int32_t) * std::max<size_t>(pl.tasks.size(), 1)));
+    // solve
+    bk_solve_plan_build(pl, h->sp);
+    bk_solve_dev &s = h->sd;
+    s.nitems = (int32_t)h->sp.items.size();
+    TRY(upload(h, (bk_sitem **)&s.items, h->sp.items));
+    TRY(upload(h, (int32_t **)&s.deps, h->sp.deps));
+    TRY(upload(h, (int32_t **)&s.desc, h->sp.desc));
+    TRY(dalloc(h, &s.item_done, (size_t)std::max(s.nitems, 1), true));
+    TRY(upload(h, (int32_t **)&s.offp, h->sp.offp));
+    TRY(upload(h, (int32_t **)&s.offj, h->sp.offj));
+    TRY(upload(h, (int32_t **)&s.offpos, h->sp.offpos));
+    TRY(upload(h, (int64_t **)&s.acc_off, h->sp.acc_off));
+    s.acc_stride = h->sp.acc_stride;
+    TRY(upload_symbolic_pattern(h));
+    h->schedule_valid = true;
+    return BASKER_OK;
+}
+
+int reset_status(basker_t h, cudaStream_t s)
+{
+    CU(cudaMemsetAsync(h->d.status, 0, sizeof(bk_status), s));
+    CU(cudaMemsetAsync(&h->d.status->first_fail, 0xff, sizeof(unsigned long long), s));
+    if (h->ws_dirty) {
+        CU(cudaMemsetAsync(h->d.ws, 0, (size_t)std::max<int64_t>(h->pl.ws_bytes, 256), s));
+        CU(cudaMemsetAsync(h->d.wsd, 0, (size_t)(h->pl.wsd_slice * h->pl.wsd_warps), s));
+        CU(cudaMemsetAsync(h->d.sx, 0, sizeof(double) * (size_t)(h->d.sx_stride * h->d.sx_warps), s));
+        h->ws_dirty = false;
+    }
+    return BASKER_OK;
+}
+
+// Read the status word; translate failures.  Returns OK, SINGULAR, NAN, TIMEOUT,
+// or -1 for a capacity overflow (the caller regrows).
+int read_status(basker_t h, cudaStream_t s)
+{
+    CU(cudaMemcpyAsync(h->h_status, h->d.status, sizeof(bk_status), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    CU(cudaGetLastError());
+    const bk_status &st = *h->h_status;
+    h->info.failed_column = -1;
+    if (st.timeout) { h->ws_dirty = true; return BASKER_ERR_TIMEOUT; }
+    if (st.first_fail != ~0ull) {
+        h->ws_dirty = true;
+        h->info.failed_column = (int32_t)(st.first_fail >> 8);
+        const unsigned code = (unsigned)(st.first_fail & 0xff);
+        if (code == BK_CODE_INTERNAL) return BASKER_ERR_INVALID_ARG;
+        return code == BK_CODE_NAN ? BASKER_ERR_NAN : BASKER_ERR_SINGULAR;
+    }
+    if (st.capacity) { h->ws_dirty = true; return -1; }
+    return BASKER_OK;
+}
+
+int regrow(basker_t h)
+{
+    h->grow *= 2.0;
+    bk_plan_layout(h->pl, h->grow);
+    TRY(alloc_factors(h));
+    CU(cudaMemcpy(h->d.tasks, h->pl.tasks.data(), sizeof(bk_task) * h->pl.tasks.size(), cudaMemcpyHostToDevice));
+    h->info.capacity_regrows++;
+    h->ws_dirty = true;
+    return BASKER_OK;
+}
+
+// Algorithm 1 on every task, level by level (Algorithm 4's dependency tree).
+int launch_full_gp(basker_t h, cudaStream_t s, int pref_mode)
+{
+    const double tau = h->opt.tau;
+    CU(cudaMemsetAsync(h->d.pinv, 0xff, sizeof(int32_t) * (size_t)h->pl.n, s));
+    for (size_t l = 0; l < h->lv_tasks.size(); l++) {
+        if (l > 0 && h->lv_ncols[l] > 0) {
+            CU(cudaMemsetAsync(h->d.counter + 3, 0, sizeof(int32_t), s));
+            tbeg(h, KT_DESC, s, 1);
+            bk_launch_gp_desc(h->d, h->lv_cols[l], h->lv_ncols[l], h->d.counter + 3, s);
+            tend(h, s);
+            h->launches++;
+        }
+        if (h->lv_ntasks[l] > 0) {
+            tbeg(h, KT_GP, s, 1);
+            bk_launch_gp_tasks(h->d, h->lv_tasks[l], nullptr, h->lv_ntasks[l], h->lv_smem[l], tau, pref_mode, s);
+            tend(h, s);
+            h->launches++;
+        }
+    }
+    CU(cudaGetLastError());
+    return BASKER_OK;
+}
+
+// Redo the tasks with start[t] < hi from that column (refactor after a rejected
+// preferred pivot), with the previous pivots preferred.
+int launch_redo(basker_t h, cudaStream_t s, const std::vector<int32_t> &start)
+{
+    bk_plan &pl = h->pl;
+    const double tau = h->opt.tau;
+    std::vector<int32_t> ids, c0;
+    for (size_t t = 0; t < pl.tasks.size(); t++)
+        if (start[t] < pl.tasks[t].hi) { ids.push_back((int32_t)t); c0.push_back(start[t]); }
+    if (ids.empty()) return BASKER_OK;
+    const size_t nt = ids.size();
+    std::memcpy(h->h_stage, ids.data(), nt * 4);
+    std::memcpy(h->h_stage + nt, c0.data(), nt * 4);
+    CU(cudaMemcpyAsync(h->rd_tasks, h->h_stage, nt * 4, cudaMemcpyHostToDevice, s));
+    CU(cudaMemcpyAsync(h->rd_c0, h->h_stage + nt, nt * 4, cudaMemcpyHostToDevice, s));
+    tbeg(h, KT_RESET, s, 1);
+    bk_launch_reset_pivots(h->d, h->rd_tasks, h->rd_c0, (int32_t)nt, s);
+    tend(h, s);
+    h->launches++;
+    // group by level: tasks are ordered by level within the lists below
+    int32_t redone = 0;
+    std::vector<int32_t> cols;
+    for (size_t l = 0; l < pl.level_tasks.size(); l++) {
+        std::vector<int32_t> lid, lc0;
+        cols.clear();
+        size_t sm = 0;
+        for (size_t k = 0; k < nt; k++) {
+            const bk_task &T = pl.tasks[(size_t)ids[k]];
+            if ((size_t)T.level != l) continue;
+            lid.push_back(ids[k]);
+            lc0.push_back(c0[k]);
+            redone += T.hi - c0[k];
+            if (T.wsoff < 0) sm = std::max(sm, bk_task_smem_bytes(T));
+            if (T.sp_lo < T.lo)
+                for (int32_t c = c0[k]; c < T.hi; c++) cols.push_back(c);
+        }
+        if (lid.empty()) continue;
+        // stage: [tasks | c0 | cols] after the first 2*nt ints of the staging buffer
+        int32_t *st = h->h_stage + 2 * nt;
+        const size_t m = lid.size();
+        CU(cudaStreamSynchronize(s));     // the staging buffer is reused per level
+        std::memcpy(st, lid.data(), m * 4);
+        std::memcpy(st + m, lc0.data(), m * 4);
+        CU(cudaMemcpyAsync(h->rd_tasks, st, m * 4, cudaMemcpyHostToDevice, s));
+        CU(cudaMemcpyAsync(h->rd_c0, st + m, m * 4, cudaMemcpyHostToDevice, s));
+        if (!cols.empty()) {
+            CU(cudaMemcpyAsync(h->rd_cols, cols.data(), cols.size() * 4, cudaMemcpyHostToDevice, s));
+            CU(cudaMemsetAsync(h->d.counter + 3, 0, sizeof(int32_t), s));
+            tbeg(h, KT_DESC, s, 1);
+            bk_launch_gp_desc(h->d, h->rd_cols, (int32_t)cols.size(), h->d.counter + 3, s);
+            tend(h, s);
+            h->launches++;
+            CU(cudaStreamSynchronize(s));  // cols is pageable host memory
+        }
+        tbeg(h, KT_GP, s, 1);
+        bk_launch_gp_tasks(h->d, h->rd_tasks, h->rd_c0, (int32_t)m, (sm + 15) & ~(size_t)15, tau, 1, s);
+        tend(h, s);
+        h->launches++;
+    }
+    h->info.last_repivot_columns = redone;
+    CU(cudaGetLastError());
+    return BASKER_OK;
+}
+
+int compute_schedule(basker_t h, cudaStream_t s)
+{
+    h->epoch++;
+    tbeg(h, KT_LEVELS, s, 4);
+    bk_launch_levels(h->d, h->epoch, h->opt.wait_budget_cycles, bk_static_blocks(), s);
+    tend(h, s);
+    h->launches += 4;
+    CU(cudaGetLastError());
+    h->schedule_valid = true;
+    h->order_is_symbolic = false;
+    return BASKER_OK;
+}
+
+int static_pass(basker_t h, cudaStream_t s)
+{
+    CU(cudaMemsetAsync(h->d.task_fail, 0x7f, sizeof(int32_t) * h->pl.tasks.size(), s));
+    CU(cudaMemsetAsync(h->d.counter, 0, sizeof(int32_t), s));
+    h->epoch++;
+    tbeg(h, KT_STATIC, s, 1);
+    bk_launch_static(h->d, h->pl.n, h->opt.tau, h->epoch, h->opt.wait_budget_cycles, bk_static_blocks(), s);
+    tend(h, s);
+    h->launches++;
+    CU(cudaGetLastError());
+    return BASKER_OK;
+}
+
+// After a static pass: which tasks must be redone, and from which column.
+void redo_set(basker_t h, std::vector<int32_t> &start)
+{
+    bk_plan &pl = h->pl;
+    const size_t nt = pl.tasks.size();
+    start.assign(nt, INT_MAX);
+    for (size_t t = 0; t < nt; t++) {
+        const int32_t f = h->h_task_fail[t];
+        if (f >= pl.tasks[t].lo && f < pl.tasks[t].hi) start[t] = f;
+    }
+    // every ancestor of a redone ND node is redone from its first column
+    for (size_t t = 0; t < nt; t++) {
+        if (start[t] == INT_MAX || pl.tasks[t].node < 0) continue;
+        const bk_task &T = pl.tasks[t];
+        for (int32_t a = 0; a < T.nanc; a++) {
+            const int32_t tid = pl.col_task[(size_t)T.anc_lo[a]];
+            start[(size_t)tid] = pl.tasks[(size_t)tid].lo;
+        }
+    }
+}
+
+int factor_impl(basker_t h, const double *values, cudaStream_t s, bool refactor)
+{
+    h->launches = 0;
+    TRY(reset_status(h, s));
+    tbeg(h, KT_GATHER, s, 1);
+    bk_launch_gather(h->d, values, h->pl.nnz, s);
+    tend(h, s);
+    h->launches++;
+    if (refactor) {
+        CU(cudaMemcpyAsync((void *)h->d.pref, h->d.prow, sizeof(int32_t) * (size_t)h->pl.n,
+                           cudaMemcpyDeviceToDevice, s));
+        if (!h->schedule_valid) TRY(compute_schedule(h, s));
+        TRY(static_pass(h, s));
+        CU(cudaMemcpyAsync(h->h_task_fail, h->d.task_fail, sizeof(int32_t) * h->pl.tasks.size(),
+                           cudaMemcpyDeviceToHost, s));
+        int st = read_status(h, s);
+        if (st == BASKER_ERR_TIMEOUT) return st;
+        h->info.last_repivot_columns = 0;
+        if (h->h_status->static_fail) {
+            std::vector<int32_t> start;
+            redo_set(h, start);
+            TRY(launch_redo(h, s, start));
+            st = read_status(h, s);
+            h->schedule_valid = false;
+            if (st == -1) {
+                // the new pivots need more room: grow and run Algorithm 1 everywhere
+                for (int tries = 0; st == -1 && tries < 6; tries++) {
+                    TRY(regrow(h));
+                    TRY(reset_status(h, s));
+                    TRY(launch_full_gp(h, s, 1));
+                    st = read_status(h, s);
+                }
+            }
+        }
+        if (st != BASKER_OK) { h->factored = false; return st == -1 ? BASKER_ERR_OOM : st; }
+        h->factored = true;
+        return BASKER_OK;
+    }
+    int st = -1;
+    for (int tries = 0; tries < 8; tries++) {
+        if (tries > 0) {
+            TRY(regrow(h));
+            TRY(reset_status(h, s));
+            tbeg(h, KT_GATHER, s, 1);
+            bk_launch_gather(h->d, values, h->pl.nnz, s);
+            tend(h, s);
+        }
+        TRY(launch_full_gp(h, s, 0));
+        st = read_status(h, s);
+        if (st != -1) break;
+    }
+    if (st != BASKER_OK) { h->factored = false; return st == -1 ? BASKER_ERR_OOM : st; }
+    h->info.off_diagonal_pivots = h->h_status->offdiag;
+    // with the natural pivots everywhere the pattern is the symbolic one, whose
+    // static schedule is already on the device
+    h->schedule_valid = (h->h_status->offdiag == 0 && h->order_is_symbolic);
+    h->factored = true;
+    return BASKER_OK;
+}
+
+int ensure_solve_buffers(basker_t h, int32_t nrhs)
+{
+    if (nrhs <= h->nrhs_cap) return BASKER_OK;
+    dfree(h, h->sd.w);
+    dfree(h, h->sd.acc);
+    h->sd.w = h->sd.acc = nullptr;
+    TRY(dalloc(h, &h->sd.w, (size_t)h->pl.n * (size_t)nrhs));
+    TRY(dalloc(h, &h->sd.acc, (size_t)h->sd.acc_stride * (size_t)nrhs));
+    h->nrhs_cap = nrhs;
+    return BASKER_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void basker_default_options(basker_options *opt)
+{
+    if (!opt) return;
+    std::memset(opt, 0, sizeof *opt);
+    opt->tau = 1e-3;
+    opt->slack = 1.0;
+    opt->wait_budget_cycles = 20000000000LL;
+    opt->factor_mode = 0;
+}
+
+const char *basker_strerror(int status)
+{
+    switch (status) {
+    case BASKER_OK: return "ok";
+    case BASKER_ERR_INVALID_ARG: return "invalid argument";
+    case BASKER_ERR_NOT_BTF: return "matrix is not block upper triangular under P, Q";
+    case BASKER_ERR_BAD_ND: return "an entry crosses an ND separator";
+    case BASKER_ERR_SINGULAR: return "singular: no nonzero pivot candidate";
+    case BASKER_ERR_NAN: return "non-finite value in a factored column";
+    case BASKER_ERR_OOM: return "out of memory";
+    case BASKER_ERR_TIMEOUT: return "in-kernel wait exceeded its budget";
+    case BASKER_ERR_CUDA: return "CUDA runtime error";
+    case BASKER_ERR_NOT_FACTORED: return "not factored";
+    default: return "unknown status";
+    }
+}
+
+int basker_symbolic(int32_t n, const int32_t *colptr, const int32_t *rowind, const int32_t *P,
+                    const int32_t *Q, int32_t nblocks, const int32_t *block_ptr, int32_t nd_block,
+                    int32_t nd_leaves, const int32_t *nd_node_ptr, const basker_options *opt,
+                    basker_t *out)
+{
+    if (!out) return BASKER_ERR_INVALID_ARG;
+    *out = nullptr;
+    basker_t h = new (std::nothrow) basker_s();
+    if (!h) return BASKER_ERR_OOM;
+    basker_default_options(&h->opt);
+    if (opt) h->opt = *opt;
+    if (!(h->opt.tau > 0.0 && h->opt.tau <= 1.0) || h->opt.slack < 0.0 || h->opt.wait_budget_cycles <= 0 ||
+        h->opt.factor_mode != 0) {
+        delete h;
+        return BASKER_ERR_INVALID_ARG;
+    }
+    cudaGetDevice(&h->device);
+    int32_t bad = -1;
+    int st = bk_plan_build(n, colptr, rowind, P, Q, nblocks, block_ptr, nd_block, nd_leaves, nd_node_ptr,
+                           h->opt.slack, h->pl, &bad);
+    if (st == BASKER_OK) st = setup_device(h);
+    if (st != BASKER_OK) {
+        h->info.failed_column = bad;
+        basker_free(h);
+        return st;
+    }
+    h->info.n = n;
+    h->info.nblocks = nblocks;
+    h->info.nd_block = h->pl.nd_block;
+    h->info.nd_leaves = h->pl.nd_leaves;
+    h->info.nnz_a = h->pl.nnz;
+    h->info.nnz_l_sym = h->pl.nnz_l_sym;
+    h->info.nnz_u_sym = h->pl.nnz_u_sym;
+    h->info.failed_column = -1;
+    *out = h;
+    return BASKER_OK;
+}
+
+int basker_factor(basker_t h, const double *values_dev, void *stream)
+{
+    if (!h || (!values_dev && h->pl.nnz > 0)) return BASKER_ERR_INVALID_ARG;
+    cudaSetDevice(h->device);
+    h->factored = false;
+    int st = factor_impl(h, values_dev, (cudaStream_t)stream, false);
+    h->info.gp_launches = h->launches;
+    return st;
+}
+
+int basker_refactor(basker_t h, const double *values_dev, void *stream)
+{
+    if (!h || (!values_dev && h->pl.nnz > 0)) return BASKER_ERR_INVALID_ARG;
+    if (!h->factored) return BASKER_ERR_NOT_FACTORED;
+    cudaSetDevice(h->device);
+    int st = factor_impl(h, values_dev, (cudaStream_t)stream, true);
+    h->info.static_launches = h->launches;
+    return st;
+}
+
+int basker_solve(basker_t h, int32_t nrhs, const double *b_dev, int32_t ldb, double *x_dev, int32_t ldx,
+                 void *stream)
+{
+    if (!h || nrhs < 0 || (nrhs > 0 && (!b_dev || !x_dev || ldb < h->pl.n || ldx < h->pl.n)))
+        return BASKER_ERR_INVALID_ARG;
+    if (!h->factored) return BASKER_ERR_NOT_FACTORED;
+    if (nrhs == 0 || h->pl.n == 0) return BASKER_OK;
+    cudaSetDevice(h->device);
+    TRY(ensure_solve_buffers(h, nrhs));
+    cudaStream_t s = (cudaStream_t)stream;
+    CU(cudaMemsetAsync(h->d.counter + 2, 0, sizeof(int32_t), s));
+    h->solve_epoch++;
+    tbeg(h, KT_SOLVE, s, 1);
+    bk_launch_solve(h->d, h->sd, nrhs, b_dev, ldb, x_dev, ldx, h->solve_epoch, h->opt.wait_budget_cycles, s);
+    tend(h, s);
+    CU(cudaGetLastError());
+    return BASKER_OK;
+}
+
+int basker_refactor_solve_host(basker_t h, const double *values_host, int32_t nrhs, const double *b_host,
+                               double *x_host, void *stream)
+{
+    if (!h || !values_host || nrhs < 0 || (nrhs > 0 && (!b_host || !x_host))) return BASKER_ERR_INVALID_ARG;
+    cudaSetDevice(h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t n = (size_t)h->pl.n;
+    if (!h->d_vals) TRY(dalloc(h, &h->d_vals, (size_t)h->pl.nnz));
+    if (nrhs > h->stage_nrhs) {
+        dfree(h, h->d_b);
+        dfree(h, h->d_x);
+        h->d_b = h->d_x = nullptr;
+        TRY(dalloc(h, &h->d_b, n * (size_t)nrhs));
+        TRY(dalloc(h, &h->d_x, n * (size_t)nrhs));
+        h->stage_nrhs = nrhs;
+    }
+    CU(cudaMemcpyAsync(h->d_vals, values_host, sizeof(double) * (size_t)h->pl.nnz, cudaMemcpyHostToDevice, s));
+    if (nrhs > 0) CU(cudaMemcpyAsync(h->d_b, b_host, sizeof(double) * n * (size_t)nrhs, cudaMemcpyHostToDevice, s));
+    int st = h->factored ? basker_refactor(h, h->d_vals, stream) : basker_factor(h, h->d_vals, stream);
+    if (st != BASKER_OK) return st;
+    if (nrhs > 0) {
+        TRY(basker_solve(h, nrhs, h->d_b, (int32_t)n, h->d_x, (int32_t)n, stream));
+        CU(cudaMemcpyAsync(x_host, h->d_x, sizeof(double) * n * (size_t)nrhs, cudaMemcpyDeviceToHost, s));
+    }
+    CU(cudaStreamSynchronize(s));
+    return BASKER_OK;
+}
+
+int basker_info(basker_t h, basker_info_t *out)
+{
+    if (!h || !out) return BASKER_ERR_INVALID_ARG;
+    cudaSetDevice(h->device);
+    h->info.device_bytes = h->device_bytes;
+    tflush(h);
+    *out = h->info;
+    for (double &v : h->info.kernel_ms) v = 0.0;
+    if (!h->factored) return BASKER_OK;
+    {
+        const size_t n = (size_t)h->pl.n;
+        std::vector<int32_t> lc(n), uc(n);
+        CU(cudaDeviceSynchronize());
+        CU(cudaMemcpy(lc.data(), h->d.Lcnt, n * 4, cudaMemcpyDeviceToHost));
+        CU(cudaMemcpy(uc.data(), h->d.Ucnt, n * 4, cudaMemcpyDeviceToHost));
+        int64_t nl = 0, nu = 0;
+        for (size_t c = 0; c < n; c++) { nl += lc[c]; nu += uc[c]; }
+        h->info.nnz_l = nl;
+        h->info.nnz_u = nu;
+        // flops: sum_j l_j (2 u_j + 1), u_j = entries right of the diagonal in row j of U
+        std::vector<int64_t> ub(n + 1);
+        CU(cudaMemcpy(ub.data(), h->d.Ubeg, (n + 1) * 8, cudaMemcpyDeviceToHost));
+        std::vector<int32_t> ui((size_t)h->pl.ucap);
+        CU(cudaMemcpy(ui.data(), h->d.Ui, ui.size() * 4, cudaMemcpyDeviceToHost));
+        std::vector<int32_t> urow(n, 0);
+        for (size_t c = 0; c < n; c++)
+            for (int32_t k = 0; k + 1 < uc[c]; k++) urow[(size_t)ui[(size_t)(ub[c] + k)]]++;
+        double fl = 0;
+        for (size_t c = 0; c < n; c++) fl += (double)lc[c] * (2.0 * urow[c] + 1.0);
+        h->info.flops = fl;
+        out->nnz_l = nl;
+        out->nnz_u = nu;
+        out->flops = fl;
+    }
+    return BASKER_OK;
+}
+
+int basker_export(basker_t h, int32_t *prow, int64_t *Lp, int32_t *Li, double *Lx, int64_t *Up, int32_t *Ui,
+                  double *Ux, int64_t *nnz_l, int64_t *nnz_u)
+{
+    if (!h || !nnz_l || !nnz_u) return BASKER_ERR_INVALID_ARG;
+    if (!h->factored) return BASKER_ERR_NOT_FACTORED;
+    cudaSetDevice(h->device);
+    CU(cudaDeviceSynchronize());
+    const size_t n = (size_t)h->pl.n;
+    std::vector<int32_t> lc(n), uc(n), pr(n), pinv(n);
+    std::vector<int64_t> lb(n + 1), ub(n + 1);
+    CU(cudaMemcpy(lc.data(), h->d.Lcnt, n * 4, cudaMemcpyDeviceToHost));
+    CU(cudaMemcpy(uc.data(), h->d.Ucnt, n * 4, cudaMemcpyDeviceToHost));
+    CU(cudaMemcpy(pr.data(), h->d.prow, n * 4, cudaMemcpyDeviceToHost));
+    CU(cudaMemcpy(pinv.data(), h->d.pinv, n * 4, cudaMemcpyDeviceToHost));
+    CU(cudaMemcpy(lb.data(), h->d.Lbeg, (n + 1) * 8, cudaMemcpyDeviceToHost));
+    CU(cudaMemcpy(ub.data(), h->d.Ubeg, (n + 1) * 8, cudaMemcpyDeviceToHost));
+    int64_t nl = 0, nu = 0;
+    for (size_t c = 0; c < n; c++) { nl += lc[c]; nu += uc[c]; }
+    *nnz_l = nl;
+    *nnz_u = nu;
+    if (!Li) return BASKER_OK;
+    if (!prow || !Lp || !Lx || !Up || !Ui || !Ux) return BASKER_ERR_INVALID_ARG;
+    std::vector<int32_t> li((size_t)h->pl.lcap), ui((size_t)h->pl.ucap);
+    std::vector<double> lx((size_t)h->pl.lcap), ux((size_t)h->pl.ucap);
+    CU(cudaMemcpy(li.data(), h->d.Li, li.size() * 4, cudaMemcpyDeviceToHost));
+    CU(cudaMemcpy(lx.data(), h->d.Lx, lx.size() * 8, cudaMemcpyDeviceToHost));
+    CU(cudaMemcpy(ui.data(), h->d.Ui, ui.size() * 4, cudaMemcpyDeviceToHost));
+    CU(cudaMemcpy(ux.data(), h->d.Ux, ux.size() * 8, cudaMemcpyDeviceToHost));
+    std::memcpy(prow, pr.data(), n * 4);
+    Lp[0] = Up[0] = 0;
+    std::vector<std::pair<int32_t, double>> col;
+    for (size_t c = 0; c < n; c++) {
+        col.clear();
+        for (int32_t k = 0; k < lc[c]; k++) {
+            const int32_t r = li[(size_t)(lb[c] + k)];
+            col.emplace_back(r >= 0 && (size_t)r < n ? pinv[(size_t)r] : -1, lx[(size_t)(lb[c] + k)]);
+        }
+        std::sort(col.begin(), col.end(), [](const std::pair<int32_t, double> &a, const std::pair<int32_t, double> &b) {
+            return a.first < b.first;
+        });
+        int64_t o = Lp[c];
+        for (auto &e : col) { Li[o] = e.first; Lx[o] = e.second; o++; }
+        Lp[c + 1] = o;
+        int64_t q = Up[c];
+        for (int32_t k = 0; k < uc[c]; k++) {
+            Ui[q] = ui[(size_t)(ub[c] + k)];
+            Ux[q] = ux[(size_t)(ub[c] + k)];
+            q++;
+        }
+        Up[c + 1] = q;
+    }
+    return BASKER_OK;
+}
+
+void basker_free(basker_t h)
+{
+    if (!h) return;
+    cudaSetDevice(h->device);
+    cudaDeviceSynchronize();
+    for (void *p : h->allocs) cudaFree(p);
+    if (h->h_stage) cudaFreeHost(h->h_stage);
+    if (h->h_status) cudaFreeHost(h->h_status);
+    if (h->h_task_fail) cudaFreeHost(h->h_task_fail);
+    for (auto &t : h->pending) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
+    for (auto e : h->pool) cudaEventDestroy(e);
+    if (h->open_ev) cudaEventDestroy(h->open_ev);
+    delete h;
+}
+
+}  // extern "C"

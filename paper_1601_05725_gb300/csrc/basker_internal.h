@@ -1,0 +1,139 @@
+// basker_internal.h -- plan, task and device-view types of the CUDA library.
+//
+// Layout in device memory (one arena per handle, all in B = A(P,Q) coordinates):
+//   Bp[n+1], Bi[nnzB]        pattern of B, rows sorted; dstart[c] = first entry of
+//                            column c inside its diagonal block (entries above it are
+//                            the off-diagonal BTF blocks, kept for the solve)
+//   bmap[nnzB]               B entry -> index in A's CSC value array (value gather)
+//   Bx[nnzB]                 values of B (double)
+//   L: Lbeg[n] (int64), Lcnt[n], Li (B rows, ascending), Lx   strictly lower part
+//   U: Ubeg[n] (int64), Ucnt[n], Ui (pivot steps, ascending, diagonal last), Ux
+//   prow[k] = B row pivoted at step k, pinv = its inverse (-1 = not yet pivoted)
+//   Each task (a BTF block, or an ND node) owns one contiguous region of L and of
+//   U; its columns are stored one after the other in column order.
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include "../../include/basker.h"
+
+#define BK_MAX_ANC 16          // ND depth limit (65,536 leaves)
+#define BK_WARP 32
+
+// One unit of Algorithm 1 work: the columns of a BTF block or of an ND node,
+// factored in order by one warp.  Rows of the task's "space" are the only rows a
+// column of the task can touch: its subtree [sp_lo, hi) (descendants are already
+// pivoted, the node's own rows [lo, hi) are the pivot candidates) followed by the
+// rows of its ND ancestors (never pivoted here, they receive the L_kj entries).
+struct bk_task {
+    int32_t c0, c1;            // columns to factor, c0 >= lo (c0 > lo: a partial redo)
+    int32_t lo, hi;            // the node's own rows / columns
+    int32_t sp_lo;             // first row of the subtree
+    int32_t nanc;              // number of ancestor ranges (ascending rows)
+    int32_t anc_lo[BK_MAX_ANC];
+    int32_t anc_hi[BK_MAX_ANC];
+    int32_t space;             // (hi - sp_lo) + sum of ancestor sizes
+    int32_t lspace;            // (hi - lo) + sum of ancestor sizes (rows that can be unpivoted)
+    int64_t lbeg, lend;        // L region
+    int64_t ubeg, uend;        // U region
+    int64_t wsoff;             // offset (bytes) of x + bitmaps in the global workspace, -1 = shared
+    int64_t ahoff;             // separators: first double of the task's A-hat columns (lspace each)
+    int64_t aboff;             // separators: first word of their pattern bitmaps (ceil(lspace/32) each)
+    int32_t level;             // height in the ND tree (0: leaves and small BTF blocks)
+    int32_t node;              // ND node (postorder) or -1
+    int32_t block;             // BTF block
+    int32_t pad;
+};
+
+// Status word written by the kernels (device), read back once per call.
+struct bk_status {
+    unsigned long long first_fail;   // min over failures of (column << 8 | code)
+    int32_t capacity;                // nonzero: an L/U region overflowed
+    int32_t timeout;                 // nonzero: a wait gave up
+    int32_t static_fail;             // nonzero: a column rejected its preferred pivot
+    int32_t offdiag;                 // number of columns pivoting off the natural row
+};
+
+enum { BK_CODE_SINGULAR = 1, BK_CODE_NAN = 2, BK_CODE_INTERNAL = 3 };  // INTERNAL: an index outside its space
+
+// Everything the kernels read, as raw device pointers (passed by value).
+struct bk_dev {
+    int32_t n;
+    int32_t ntasks;
+    const int32_t *Bp, *Bi, *dstart, *bmap, *col_task;
+    double *Bx;
+    bk_task *tasks;
+    int32_t *prow, *pinv;
+    const int32_t *pref;             // refactor: the previous pivot rows, preferred
+    int64_t *Lbeg, *Ubeg;
+    int32_t *Lcnt, *Ucnt;
+    int32_t *Li, *Ui;
+    double *Lx, *Ux;
+    bk_status *status;
+    int32_t *task_fail;              // per task: first column that rejected its preferred pivot
+    unsigned char *ws;               // global workspace (zero between uses)
+    int32_t *done;                   // per column: epoch of its last completion (static kernel)
+    int32_t *order;                  // static kernel claim order (topological)
+    int32_t *counter;                // claim counters
+    int32_t *level;                  // per column level in the static DAG
+    double *ahat;                    // separator columns after the descendant phase (dense, L-space)
+    uint32_t *abits;                 // their patterns
+    int32_t *dcnt;                   // per column: U entries written by the descendant phase
+    unsigned char *wsd;              // descendant-phase workspace, one slice per warp
+    int64_t wsd_slice;               // bytes per slice
+    int32_t wsd_warps;
+    double *sx;                      // static kernel: per-warp dense x slices
+    int64_t sx_stride;               // doubles per warp slice
+    int32_t sx_warps;
+    // solve
+    int32_t nblocks;
+    const int32_t *block_ptr;
+    const int32_t *P, *Q;
+};
+
+// Host-side plan built by the symbolic pass.
+struct bk_plan {
+    int32_t n = 0, nblocks = 0, nd_block = -1, nd_leaves = 0, depth = 0;
+    int64_t nnz = 0;
+    std::vector<int32_t> P, Q, block_ptr, nd_ptr, nd_first, nd_height;
+    std::vector<int32_t> Bp, Bi, bmap, dstart;
+    std::vector<bk_task> tasks;
+    std::vector<int32_t> col_task;
+    std::vector<std::vector<int32_t>> level_tasks;   // task ids per GP level
+    // pattern under the preferred (natural) pivots, in the task-region layout
+    std::vector<int64_t> sLbeg, sUbeg;
+    std::vector<int32_t> sLcnt, sUcnt, sLi, sUi, sprow;
+    std::vector<int32_t> slevel, sorder;              // static DAG levels and claim order
+    int64_t lcap = 0, ucap = 0, nnz_l_sym = 0, nnz_u_sym = 0;
+    int64_t ws_bytes = 0;                             // GP global workspace
+    int64_t ahat_doubles = 0, ahat_words = 0;         // separator A-hat scratch
+    int64_t wsd_slice = 0;                            // descendant-phase slice (bytes)
+    int32_t wsd_warps = 0;                            // descendant-phase warps (max columns of a level)
+    int32_t max_space = 0;
+    int32_t symbolic_singular = -1;                   // first column without a structural pivot
+    double slack = 0.5;
+};
+
+// symbolic.cpp
+int bk_plan_build(int32_t n, const int32_t *colptr, const int32_t *rowind, const int32_t *P,
+                  const int32_t *Q, int32_t nblocks, const int32_t *block_ptr, int32_t nd_block,
+                  int32_t nd_leaves, const int32_t *nd_node_ptr, double slack, bk_plan &plan,
+                  int32_t *bad_col);
+void bk_plan_layout(bk_plan &plan, double grow);   // (re)assign L/U regions with capacities
+size_t bk_task_smem_bytes(const bk_task &t);
+bool bk_task_fits_smem(const bk_task &t);
+
+// kernels (launchers), kernels_*.cu
+void bk_launch_gather(const bk_dev &d, const double *values, int64_t nnz, void *stream);
+void bk_launch_gp_tasks(const bk_dev &d, const int32_t *task_ids, const int32_t *task_c0,
+                        int32_t ntasks, size_t smem, double tau, int pref_mode, void *stream);
+void bk_launch_gp_desc(const bk_dev &d, const int32_t *cols, int32_t ncols, int32_t *counter,
+                       void *stream);
+void bk_launch_reset_pivots(const bk_dev &d, const int32_t *task_ids, const int32_t *task_c0,
+                            int32_t ntasks, void *stream);
+void bk_launch_static(const bk_dev &d, int32_t ncols, double tau, int32_t epoch,
+                      long long budget, int blocks, void *stream);
+void bk_launch_levels(const bk_dev &d, int32_t epoch, long long budget, int blocks, void *stream);
+int bk_static_blocks();
+size_t bk_gp_smem_limit();

@@ -1,0 +1,122 @@
+// device_util.cuh -- small device helpers shared by the library's kernels.
+#pragma once
+
+#include <cstdint>
+
+#include "basker_internal.h"
+
+#define BK_FULL 0xffffffffu
+
+namespace bk {
+
+// Slot of row r in a task's dense column space.  The space lists the rows
+// [base, hi) (base = sp_lo: subtree and own rows; base = lo: own rows only) and
+// then each ancestor node's rows, ancestors in ascending row order; so slots are
+// ascending in r.  Returns -1 for a row outside the space.
+__device__ __forceinline__ int slot_of(const bk_task &T, int base, int r)
+{
+    if (r >= base && r < T.hi) return r - base;
+    int off = T.hi - base;
+#pragma unroll 1
+    for (int a = 0; a < T.nanc; a++) {
+        const int lo = T.anc_lo[a], hi = T.anc_hi[a];
+        if (r >= lo && r < hi) return off + (r - lo);
+        off += hi - lo;
+    }
+    return -1;
+}
+
+// Row of an index of the L-space (own rows [lo, hi), then the ancestors' rows).
+__device__ __forceinline__ int row_of_lslot(const bk_task &T, int ls)
+{
+    const int own = T.hi - T.lo;
+    if (ls < own) return T.lo + ls;
+    ls -= own;
+#pragma unroll 1
+    for (int a = 0; a < T.nanc; a++) {
+        const int sz = T.anc_hi[a] - T.anc_lo[a];
+        if (ls < sz) return T.anc_lo[a] + ls;
+        ls -= sz;
+    }
+    return -1;
+}
+
+__device__ __forceinline__ double warp_max(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(BK_FULL, v, o));
+    return v;
+}
+
+__device__ __forceinline__ int warp_sum(int v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(BK_FULL, v, o);
+    return v;
+}
+
+__device__ __forceinline__ int warp_min(int v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(BK_FULL, v, o));
+    return v;
+}
+
+__device__ __forceinline__ int warp_max_i(int v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(BK_FULL, v, o));
+    return v;
+}
+
+// Exclusive prefix sum over the warp.
+__device__ __forceinline__ int warp_exscan(int v, int lane)
+{
+    int s = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(BK_FULL, s, o);
+        if (lane >= o) s += t;
+    }
+    return s - v;
+}
+
+__device__ __forceinline__ int ld_acquire(const int *p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(int *p, int v)
+{
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Copy a task descriptor into shared memory (all lanes of the warp).
+__device__ __forceinline__ void load_task(bk_task &dst, const bk_task *src, int lane)
+{
+    const int *s = reinterpret_cast<const int *>(src);
+    int *d = reinterpret_cast<int *>(&dst);
+    for (int i = lane; i < (int)(sizeof(bk_task) / 4); i += 32) d[i] = s[i];
+    __syncwarp();
+}
+
+// A failure (SINGULAR / NAN) at column c; the smallest column wins, as in a
+// column-by-column factorization that stops at its first failure.
+__device__ __forceinline__ void report_fail(bk_status *st, int c, int code)
+{
+    atomicMin(&st->first_fail, ((unsigned long long)(unsigned)c << 8) | (unsigned)code);
+}
+
+// Stop work on column c if an earlier (or the same) column already failed, or an
+// L/U region overflowed (the host regrows and starts over).
+__device__ __forceinline__ bool should_stop(const bk_status *st, int c)
+{
+    const unsigned long long f = *reinterpret_cast<const volatile unsigned long long *>(&st->first_fail);
+    const int cap = *reinterpret_cast<const volatile int *>(&st->capacity);
+    const int to = *reinterpret_cast<const volatile int *>(&st->timeout);
+    return cap != 0 || to != 0 || (long long)(f >> 8) <= (long long)c;
+}
+
+}  // namespace bk

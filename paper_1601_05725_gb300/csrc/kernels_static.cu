@@ -1,0 +1,263 @@
+// kernels_static.cu -- refactorization on a known pattern (the matrix-sequence
+// case of Sec. V-F: same pattern, new values, previous pivots preferred).
+//
+//   bk_static_kernel   persistent; each warp claims columns in a topological order
+//                      of the column DAG (column c waits for every step of
+//                      U(:,c)) and recomputes the column on the stored pattern:
+//                      x = B(:,c); for each step j of U(:,c), lowest first:
+//                      x -= L(:,j) x(prow j); then L(:,c) = x / pivot.  The
+//                      preferred pivot is validated as Algorithm 1 line 7 would
+//                      decide it (|x_pref| >= tau * max over the node's candidate
+//                      rows); a column that would pick another row is reported for
+//                      the reach-based path.  Waits are point-to-point flags (the
+//                      paper's volatile-flag synchronisation, Sec. IV) with an
+//                      iteration budget: a wait that runs out sets the timeout
+//                      status and every warp returns.
+//   bk_levels_kernel   the same dataflow over the current pattern, computing each
+//                      column's DAG level; a counting sort then gives the claim
+//                      order for the next static pass.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "basker_internal.h"
+#include "device_util.cuh"
+
+using namespace bk;
+
+namespace {
+
+// Wait until flag == epoch (lane 0 spins, the warp follows).  Returns false if the
+// budget ran out or another warp already gave up.
+__device__ __forceinline__ bool wait_flag(const bk_dev &d, const int *flag, int epoch, long long budget,
+                                          int lane)
+{
+    int ok = 1;
+    if (lane == 0) {
+        if (ld_acquire(flag) != epoch) {
+            const long long t0 = clock64();
+            for (;;) {
+                if (ld_acquire(flag) == epoch) break;
+                if (*reinterpret_cast<const volatile int *>(&d.status->timeout)) { ok = 0; break; }
+                if (clock64() - t0 > budget) {
+                    atomicExch(&d.status->timeout, 1);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+    }
+    ok = __shfl_sync(BK_FULL, ok, 0);
+    return ok != 0;
+}
+
+__global__ void __launch_bounds__(128) bk_static_kernel(bk_dev d, int32_t ncols, double tau, int32_t epoch,
+                                                        long long budget)
+{
+    __shared__ bk_task Ts[4];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int gw = blockIdx.x * 4 + wib;
+    if (gw >= d.sx_warps) return;
+    bk_task &T = Ts[wib];
+    double *x = d.sx + (int64_t)gw * d.sx_stride;
+    int cur = -1;
+    for (;;) {
+        int k = 0;
+        if (lane == 0) k = atomicAdd(d.counter, 1);
+        k = __shfl_sync(BK_FULL, k, 0);
+        if (k >= ncols) break;
+        const int c = d.order[k];
+        const int tid = d.col_task[c];
+        if (tid != cur) {
+            load_task(T, d.tasks + tid, lane);
+            cur = tid;
+        }
+        const int base = T.sp_lo;
+        const int e1 = d.Bp[c + 1];
+        bool broken = false;
+        for (int e = d.dstart[c] + lane; e < e1; e += 32) {
+            const int s = slot_of(T, base, d.Bi[e]);
+            if (s < 0) { broken = true; continue; }
+            x[s] = d.Bx[e];
+        }
+        __syncwarp();
+        const int64_t ub = d.Ubeg[c];
+        const int uc = d.Ucnt[c];
+        bool bad = false;
+        for (int q = 0; q < uc - 1; ++q) {
+            const int j = d.Ui[ub + q];
+            if (!wait_flag(d, d.done + j, epoch, budget, lane)) return;
+            const int sp = slot_of(T, base, d.prow[j]);
+            if (sp < 0) { broken = true; continue; }
+            const double m = x[sp];
+            __syncwarp();
+            if (lane == 0) {
+                x[sp] = 0.0;
+                d.Ux[ub + q] = m;
+            }
+            if (!isfinite(m)) bad = true;
+            const int64_t jl = d.Lbeg[j];
+            const int jc = d.Lcnt[j];
+            for (int t = lane; t < jc; t += 32) {
+                const int s = slot_of(T, base, d.Li[jl + t]);
+                if (s < 0) { broken = true; continue; }
+                x[s] = fma(-__ldcg(d.Lx + jl + t), m, x[s]);
+            }
+            __syncwarp();
+        }
+        const int p = d.prow[c];
+        int sp = slot_of(T, base, p);
+        if (sp < 0) { broken = true; sp = 0; }
+        const double xp = x[sp];
+        double amax = fabs(xp);
+        if (!isfinite(xp)) bad = true;
+        const int64_t lb = d.Lbeg[c];
+        const int lc = d.Lcnt[c];
+        for (int t = lane; t < lc; t += 32) {
+            const int r = d.Li[lb + t];
+            const int s = slot_of(T, base, r);
+            if (s < 0) { broken = true; continue; }
+            const double v = x[s];
+            x[s] = 0.0;
+            if (!isfinite(v)) bad = true;
+            if (r >= T.lo && r < T.hi) amax = fmax(amax, fabs(v));
+            d.Lx[lb + t] = v / xp;
+        }
+        amax = warp_max(amax);
+        bad = __any_sync(BK_FULL, bad);
+        if (__any_sync(BK_FULL, broken) && lane == 0) report_fail(d.status, c, BK_CODE_INTERNAL);
+        const bool ok = !bad && amax > 0.0 && fabs(xp) >= tau * amax;
+        __syncwarp();
+        __threadfence();
+        if (lane == 0) {
+            x[sp] = 0.0;
+            d.Ux[ub + uc - 1] = xp;
+            if (!ok) {
+                atomicMin(d.task_fail + tid, c);
+                atomicExch(&d.status->static_fail, 1);
+            }
+            __threadfence();
+            st_release(d.done + c, epoch);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(128) bk_levels_kernel(bk_dev d, int32_t epoch, long long budget,
+                                                        int32_t *maxlev)
+{
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        int c = 0;
+        if (lane == 0) c = atomicAdd(d.counter + 1, 1);
+        c = __shfl_sync(BK_FULL, c, 0);
+        if (c >= d.n) break;
+        const int64_t ub = d.Ubeg[c];
+        const int uc = d.Ucnt[c];
+        int lv = 0;
+        int ok = 1;
+        for (int q = lane; q < uc - 1; q += 32) {
+            const int j = d.Ui[ub + q];
+            const int *flag = d.done + j;
+            if (ld_acquire(flag) != epoch) {
+                const long long t0 = clock64();
+                while (ld_acquire(flag) != epoch) {
+                    if (*reinterpret_cast<const volatile int *>(&d.status->timeout) || clock64() - t0 > budget) {
+                        atomicExch(&d.status->timeout, 1);
+                        ok = 0;
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+            }
+            if (!ok) break;
+            lv = max(lv, __ldcg(d.level + j) + 1);
+        }
+        if (__any_sync(BK_FULL, !ok)) return;
+        lv = warp_max_i(lv);
+        if (lane == 0) {
+            d.level[c] = lv;
+            atomicMax(maxlev, lv);
+            __threadfence();
+            st_release(d.done + c, epoch);
+        }
+        __syncwarp();
+    }
+}
+
+__global__ void bk_level_count(const int32_t *__restrict__ level, int32_t n, int32_t *cnt)
+{
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x)
+        atomicAdd(cnt + level[c], 1);
+}
+
+// Exclusive scan of cnt[0..m) in place, one block of 1024 threads.
+__global__ void __launch_bounds__(1024) bk_level_scan(int32_t *cnt, int32_t m)
+{
+    __shared__ int part[1024];
+    const int t = threadIdx.x;
+    const int chunk = (m + 1023) / 1024;
+    const int a = min(m, t * chunk), b = min(m, a + chunk);
+    int s = 0;
+    for (int i = a; i < b; i++) s += cnt[i];
+    part[t] = s;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        int v = t >= o ? part[t - o] : 0;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    int run = part[t] - s;
+    for (int i = a; i < b; i++) {
+        const int v = cnt[i];
+        cnt[i] = run;
+        run += v;
+    }
+}
+
+__global__ void bk_level_scatter(const int32_t *__restrict__ level, int32_t n, int32_t *cursor,
+                                 int32_t *order)
+{
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x)
+        order[atomicAdd(cursor + level[c], 1)] = c;
+}
+
+}  // namespace
+
+int bk_static_blocks()
+{
+    static int blocks = 0;
+    if (!blocks) {
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, bk_static_kernel, 128, 0);
+        blocks = std::max(1, sms) * std::max(1, std::min(per, 4));
+    }
+    return blocks;
+}
+
+void bk_launch_static(const bk_dev &d, int32_t ncols, double tau, int32_t epoch, long long budget,
+                      int blocks, void *stream)
+{
+    if (ncols <= 0) return;
+    bk_static_kernel<<<blocks, 128, 0, (cudaStream_t)stream>>>(d, ncols, tau, epoch, budget);
+}
+
+// Levels of the current pattern's column DAG and the claim order sorted by level.
+// scratch: n + 2 ints (counts), last one receives the maximum level.
+void bk_launch_levels(const bk_dev &d, int32_t epoch, long long budget, int blocks, void *stream)
+{
+    cudaStream_t s = (cudaStream_t)stream;
+    int32_t *cnt = d.level + d.n;               // level array holds n + (n + 2) ints
+    int32_t *maxlev = cnt + d.n + 1;
+    cudaMemsetAsync(cnt, 0, sizeof(int32_t) * ((size_t)d.n + 2), s);
+    cudaMemsetAsync(d.counter + 1, 0, sizeof(int32_t), s);
+    bk_levels_kernel<<<blocks, 128, 0, s>>>(d, epoch, budget, maxlev);
+    int g = std::max(1, std::min((d.n + 255) / 256, 152 * 8));
+    bk_level_count<<<g, 256, 0, s>>>(d.level, d.n, cnt);
+    bk_level_scan<<<1, 1024, 0, s>>>(cnt, d.n + 1);
+    bk_level_scatter<<<g, 256, 0, s>>>(d.level, d.n, cnt, d.order);
+}

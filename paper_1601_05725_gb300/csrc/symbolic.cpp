@@ -1,0 +1,368 @@
+// symbolic.cpp -- host planner of the CUDA library (basker_symbolic).
+//
+// Validates the input, forms the pattern of B = A(P,Q) (the BTF form of Sec. II /
+// III-A), checks that B is block upper triangular and that, inside the ND block,
+// every entry joins two nodes on one root path (the separators of Sec. III-C
+// disconnect their halves), builds the tasks of the level schedule (Algorithm 4's
+// dependency tree: leaves and small BTF blocks first, then separators by height),
+// and runs a structural Gilbert-Peierls pass under the preferred (natural) pivots
+// to size every column's L and U storage (the role of Algorithms 2 and 3, which
+// estimate counts; this pass computes them exactly for those pivots and adds
+// slack for pivoting).  The pass uses symmetric pruning of the reach graph
+// (Eisenstat and Liu) so that its cost stays near |L+U|.
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+
+#include "basker_internal.h"
+
+namespace {
+
+bool is_permutation(int32_t n, const int32_t *p)
+{
+    std::vector<char> seen((size_t)n, 0);
+    for (int32_t i = 0; i < n; i++) {
+        if (p[i] < 0 || p[i] >= n || seen[(size_t)p[i]]) return false;
+        seen[(size_t)p[i]] = 1;
+    }
+    return true;
+}
+
+// Complete binary ND tree in postorder: children before the separator above them.
+int32_t number_tree(int32_t height, int32_t &next, std::vector<int32_t> &first,
+                    std::vector<int32_t> &h, std::vector<int32_t> &parent)
+{
+    int32_t start = next, a = -1, b = -1;
+    if (height > 0) {
+        a = number_tree(height - 1, next, first, h, parent);
+        b = number_tree(height - 1, next, first, h, parent);
+    }
+    int32_t t = next++;
+    first[(size_t)t] = start;
+    h[(size_t)t] = height;
+    if (a >= 0) { parent[(size_t)a] = t; parent[(size_t)b] = t; }
+    return t;
+}
+
+}  // namespace
+
+// Column state of the in-node kernel: x over the L-space, a bitmap of own steps
+// and a bitmap of L-space rows.
+size_t bk_task_smem_bytes(const bk_task &t)
+{
+    size_t own = (size_t)(t.hi - t.lo);
+    return (size_t)t.lspace * 8 + ((own + 31) / 32) * 4 + (((size_t)t.lspace + 31) / 32) * 4 + 16;
+}
+
+bool bk_task_fits_smem(const bk_task &t) { return bk_task_smem_bytes(t) <= bk_gp_smem_limit(); }
+
+int bk_plan_build(int32_t n, const int32_t *colptr, const int32_t *rowind, const int32_t *P,
+                  const int32_t *Q, int32_t nblocks, const int32_t *block_ptr, int32_t nd_block,
+                  int32_t nd_leaves, const int32_t *nd_node_ptr, double slack, bk_plan &pl,
+                  int32_t *bad_col)
+{
+    *bad_col = -1;
+    if (n < 0 || nblocks < 0 || (n > 0 && nblocks < 1) || !colptr || (n > 0 && (!P || !Q || !block_ptr)))
+        return BASKER_ERR_INVALID_ARG;
+    if (colptr[0] != 0) return BASKER_ERR_INVALID_ARG;
+    for (int32_t j = 0; j < n; j++) {
+        if (colptr[j + 1] < colptr[j]) return BASKER_ERR_INVALID_ARG;
+        for (int32_t p = colptr[j]; p < colptr[j + 1]; p++)
+            if (rowind[p] < 0 || rowind[p] >= n || (p > colptr[j] && rowind[p] <= rowind[p - 1]))
+                return BASKER_ERR_INVALID_ARG;
+    }
+    if (n > 0 && (!is_permutation(n, P) || !is_permutation(n, Q))) return BASKER_ERR_INVALID_ARG;
+    if (block_ptr[0] != 0 || block_ptr[nblocks] != n) return BASKER_ERR_INVALID_ARG;
+    for (int32_t d = 0; d < nblocks; d++)
+        if (block_ptr[d + 1] <= block_ptr[d]) return BASKER_ERR_INVALID_ARG;
+
+    pl.n = n;
+    pl.nblocks = nblocks;
+    pl.slack = slack;
+    pl.P.assign(P, P + n);
+    pl.Q.assign(Q, Q + n);
+    pl.block_ptr.assign(block_ptr, block_ptr + nblocks + 1);
+    std::vector<int32_t> blk((size_t)n);
+    for (int32_t d = 0; d < nblocks; d++)
+        for (int32_t i = block_ptr[d]; i < block_ptr[d + 1]; i++) blk[(size_t)i] = d;
+
+    // ---- ND tree of one block
+    std::vector<int32_t> node_of;
+    std::vector<int32_t> parent;
+    pl.nd_block = -1;
+    if (nd_block >= 0) {
+        int32_t depth = 0;
+        while ((1 << depth) < nd_leaves && depth < 30) depth++;
+        if (nd_block >= nblocks || nd_leaves < 1 || (1 << depth) != nd_leaves || depth > BK_MAX_ANC || !nd_node_ptr)
+            return BASKER_ERR_INVALID_ARG;
+        int32_t nodes = 2 * nd_leaves - 1;
+        if (nd_node_ptr[0] != block_ptr[nd_block] || nd_node_ptr[nodes] != block_ptr[nd_block + 1])
+            return BASKER_ERR_INVALID_ARG;
+        for (int32_t t = 0; t < nodes; t++)
+            if (nd_node_ptr[t + 1] < nd_node_ptr[t]) return BASKER_ERR_INVALID_ARG;
+        pl.nd_block = nd_block;
+        pl.nd_leaves = nd_leaves;
+        pl.depth = depth;
+        pl.nd_ptr.assign(nd_node_ptr, nd_node_ptr + nodes + 1);
+        pl.nd_first.assign((size_t)nodes, 0);
+        pl.nd_height.assign((size_t)nodes, 0);
+        parent.assign((size_t)nodes, -1);
+        int32_t next = 0;
+        number_tree(depth, next, pl.nd_first, pl.nd_height, parent);
+        node_of.assign((size_t)n, -1);
+        for (int32_t t = 0; t < nodes; t++)
+            for (int32_t i = nd_node_ptr[t]; i < nd_node_ptr[t + 1]; i++) node_of[(size_t)i] = t;
+    }
+
+    // ---- B = A(P,Q), rows sorted, with the map back to A's entries
+    int64_t nnz = colptr[n];
+    if (nnz >= (int64_t)1 << 31) return BASKER_ERR_INVALID_ARG;
+    pl.nnz = nnz;
+    std::vector<int32_t> Pinv((size_t)n);
+    for (int32_t i = 0; i < n; i++) Pinv[(size_t)P[i]] = i;
+    pl.Bp.assign((size_t)n + 1, 0);
+    for (int32_t j = 0; j < n; j++) pl.Bp[(size_t)j + 1] = pl.Bp[(size_t)j] + (colptr[Q[j] + 1] - colptr[Q[j]]);
+    pl.Bi.resize((size_t)nnz);
+    pl.bmap.resize((size_t)nnz);
+    pl.dstart.resize((size_t)n);
+    std::vector<std::pair<int32_t, int32_t>> tmp;
+    for (int32_t j = 0; j < n; j++) {
+        int32_t q = Q[j];
+        tmp.clear();
+        for (int32_t p = colptr[q]; p < colptr[q + 1]; p++) tmp.emplace_back(Pinv[(size_t)rowind[p]], p);
+        std::sort(tmp.begin(), tmp.end());
+        int32_t o = pl.Bp[(size_t)j];
+        int32_t k0 = block_ptr[blk[(size_t)j]];
+        int32_t ds = -1;
+        for (size_t k = 0; k < tmp.size(); k++) {
+            int32_t r = tmp[k].first;
+            pl.Bi[(size_t)o + k] = r;
+            pl.bmap[(size_t)o + k] = tmp[k].second;
+            if (blk[(size_t)r] > blk[(size_t)j]) { *bad_col = j; return BASKER_ERR_NOT_BTF; }
+            if (ds < 0 && r >= k0) ds = o + (int32_t)k;
+            if (node_of.size() && blk[(size_t)j] == pl.nd_block && r >= k0) {
+                int32_t a = node_of[(size_t)r], b = node_of[(size_t)j];
+                bool rel = (pl.nd_first[(size_t)a] <= b && b <= a) || (pl.nd_first[(size_t)b] <= a && a <= b);
+                if (!rel) { *bad_col = j; return BASKER_ERR_BAD_ND; }
+            }
+        }
+        pl.dstart[(size_t)j] = ds < 0 ? pl.Bp[(size_t)j + 1] : ds;
+    }
+
+    // ---- tasks: BTF blocks, ND nodes (postorder), each with its row space
+    pl.tasks.clear();
+    pl.col_task.assign((size_t)n, -1);
+    int32_t maxlevel = 0;
+    for (int32_t d = 0; d < nblocks; d++) {
+        if (d == pl.nd_block) {
+            int32_t nodes = 2 * nd_leaves - 1;
+            for (int32_t t = 0; t < nodes; t++) {
+                if (pl.nd_ptr[(size_t)t + 1] == pl.nd_ptr[(size_t)t]) continue;
+                bk_task T;
+                std::memset(&T, 0, sizeof T);
+                T.lo = T.c0 = pl.nd_ptr[(size_t)t];
+                T.hi = T.c1 = pl.nd_ptr[(size_t)t + 1];
+                T.sp_lo = pl.nd_ptr[(size_t)pl.nd_first[(size_t)t]];
+                T.nanc = 0;
+                int32_t lsp = T.hi - T.lo;
+                for (int32_t a = parent[(size_t)t]; a >= 0; a = parent[(size_t)a]) {
+                    if (pl.nd_ptr[(size_t)a + 1] == pl.nd_ptr[(size_t)a]) continue;
+                    T.anc_lo[T.nanc] = pl.nd_ptr[(size_t)a];
+                    T.anc_hi[T.nanc] = pl.nd_ptr[(size_t)a + 1];
+                    lsp += T.anc_hi[T.nanc] - T.anc_lo[T.nanc];
+                    T.nanc++;
+                }
+                T.space = (T.hi - T.sp_lo) + (lsp - (T.hi - T.lo));
+                T.lspace = lsp;
+                T.level = pl.nd_height[(size_t)t];
+                T.node = t;
+                T.block = d;
+                maxlevel = std::max(maxlevel, T.level);
+                for (int32_t c = T.lo; c < T.hi; c++) pl.col_task[(size_t)c] = (int32_t)pl.tasks.size();
+                pl.tasks.push_back(T);
+            }
+        } else {
+            bk_task T;
+            std::memset(&T, 0, sizeof T);
+            T.lo = T.c0 = T.sp_lo = block_ptr[d];
+            T.hi = T.c1 = block_ptr[d + 1];
+            T.space = T.lspace = T.hi - T.lo;
+            T.level = 0;
+            T.node = -1;
+            T.block = d;
+            for (int32_t c = T.lo; c < T.hi; c++) pl.col_task[(size_t)c] = (int32_t)pl.tasks.size();
+            pl.tasks.push_back(T);
+        }
+    }
+    pl.level_tasks.assign((size_t)maxlevel + 1, {});
+    for (size_t i = 0; i < pl.tasks.size(); i++) pl.level_tasks[(size_t)pl.tasks[i].level].push_back((int32_t)i);
+    pl.max_space = 0;
+    for (auto &T : pl.tasks) pl.max_space = std::max(pl.max_space, T.space);
+
+    // ---- structural Gilbert-Peierls pass under the preferred pivots
+    std::vector<int32_t> pinv((size_t)n, -1), mark((size_t)n, -1);
+    pl.sprow.assign((size_t)n, -1);
+    std::vector<int64_t> Lst((size_t)n + 1, 0), Ust((size_t)n + 1, 0);
+    std::vector<int32_t> Lrows, Usteps;            // flat, column order
+    std::vector<int32_t> g;                        // reach graph: copy of L rows, prunable
+    std::vector<int64_t> gbeg((size_t)n, 0);
+    std::vector<int32_t> gend((size_t)n, 0), glen((size_t)n, 0);
+    std::vector<char> pruned((size_t)n, 0);
+    std::vector<int32_t> stack, spos, lrow, ustep;
+    pl.symbolic_singular = -1;
+    for (int32_t c = 0; c < n; c++) {
+        const bk_task &T = pl.tasks[(size_t)pl.col_task[(size_t)c]];
+        lrow.clear();
+        ustep.clear();
+        for (int32_t p = pl.dstart[(size_t)c]; p < pl.Bp[(size_t)c + 1]; p++) {
+            int32_t r0 = pl.Bi[(size_t)p];
+            if (mark[(size_t)r0] == c) continue;
+            mark[(size_t)r0] = c;
+            stack.assign(1, r0);
+            spos.assign(1, 0);
+            while (!stack.empty()) {
+                int32_t r = stack.back();
+                int32_t j = pinv[(size_t)r];
+                bool pushed = false;
+                if (j >= 0) {
+                    int32_t &k = spos.back();
+                    while (k < gend[(size_t)j]) {
+                        int32_t r2 = g[(size_t)(gbeg[(size_t)j] + k)];
+                        k++;
+                        if (mark[(size_t)r2] != c) {
+                            mark[(size_t)r2] = c;
+                            stack.push_back(r2);
+                            spos.push_back(0);
+                            pushed = true;
+                            break;
+                        }
+                    }
+                }
+                if (!pushed) {
+                    if (j >= 0) ustep.push_back(j); else lrow.push_back(r);
+                    stack.pop_back();
+                    spos.pop_back();
+                }
+            }
+        }
+        std::sort(ustep.begin(), ustep.end());
+        std::sort(lrow.begin(), lrow.end());
+        int32_t piv = -1;
+        if (mark[(size_t)c] == c && pinv[(size_t)c] < 0) piv = c;
+        else
+            for (int32_t r : lrow)
+                if (r >= T.lo && r < T.hi) { piv = r; break; }
+        if (piv < 0 && pl.symbolic_singular < 0) pl.symbolic_singular = c;
+        for (int32_t j : ustep) Usteps.push_back(j);
+        Usteps.push_back(c);
+        gbeg[(size_t)c] = (int64_t)g.size();
+        for (int32_t r : lrow)
+            if (r != piv) { Lrows.push_back(r); g.push_back(r); }
+        glen[(size_t)c] = gend[(size_t)c] = (int32_t)((int64_t)g.size() - gbeg[(size_t)c]);
+        Lst[(size_t)c + 1] = (int64_t)Lrows.size();
+        Ust[(size_t)c + 1] = (int64_t)Usteps.size();
+        if (piv >= 0) { pinv[(size_t)piv] = c; pl.sprow[(size_t)c] = piv; }
+        // symmetric pruning: a column j of the reach whose L holds the new pivot row
+        // keeps only its already pivoted rows for later reaches
+        if (piv >= 0)
+            for (int32_t j : ustep) {
+                if (pruned[(size_t)j]) continue;
+                int32_t *gj = g.data() + gbeg[(size_t)j];
+                int32_t len = glen[(size_t)j];
+                bool has = false;
+                for (int32_t k = 0; k < len; k++) if (gj[k] == piv) { has = true; break; }
+                if (!has) continue;
+                int32_t head = 0, tail = len;
+                while (head < tail) {
+                    if (pinv[(size_t)gj[head]] >= 0) head++;
+                    else std::swap(gj[head], gj[--tail]);
+                }
+                gend[(size_t)j] = tail;
+                pruned[(size_t)j] = 1;
+            }
+    }
+    pl.nnz_l_sym = (int64_t)Lrows.size();
+    pl.nnz_u_sym = (int64_t)Usteps.size();
+
+    // ---- static DAG levels (column c waits for the steps of U(:,c)) and claim order
+    pl.slevel.assign((size_t)n, 0);
+    int32_t nlev = 0;
+    for (int32_t c = 0; c < n; c++) {
+        int32_t lv = 0;
+        for (int64_t k = Ust[(size_t)c]; k < Ust[(size_t)c + 1] - 1; k++)
+            lv = std::max(lv, pl.slevel[(size_t)Usteps[(size_t)k]] + 1);
+        pl.slevel[(size_t)c] = lv;
+        nlev = std::max(nlev, lv + 1);
+    }
+    std::vector<int64_t> cnt((size_t)nlev + 1, 0);
+    for (int32_t c = 0; c < n; c++) cnt[(size_t)pl.slevel[(size_t)c] + 1]++;
+    for (int32_t l = 0; l < nlev; l++) cnt[(size_t)l + 1] += cnt[(size_t)l];
+    pl.sorder.assign((size_t)n, 0);
+    for (int32_t c = 0; c < n; c++) pl.sorder[(size_t)cnt[(size_t)pl.slevel[(size_t)c]]++] = c;
+
+    // ---- keep the symbolic pattern column by column (laid out by bk_plan_layout)
+    pl.sLcnt.assign((size_t)n, 0);
+    pl.sUcnt.assign((size_t)n, 0);
+    for (int32_t c = 0; c < n; c++) {
+        pl.sLcnt[(size_t)c] = (int32_t)(Lst[(size_t)c + 1] - Lst[(size_t)c]);
+        pl.sUcnt[(size_t)c] = (int32_t)(Ust[(size_t)c + 1] - Ust[(size_t)c]);
+    }
+    pl.sLi.swap(Lrows);
+    pl.sUi.swap(Usteps);
+    bk_plan_layout(pl, 1.0);
+    return BASKER_OK;
+}
+
+// Per-column L and U regions: count x (1 + slack) x grow + a margin.  Columns are
+// stored one after the other, so Lbeg[c] is a prefix sum of the capacities.
+void bk_plan_layout(bk_plan &pl, double grow)
+{
+    int32_t n = pl.n;
+    pl.sLbeg.assign((size_t)n + 1, 0);
+    pl.sUbeg.assign((size_t)n + 1, 0);
+    for (int32_t c = 0; c < n; c++) {
+        const bk_task &T = pl.tasks[(size_t)pl.col_task[(size_t)c]];
+        double f = (1.0 + pl.slack) * grow;
+        int64_t lc = (int64_t)(pl.sLcnt[(size_t)c] * f) + 8;
+        int64_t uc = (int64_t)(pl.sUcnt[(size_t)c] * f) + 8;
+        lc = std::min<int64_t>(lc, T.lspace);                 // L rows: unpivoted rows of the space
+        uc = std::min<int64_t>(uc, (int64_t)(c - T.sp_lo) + 1); // U rows: earlier steps + diagonal
+        lc = (lc + 3) & ~(int64_t)3;
+        uc = (uc + 3) & ~(int64_t)3;
+        pl.sLbeg[(size_t)c + 1] = pl.sLbeg[(size_t)c] + lc;
+        pl.sUbeg[(size_t)c + 1] = pl.sUbeg[(size_t)c] + uc;
+    }
+    pl.lcap = pl.sLbeg[(size_t)n];
+    pl.ucap = pl.sUbeg[(size_t)n];
+    // global workspace of the in-node tasks whose column state does not fit in
+    // shared memory, 256-byte aligned
+    int64_t off = 0;
+    for (auto &T : pl.tasks) {
+        if (bk_task_fits_smem(T)) { T.wsoff = -1; continue; }
+        T.wsoff = off;
+        off += ((int64_t)bk_task_smem_bytes(T) + 255) & ~(int64_t)255;
+    }
+    // separators: A-hat scratch (dense over the L-space per column) and the
+    // descendant-phase slice (x over the whole space plus two bitmaps)
+    int64_t ah = 0, ab = 0, slice = 0;
+    std::vector<int64_t> level_cols(pl.level_tasks.size(), 0);
+    for (auto &T : pl.tasks) {
+        T.ahoff = T.aboff = 0;
+        if (T.sp_lo >= T.lo) continue;
+        const int64_t own = T.hi - T.lo, words = (T.lspace + 31) / 32;
+        T.ahoff = ah;
+        T.aboff = ab;
+        ah += own * T.lspace;
+        ab += own * words;
+        int64_t sl = (int64_t)T.space * 8 + ((int64_t)(T.lo - T.sp_lo) + 31) / 32 * 4 + words * 4;
+        slice = std::max(slice, (sl + 255) & ~(int64_t)255);
+        level_cols[(size_t)T.level] += own;
+    }
+    pl.ahat_doubles = std::max<int64_t>(ah, 1);
+    pl.ahat_words = std::max<int64_t>(ab, 1);
+    pl.wsd_slice = std::max<int64_t>(slice, 256);
+    int64_t wmax = 1;
+    for (int64_t v : level_cols) wmax = std::max(wmax, v);
+    pl.wsd_warps = (int32_t)std::min<int64_t>(wmax, 152 * 16);
+    pl.ws_bytes = off;
+}
