@@ -35,7 +35,6 @@ struct basker_s {
     int32_t nrhs_cap = 0;
     double *d_vals = nullptr, *d_b = nullptr, *d_x = nullptr;
     int32_t stage_nrhs = 0;
-    double grow = 1.0;
     basker_info_t info{};
     int64_t device_bytes = 0;
     int32_t launches = 0;
@@ -200,6 +199,8 @@ int setup_device(basker_t h)
     TRY(dalloc(h, &d.Ucnt, (size_t)n, true));
     TRY(alloc_factors(h));
     TRY(dalloc(h, &d.status, 1, true));
+    TRY(dalloc(h, &d.col_over, (size_t)n, true));
+    TRY(dalloc(h, &d.task_stop, pl.tasks.size(), true));
     TRY(dalloc(h, &d.task_fail, pl.tasks.size()));
     TRY(dalloc(h, &d.ws, (size_t)std::max<int64_t>(pl.ws_bytes, 256), true));
     TRY(dalloc(h, &d.done, (size_t)n, true));
@@ -269,6 +270,7 @@ int setup_device(basker_t h)
 int reset_status(basker_t h, cudaStream_t s)
 {
     CU(cudaMemsetAsync(h->d.status, 0, sizeof(bk_status), s));
+    CU(cudaMemsetAsync(h->d.task_stop, 0, sizeof(int32_t) * std::max<size_t>(h->pl.tasks.size(), 1), s));
     CU(cudaMemsetAsync(&h->d.status->first_fail, 0xff, sizeof(unsigned long long), s));
     if (h->ws_dirty) {
         CU(cudaMemsetAsync(h->d.ws, 0, (size_t)std::max<int64_t>(h->pl.ws_bytes, 256), s));
@@ -302,10 +304,12 @@ int read_status(basker_t h, cudaStream_t s)
 
 int regrow(basker_t h)
 {
-    h->grow *= 2.0;
-    bk_plan_layout(h->pl, h->grow);
+    std::vector<int32_t> over((size_t)h->pl.n);
+    CU(cudaDeviceSynchronize());
+    CU(cudaMemcpy(over.data(), h->d.col_over, over.size() * 4, cudaMemcpyDeviceToHost));
+    CU(cudaMemset(h->d.col_over, 0, over.size() * 4));
+    bk_plan_regrow(h->pl, over.data());
     TRY(alloc_factors(h));
-    CU(cudaMemcpy(h->d.tasks, h->pl.tasks.data(), sizeof(bk_task) * h->pl.tasks.size(), cudaMemcpyHostToDevice));
     h->info.capacity_regrows++;
     h->ws_dirty = true;
     return BASKER_OK;
@@ -472,7 +476,7 @@ int factor_impl(basker_t h, const double *values, cudaStream_t s, bool refactor)
             h->schedule_valid = false;
             if (st == -1) {
                 // the new pivots need more room: grow and run Algorithm 1 everywhere
-                for (int tries = 0; st == -1 && tries < 6; tries++) {
+                for (int tries = 0; st == -1 && tries < 16; tries++) {
                     TRY(regrow(h));
                     TRY(reset_status(h, s));
                     TRY(launch_full_gp(h, s, 1));
@@ -485,7 +489,7 @@ int factor_impl(basker_t h, const double *values, cudaStream_t s, bool refactor)
         return BASKER_OK;
     }
     int st = -1;
-    for (int tries = 0; tries < 8; tries++) {
+    for (int tries = 0; tries < 16; tries++) {
         if (tries > 0) {
             TRY(regrow(h));
             TRY(reset_status(h, s));

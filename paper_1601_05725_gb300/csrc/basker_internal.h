@@ -71,6 +71,8 @@ struct bk_dev {
     int32_t *Li, *Ui;
     double *Lx, *Ux;
     bk_status *status;
+    int32_t *col_over;               // per column: 1 = its L region overflowed, 2 = its U region
+    int32_t *task_stop;              // per task: nonzero once it or a descendant ran out of room
     int32_t *task_fail;              // per task: first column that rejected its preferred pivot
     unsigned char *ws;               // global workspace (zero between uses)
     int32_t *done;                   // per column: epoch of its last completion (static kernel)
@@ -102,7 +104,7 @@ struct bk_plan {
     std::vector<int32_t> col_task;
     std::vector<std::vector<int32_t>> level_tasks;   // task ids per GP level
     // pattern under the preferred (natural) pivots, in the task-region layout
-    std::vector<int64_t> sLbeg, sUbeg;
+    std::vector<int64_t> sLbeg, sUbeg, lcapc, ucapc;  // region starts; per-column capacities
     std::vector<int32_t> sLcnt, sUcnt, sLi, sUi, sprow;
     std::vector<int32_t> slevel, sorder;              // static DAG levels and claim order
     int64_t lcap = 0, ucap = 0, nnz_l_sym = 0, nnz_u_sym = 0;
@@ -120,7 +122,8 @@ int bk_plan_build(int32_t n, const int32_t *colptr, const int32_t *rowind, const
                   const int32_t *Q, int32_t nblocks, const int32_t *block_ptr, int32_t nd_block,
                   int32_t nd_leaves, const int32_t *nd_node_ptr, double slack, bk_plan &plan,
                   int32_t *bad_col);
-void bk_plan_layout(bk_plan &plan, double grow);   // (re)assign L/U regions with capacities
+void bk_plan_layout(bk_plan &plan);                      // L/U regions, workspaces
+void bk_plan_regrow(bk_plan &plan, const int32_t *over); // after an overflow (per-column flags)
 size_t bk_task_smem_bytes(const bk_task &t);
 bool bk_task_fits_smem(const bk_task &t);
 

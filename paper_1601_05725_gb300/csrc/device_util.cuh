@@ -109,14 +109,26 @@ __device__ __forceinline__ void report_fail(bk_status *st, int c, int code)
     atomicMin(&st->first_fail, ((unsigned long long)(unsigned)c << 8) | (unsigned)code);
 }
 
-// Stop work on column c if an earlier (or the same) column already failed, or an
-// L/U region overflowed (the host regrows and starts over).
-__device__ __forceinline__ bool should_stop(const bk_status *st, int c)
+// Stop work on column c of task tid if an earlier (or the same) column already
+// failed, a wait gave up, or this task or one of its descendants ran out of L/U
+// room (the host regrows and starts over; independent tasks run on, so one
+// attempt finds the first overflow of every task).
+__device__ __forceinline__ bool should_stop(const bk_dev &d, int tid, int c)
 {
-    const unsigned long long f = *reinterpret_cast<const volatile unsigned long long *>(&st->first_fail);
-    const int cap = *reinterpret_cast<const volatile int *>(&st->capacity);
-    const int to = *reinterpret_cast<const volatile int *>(&st->timeout);
-    return cap != 0 || to != 0 || (long long)(f >> 8) <= (long long)c;
+    const unsigned long long f = *reinterpret_cast<const volatile unsigned long long *>(&d.status->first_fail);
+    const int to = *reinterpret_cast<const volatile int *>(&d.status->timeout);
+    const int ts = *reinterpret_cast<const volatile int *>(d.task_stop + tid);
+    return ts != 0 || to != 0 || (long long)(f >> 8) <= (long long)c;
+}
+
+// Column c of task T ran out of room (what: 1 = L, 2 = U): flag it for the
+// host, and stop the task and every ND ancestor (their input is incomplete).
+__device__ __forceinline__ void report_overflow(const bk_dev &d, const bk_task &T, int tid, int c, int what)
+{
+    atomicOr(d.col_over + c, what);
+    atomicExch(&d.status->capacity, 1);
+    atomicExch(d.task_stop + tid, 1);
+    for (int a = 0; a < T.nanc; a++) atomicExch(d.task_stop + d.col_task[T.anc_lo[a]], 1);
 }
 
 }  // namespace bk

@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(32) bk_gp_task_kernel(bk_dev d, const int32_t 
     const int c_begin = task_c0 ? task_c0[blockIdx.x] : T.lo;
 
     for (int c = c_begin; c < T.hi; ++c) {
-        if (__shfl_sync(BK_FULL, (int)should_stop(d.status, c), 0)) return;
+        if (__shfl_sync(BK_FULL, (int)should_stop(d, tid, c), 0)) return;
         const int64_t ub = d.Ubeg[c], ue = d.Ubeg[c + 1];
         const int64_t lb = d.Lbeg[c], le = d.Lbeg[c + 1];
         int nu = 0;
@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(32) bk_gp_task_kernel(bk_dev d, const int32_t 
             }
             if (!isfinite(m)) bad = true;
             if (ub + nu + 2 > ue) {
-                if (lane == 0) atomicExch(&d.status->capacity, 1);
+                if (lane == 0) report_overflow(d, T, tid, c, 2);
                 return;
             }
             if (lane == 0) {
@@ -256,7 +256,7 @@ __global__ void __launch_bounds__(32) bk_gp_task_kernel(bk_dev d, const int32_t 
             const int pre = warp_exscan(cnt, lane);
             const int tot = __shfl_sync(BK_FULL, pre + cnt, 31);
             if (lpos + tot > le) {
-                if (lane == 0) atomicExch(&d.status->capacity, 1);
+                if (lane == 0) report_overflow(d, T, tid, c, 1);
                 return;
             }
             int64_t q = lpos + pre;
@@ -305,8 +305,8 @@ __global__ void __launch_bounds__(128) bk_gp_desc_kernel(bk_dev d, const int32_t
         k = __shfl_sync(BK_FULL, k, 0);
         if (k >= ncols) break;
         const int c = cols[k];
-        if (__shfl_sync(BK_FULL, (int)should_stop(d.status, c), 0)) continue;
         const int tid = d.col_task[c];
+        if (__shfl_sync(BK_FULL, (int)should_stop(d, tid, c), 0)) continue;
         if (tid != cur_task) {
             load_task(T, d.tasks + tid, lane);
             cur_task = tid;
@@ -401,7 +401,7 @@ __global__ void __launch_bounds__(128) bk_gp_desc_kernel(bk_dev d, const int32_t
         }
         if (lane == 0) {
             d.dcnt[c] = nu;
-            if (overflow) atomicExch(&d.status->capacity, 1);
+            if (overflow) report_overflow(d, T, tid, c, 2);
             else if (bad) report_fail(d.status, c, BK_CODE_NAN);
         }
         __syncwarp();

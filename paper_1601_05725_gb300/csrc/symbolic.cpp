@@ -309,31 +309,61 @@ int bk_plan_build(int32_t n, const int32_t *colptr, const int32_t *rowind, const
     }
     pl.sLi.swap(Lrows);
     pl.sUi.swap(Usteps);
-    bk_plan_layout(pl, 1.0);
+    bk_plan_layout(pl);
     return BASKER_OK;
 }
 
-// Per-column L and U regions: count x (1 + slack) x grow + a margin.  Columns are
-// stored one after the other, so Lbeg[c] is a prefix sum of the capacities.
-void bk_plan_layout(bk_plan &pl, double grow)
+// Largest possible L and U counts of column c: the unpivoted rows of its node
+// other than the pivot plus its ancestors' rows; the earlier steps of its subtree
+// plus the diagonal.
+static int64_t l_bound(const bk_task &T, int32_t c) { return (int64_t)(T.hi - c - 1) + (T.lspace - (T.hi - T.lo)); }
+static int64_t u_bound(const bk_task &T, int32_t c) { return (int64_t)(c - T.sp_lo) + 1; }
+
+static void prefix_layout(bk_plan &pl)
 {
-    int32_t n = pl.n;
+    const int32_t n = pl.n;
     pl.sLbeg.assign((size_t)n + 1, 0);
     pl.sUbeg.assign((size_t)n + 1, 0);
     for (int32_t c = 0; c < n; c++) {
-        const bk_task &T = pl.tasks[(size_t)pl.col_task[(size_t)c]];
-        double f = (1.0 + pl.slack) * grow;
-        int64_t lc = (int64_t)(pl.sLcnt[(size_t)c] * f) + 8;
-        int64_t uc = (int64_t)(pl.sUcnt[(size_t)c] * f) + 8;
-        lc = std::min<int64_t>(lc, T.lspace);                 // L rows: unpivoted rows of the space
-        uc = std::min<int64_t>(uc, (int64_t)(c - T.sp_lo) + 1); // U rows: earlier steps + diagonal
-        lc = (lc + 3) & ~(int64_t)3;
-        uc = (uc + 3) & ~(int64_t)3;
-        pl.sLbeg[(size_t)c + 1] = pl.sLbeg[(size_t)c] + lc;
-        pl.sUbeg[(size_t)c + 1] = pl.sUbeg[(size_t)c] + uc;
+        pl.sLbeg[(size_t)c + 1] = pl.sLbeg[(size_t)c] + pl.lcapc[(size_t)c];
+        pl.sUbeg[(size_t)c + 1] = pl.sUbeg[(size_t)c] + pl.ucapc[(size_t)c];
     }
     pl.lcap = pl.sLbeg[(size_t)n];
     pl.ucap = pl.sUbeg[(size_t)n];
+}
+
+// After an overflow: a column that overflowed gets its exact upper bound, the
+// later columns of the same task twice their room (pivoting moved fill there).
+void bk_plan_regrow(bk_plan &pl, const int32_t *over)
+{
+    for (const bk_task &T : pl.tasks) {
+        bool al = false, au = false;
+        for (int32_t c = T.lo; c < T.hi; c++) {
+            const size_t k = (size_t)c;
+            if (over[k] & 1) { pl.lcapc[k] = l_bound(T, c); al = true; }
+            else if (al) pl.lcapc[k] = std::min<int64_t>(2 * pl.lcapc[k] + 8, l_bound(T, c));
+            if (over[k] & 2) { pl.ucapc[k] = u_bound(T, c); au = true; }
+            else if (au) pl.ucapc[k] = std::min<int64_t>(2 * pl.ucapc[k] + 8, u_bound(T, c));
+        }
+    }
+    prefix_layout(pl);
+}
+
+// Per-column L and U regions: count x (1 + slack) + a margin, at most the
+// column's upper bound.  Columns are stored one after the other, so Lbeg[c] is a
+// prefix sum of the capacities.
+void bk_plan_layout(bk_plan &pl)
+{
+    int32_t n = pl.n;
+    pl.lcapc.assign((size_t)n, 0);
+    pl.ucapc.assign((size_t)n, 0);
+    for (int32_t c = 0; c < n; c++) {
+        const bk_task &T = pl.tasks[(size_t)pl.col_task[(size_t)c]];
+        const double f = 1.0 + pl.slack;
+        pl.lcapc[(size_t)c] = std::min<int64_t>((int64_t)(pl.sLcnt[(size_t)c] * f) + 8, l_bound(T, c));
+        pl.ucapc[(size_t)c] = std::min<int64_t>((int64_t)(pl.sUcnt[(size_t)c] * f) + 8, u_bound(T, c));
+    }
+    prefix_layout(pl);
     // global workspace of the in-node tasks whose column state does not fit in
     // shared memory, 256-byte aligned
     int64_t off = 0;
