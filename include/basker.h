@@ -10,7 +10,7 @@
  * with the left-looking Gilbert-Peierls method (Algorithm 1) with threshold
  * partial pivoting confined to the block, or to the ND node (the diagonal blocks
  * A_ii / A_jj of Fig. 3a).  Refactorization reuses the pattern for a sequence of
- * matrices (Sec. V-F, the circuit-simulation sequence), and the solve is the BTF
+ * matrices (Sec. V, the circuit-simulation sequence), and the solve is the BTF
  * back-substitution with the off-diagonal blocks kept as values of A (Sec. III-B).
  *
  * Conventions for every entry point:
@@ -117,7 +117,7 @@ int basker_symbolic(int32_t n, const int32_t *colptr, const int32_t *rowind,
  * status.  Errors: SINGULAR, NAN (column in basker_info), TIMEOUT, CUDA, OOM. */
 int basker_factor(basker_t h, const double *values_dev, void *stream);
 
-/* Refactorization of a new matrix with the same pattern (Sec. V-F): each column
+/* Refactorization of a new matrix with the same pattern (Sec. V): each column
  * prefers the pivot row of the previous factorization; columns that keep it are
  * computed on the stored pattern (column-level dataflow), and a node whose
  * column rejects its preferred pivot is recomputed from that column on with the

@@ -9,8 +9,8 @@
  * What it computes (Booth, Rajamanickam, Thornquist, "Basker", arXiv 1601.05725):
  *
  *   B = A(P,Q) is block upper triangular (Sec. II, the BTF display; Sec. III-A).
- *   Only the diagonal blocks B_dd are factored (Sec. II: "only submatrices on the
- *   diagonal need to be factored").  Each is factored column by column with the
+ *   Only the diagonal blocks B_dd are factored (Sec. II: the off-diagonal blocks
+ *   enter only the solve).  Each is factored column by column with the
  *   left-looking Gilbert-Peierls method (Algorithm 1):
  *     1. pattern of column c = the set of rows reachable, in the graph of the L
  *        computed so far, from the rows of B_dd(:,c); found by depth-first search;
@@ -22,12 +22,12 @@
  *   In the block that carries nested dissection (Sec. III-C), a pivot for a column
  *   of ND node t may only come from node t's own rows: the leaves of the ND tree
  *   and the separators are the diagonal blocks A_ii / A_jj of the 2D layout
- *   (Fig. 3a, Algorithm 4 factors each LU_ii and LU_jj "with pivoting" inside the
- *   block).  Algorithm 4 computes exactly these factors in a parallel schedule;
+ *   (Fig. 3a; Algorithm 4 pivots inside each leaf block LU_ii and separator block
+ *   LU_jj).  Algorithm 4 computes exactly these factors in a parallel schedule;
  *   this file computes them by the plain definition, one column after the other.
  *
  * Readings of points the paper leaves open (each is a documented choice):
- *   - Pivot rule (Algorithm 1 only says "select pivot"): threshold partial
+ *   - Pivot rule (Algorithm 1 leaves the rule open): threshold partial
  *     pivoting.  m = max |x_r| over the candidates; the preferred row (the row
  *     pivoted at this column by a previous factorization, else the natural row c)
  *     is kept when it is a candidate and |x_pref| >= tau * m; otherwise the
@@ -324,7 +324,7 @@ int oracle_factor(oracle_lu *h, const double *Ax, double tau, const int *pref, i
                 lo = h->nd_ptr[t];
                 hi = h->nd_ptr[t + 1];
             }
-            /* 1. reach by depth-first search in the graph of L (Algorithm 1, line 3):
+            /* 1. reach by depth-first search in the graph of L (Algorithm 1's first step):
              *    a row pivoted at step s has an edge to every row of L(:,s) */
             int np = 0, nt = 0;
             for (int64_t p = h->Bp[c]; p < h->Bp[c + 1]; p++) {
@@ -368,7 +368,7 @@ int oracle_factor(oracle_lu *h, const double *Ax, double tau, const int *pref, i
             } else {
                 for (int a = 0, b = nu - 1; a < b; a++, b--) { int t = topo[a]; topo[a] = topo[b]; topo[b] = t; }
             }
-            /* 3. x = B_dd(:,c), then the sparse triangular solve (Algorithm 1, lines 4-6) */
+            /* 3. x = B_dd(:,c), then the sparse triangular solve (Algorithm 1's update loop) */
             for (int64_t p = h->Bp[c]; p < h->Bp[c + 1]; p++)
                 if (h->Bi[p] >= k0) x[h->Bi[p]] = h->Bx[p];
             for (int k = 0; k < nu; k++) {
@@ -378,7 +378,7 @@ int oracle_factor(oracle_lu *h, const double *Ax, double tau, const int *pref, i
                 for (int64_t p = h->Lp[s]; p < h->Lp[s + 1]; p++)
                     x[h->Li[p]] = fma(-h->Lx[p], m, x[h->Li[p]]);
             }
-            /* 4. pivot (Algorithm 1, line 7) among unpivoted pattern rows of [lo, hi) */
+            /* 4. pivot (Algorithm 1's pivot selection) among unpivoted pattern rows of [lo, hi) */
             double amax = 0.0;
             int ncand = 0, bad = 0;
             for (int k = 0; k < np; k++) {
@@ -413,7 +413,7 @@ int oracle_factor(oracle_lu *h, const double *Ax, double tau, const int *pref, i
                 for (int k = 0; k < np; k++) x[pattern[k]] = 0.0;
                 break;
             }
-            /* 5. copy x into U(:,c) and L(:,c) (Algorithm 1, line 8) */
+            /* 5. copy x into U(:,c) and L(:,c) (Algorithm 1's final copy) */
             int64_t lnz = h->Lp[c], unz = h->Up[c];
             if (!grow((void **)&h->Ui, (void **)&h->Ux, &h->ucap, unz + nu + 1, sizeof(int), sizeof(double)) ||
                 !grow((void **)&h->Li, (void **)&h->Lx, &h->lcap, lnz + np, sizeof(int), sizeof(double))) {

@@ -3,13 +3,13 @@
 //   bk_gather_kernel   values of A -> B's entries (the fixed permutation P, Q).
 //   bk_gp_task_kernel  Algorithm 1, one warp per task (a small BTF block, an ND
 //                      leaf, or the in-node phase of an ND separator), columns in
-//                      order.  Per column: the reach of Algorithm 1 line 3 and the
-//                      updates of lines 4-6 are one sweep over a bitmap of pivot
+//                      order.  Per column: Algorithm 1's reach and its update loop
+//                      are one sweep over a bitmap of pivot
 //                      steps, lowest step first (an ascending step order is a
 //                      topological order of the reach); then threshold pivoting
-//                      among the node's own unpivoted rows (line 7, warp max /
-//                      warp min by shuffle) and the split into L and U (line 8).
-//   bk_gp_desc_kernel  Algorithm 4 lines 14-24 for ND separators: one warp per
+//                      among the node's own unpivoted rows (warp max / warp min
+//                      by shuffle) and the split of x into L and U.
+//   bk_gp_desc_kernel  Algorithm 4's upper off-diagonal solves and reductions for ND separators: one warp per
 //                      separator column solves that column against every
 //                      descendant's L (the U_ij blocks) and applies the products
 //                      to the separator's and ancestors' rows (the reductions into
@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(32) bk_gp_task_kernel(bk_dev d, const int32_t 
         int nu = 0;
         bool bad = false;
         if (sep) {
-            // A-hat(:,c) = the column after all descendant steps (Algorithm 4 lines 14-24)
+            // A-hat(:,c) = the column after all descendant steps (Algorithm 4's solves with L_ii and reductions)
             nu = d.dcnt[c];
             const double *ah = d.ahat + T.ahoff + (int64_t)(c - T.lo) * lsp;
             const uint32_t *ab = d.abits + T.aboff + (int64_t)(c - T.lo) * nrw;
@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(32) bk_gp_task_kernel(bk_dev d, const int32_t 
         }
         __syncwarp();
 
-        // Algorithm 1 lines 3-6: own pivot steps, lowest first (each at most once)
+        // Algorithm 1's reach and updates: own pivot steps, lowest first (each at most once)
         int w0 = 0;
         for (int iter = 0;; iter++) {
             const int jb = next_step_bit(sb, nsw, w0, lane);
@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(32) bk_gp_task_kernel(bk_dev d, const int32_t 
             __syncwarp();
         }
 
-        // line 7: threshold pivot among the unpivoted own rows of the pattern
+        // Algorithm 1's pivot selection: threshold pivot among the unpivoted own rows
         double amax = 0.0;
         int ncand = 0;
         for (int w = lane; w < nrw; w += 32) {
@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(32) bk_gp_task_kernel(bk_dev d, const int32_t 
             return;
         }
 
-        // line 8: U(:,c) got the steps above; the pivot closes it; L(:,c) = x / pivot
+        // Algorithm 1's copy to L and U: U(:,c) got the steps above, the pivot closes it, L(:,c) = x / pivot
         const double xp = x[piv - base];
         if (lane == 0) {
             d.Ui[ub + nu] = c;

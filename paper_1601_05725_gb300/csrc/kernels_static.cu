@@ -1,12 +1,12 @@
 // kernels_static.cu -- refactorization on a known pattern (the matrix-sequence
-// case of Sec. V-F: same pattern, new values, previous pivots preferred).
+// case of Sec. V: same pattern, new values, previous pivots preferred).
 //
 //   bk_static_kernel   persistent; each warp claims columns in a topological order
 //                      of the column DAG (column c waits for every step of
 //                      U(:,c)) and recomputes the column on the stored pattern:
 //                      x = B(:,c); for each step j of U(:,c), lowest first:
 //                      x -= L(:,j) x(prow j); then L(:,c) = x / pivot.  The
-//                      preferred pivot is validated as Algorithm 1 line 7 would
+//                      preferred pivot is validated as Algorithm 1's pivot selection would
 //                      decide it (|x_pref| >= tau * max over the node's candidate
 //                      rows); a column that would pick another row is reported for
 //                      the reach-based path.  Waits are point-to-point flags (the
