@@ -141,6 +141,33 @@ int basker_solve(basker_t h, int32_t nrhs, const double *b_dev, int32_t ldb,
 int basker_refactor_solve_host(basker_t h, const double *values_host, int32_t nrhs,
                                const double *b_host, double *x_host, void *stream);
 
+/* Size, in doubles, of the fixed device array basker_solve_noalloc works in
+ * (8 MiB on every GPU that loads the library, held until the process exits). */
+#define BASKER_NOALLOC_SCRATCH_DOUBLES (1 << 20)
+
+/* basker_solve for callers that must not allocate device memory.  The paper has
+ * no counterpart; this entry point exists for users of the library, such as a
+ * simulator's time-step loop whose device memory is all reserved up front by
+ * its own pool or caching allocator (a cudaMalloc there can fail while the pool
+ * holds the memory, and cudaFree synchronises the whole device), which still
+ * need to solve with factors made earlier.
+ *   Same arguments and results as basker_solve; the handle must be factored.
+ *   The work vectors and ND buffers of the solve live in one array of
+ *   BASKER_NOALLOC_SCRATCH_DOUBLES doubles compiled into the library, so the call
+ *   performs no cudaMalloc, cudaFree or other allocation.  It needs
+ *   nrhs * (n + the ND buffer length) doubles; larger requests return
+ *   BASKER_ERR_INVALID_ARG without launching anything.
+ *   The first call on a device looks up the array's device address (with that
+ *   device current) and caches it; make that first call before any stream
+ *   capture begins.
+ *   All calls, from every handle, share the one array and the solve leaves its
+ *   contents behind; everything the solve reads it writes first in the same
+ *   call.  Calls whose work overlaps on the GPU (different streams, or
+ *   concurrent host threads) race on the array: serialise them.
+ *   Errors: INVALID_ARG, NOT_FACTORED, CUDA. */
+int basker_solve_noalloc(basker_t h, int32_t nrhs, const double *b_dev, int32_t ldb,
+                         double *x_dev, int32_t ldx, void *stream);
+
 /* Counters of the handle (sizes, flops, failing column, repivots). */
 int basker_info(basker_t h, basker_info_t *out);
 

@@ -57,7 +57,7 @@ KERNEL_KINDS = ["gather", "static_refactor", "dag_levels", "gp_in_node", "gp_des
 
 EXPORTED = ["basker_default_options", "basker_symbolic", "basker_factor", "basker_refactor",
             "basker_solve", "basker_refactor_solve_host", "basker_info", "basker_export",
-            "basker_free", "basker_strerror"]
+            "basker_free", "basker_strerror", "basker_solve_noalloc"]
 
 
 def library_path() -> str:
@@ -85,6 +85,8 @@ def load(path: Optional[str] = None):
             getattr(L, f).restype = ctypes.c_int
         L.basker_solve.argtypes = [vp, i32, vp, i32, vp, i32, vp]
         L.basker_solve.restype = ctypes.c_int
+        L.basker_solve_noalloc.argtypes = [vp, i32, vp, i32, vp, i32, vp]
+        L.basker_solve_noalloc.restype = ctypes.c_int
         L.basker_refactor_solve_host.argtypes = [vp, vp, i32, vp, vp, vp]
         L.basker_refactor_solve_host.restype = ctypes.c_int
         L.basker_info.argtypes = [vp, ctypes.POINTER(Info)]
@@ -185,6 +187,25 @@ class Handle:
             x.copy_(out)
             return x
         return out
+
+    def solve_noalloc(self, b, x):
+        """basker_solve_noalloc: like solve(), for callers that cannot allocate
+        device memory; b and x are CUDA float64 (n,) or column-major (n, nrhs)
+        buffers the caller owns (x is written in place)."""
+        nrhs = 1 if b.dim() == 1 else b.shape[1]
+
+        def lead(t):
+            if t.dim() == 1 or t.shape[1] == 1:
+                if t.dim() == 2 and t.stride(0) != 1:
+                    raise ValueError("b and x must be column-major (n, nrhs) views")
+                return self.n
+            if not (t.stride(0) == 1 and t.stride(1) >= self.n):
+                raise ValueError("b and x must be column-major (n, nrhs) views")
+            return t.stride(1)
+        ldb, ldx = lead(b), lead(x)
+        s = self.lib.basker_solve_noalloc(self.h, nrhs, _dev_ptr(b), ldb, _dev_ptr(x), ldx, _stream_ptr(None))
+        self._check(s, "basker_solve_noalloc")
+        return x
 
     def refactor_solve_host(self, values: np.ndarray, b: np.ndarray, stream=None) -> np.ndarray:
         """Host arrays in, host solution out (copies inside the call)."""

@@ -524,6 +524,35 @@ int ensure_solve_buffers(basker_t h, int32_t nrhs)
 
 }  // namespace
 
+// Helpers of the allocation-free solve (noalloc.cu).  They launch the same solve
+// kernel as basker_solve on scratch memory the caller provides and allocate
+// nothing themselves.
+int bk_handle_device(basker_t h) { return h ? h->device : -1; }
+
+int32_t bk_handle_n(basker_t h) { return h->pl.n; }
+
+int64_t bk_solve_scratch_doubles(basker_t h, int32_t nrhs)
+{
+    return (int64_t)nrhs * ((int64_t)h->pl.n + h->sd.acc_stride);
+}
+
+int bk_solve_on_scratch(basker_t h, int32_t nrhs, const double *b_dev, int32_t ldb, double *x_dev, int32_t ldx,
+                        double *scratch, void *stream)
+{
+    if (!h->factored) return BASKER_ERR_NOT_FACTORED;
+    if (nrhs == 0 || h->pl.n == 0) return BASKER_OK;
+    bk_solve_dev sd = h->sd;
+    sd.w = scratch;
+    sd.acc = scratch + (size_t)nrhs * (size_t)h->pl.n;
+    cudaStream_t s = (cudaStream_t)stream;
+    CU(cudaMemsetAsync(h->d.counter + 2, 0, sizeof(int32_t), s));
+    h->solve_epoch++;
+    h->info.kernel_launches++;
+    bk_launch_solve(h->d, sd, nrhs, b_dev, ldb, x_dev, ldx, h->solve_epoch, h->opt.wait_budget_cycles, s);
+    CU(cudaGetLastError());
+    return BASKER_OK;
+}
+
 extern "C" {
 
 void basker_default_options(basker_options *opt)
