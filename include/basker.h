@@ -84,8 +84,13 @@ typedef struct {
                                      the last basker_info call: [0] value gather,
                                      [1] stored-pattern refactor, [2] DAG levels,
                                      [3] in-node Algorithm 1, [4] separator descendant
-                                     phase, [5] solve, [6] pivot reset, [7] unused */
-    int32_t reserved[8];
+                                     phase, [5] solve, [6] pivot reset,
+                                     [7] speculative separator refactor */
+    int32_t internal_site;        /* nonzero: code of the internal consistency check that
+                                     failed (reported as INVALID_ARG), for diagnosis */
+    int32_t internal_col;         /* column of that check */
+    int32_t last_rounds;          /* redo rounds of the last refactor (0: no pivot rejected) */
+    int32_t reserved[5];
 } basker_info_t;
 
 /* Defaults listed in basker_options. */

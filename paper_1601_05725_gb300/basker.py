@@ -49,10 +49,11 @@ class Info(ctypes.Structure):
                 ("capacity_regrows", ctypes.c_int32), ("device_bytes", ctypes.c_int64),
                 ("gp_launches", ctypes.c_int32), ("static_launches", ctypes.c_int32),
                 ("kernel_launches", ctypes.c_int64), ("kernel_ms", ctypes.c_double * 8),
-                ("reserved", ctypes.c_int32 * 8)]
+                ("internal_site", ctypes.c_int32), ("internal_col", ctypes.c_int32),
+                ("last_rounds", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 KERNEL_KINDS = ["gather", "static_refactor", "dag_levels", "gp_in_node", "gp_descendant", "solve",
-                "pivot_reset", "unused"]
+                "pivot_reset", "spec_separator"]
 
 
 EXPORTED = ["basker_default_options", "basker_symbolic", "basker_factor", "basker_refactor",
@@ -161,8 +162,12 @@ class Handle:
 
     def _check(self, s: int, where: str):
         if s != 0:
-            col = self.info()["failed_column"] if s in (4, 5) else -1
-            raise BaskerError(s, where, col)
+            inf = self.info()
+            col = inf["failed_column"] if s in (4, 5) else -1
+            err = BaskerError(s, where, col)
+            if inf["internal_site"]:
+                err.args = (err.args[0] + f" [internal check {inf['internal_site']} at column {inf['internal_col']}]",)
+            raise err
 
     def factor(self, values, stream=None) -> None:
         """values: CUDA float64 tensor of nnz(A) entries in A's CSC order."""

@@ -30,7 +30,7 @@ struct basker_s {
     int32_t *h_stage = nullptr;      // pinned, 3n + ntasks + 16 ints
     bk_status *h_status = nullptr;   // pinned
     int32_t *h_task_fail = nullptr;  // pinned
-    int32_t epoch = 0, solve_epoch = 0;
+    int32_t epoch = 0, solve_epoch = 0, refno = 0;
     bool factored = false, ws_dirty = false, schedule_valid = true, order_is_symbolic = true;
     int32_t nrhs_cap = 0;
     double *d_vals = nullptr, *d_b = nullptr, *d_x = nullptr;
@@ -48,7 +48,7 @@ struct basker_s {
 
 namespace {
 
-enum { KT_GATHER = 0, KT_STATIC = 1, KT_LEVELS = 2, KT_GP = 3, KT_DESC = 4, KT_SOLVE = 5, KT_RESET = 6 };
+enum { KT_GATHER = 0, KT_STATIC = 1, KT_LEVELS = 2, KT_GP = 3, KT_DESC = 4, KT_SOLVE = 5, KT_RESET = 6, KT_SPEC = 7 };
 
 cudaEvent_t take_event(basker_t h)
 {
@@ -139,20 +139,28 @@ int upload(basker_t h, T **p, const std::vector<T> &v)
         }                                      \
     } while (0)
 
-// L/U arrays sized by the current layout (symbolic pattern, slack, growth)
+// L/U arrays sized by the current layout (symbolic pattern, slack, growth), each
+// followed by its spill pool; per-column region starts and ends.
 int alloc_factors(basker_t h)
 {
     bk_plan &pl = h->pl;
     dfree(h, h->d.Li); dfree(h, (void *)h->d.Lx); dfree(h, h->d.Ui); dfree(h, (void *)h->d.Ux);
-    dfree(h, h->d.Lbeg); dfree(h, h->d.Ubeg);
+    dfree(h, h->d.Lbeg); dfree(h, h->d.Ubeg); dfree(h, h->d.Lend); dfree(h, h->d.Uend);
     h->d.Li = h->d.Ui = nullptr;
     h->d.Lx = h->d.Ux = nullptr;
-    TRY(dalloc(h, &h->d.Li, (size_t)pl.lcap));
-    TRY(dalloc(h, &h->d.Lx, (size_t)pl.lcap));
-    TRY(dalloc(h, &h->d.Ui, (size_t)pl.ucap));
-    TRY(dalloc(h, &h->d.Ux, (size_t)pl.ucap));
+    h->d.lpool_end = pl.lcap + pl.lpool;
+    h->d.upool_end = pl.ucap + pl.upool;
+    TRY(dalloc(h, &h->d.Li, (size_t)h->d.lpool_end));
+    TRY(dalloc(h, &h->d.Lx, (size_t)h->d.lpool_end));
+    TRY(dalloc(h, &h->d.Ui, (size_t)h->d.upool_end));
+    TRY(dalloc(h, &h->d.Ux, (size_t)h->d.upool_end));
     TRY(upload(h, &h->d.Lbeg, pl.sLbeg));
     TRY(upload(h, &h->d.Ubeg, pl.sUbeg));
+    std::vector<int64_t> le(pl.sLbeg.begin() + 1, pl.sLbeg.end()), ue(pl.sUbeg.begin() + 1, pl.sUbeg.end());
+    TRY(upload(h, &h->d.Lend, le));
+    TRY(upload(h, &h->d.Uend, ue));
+    unsigned long long next[2] = {(unsigned long long)pl.lcap, (unsigned long long)pl.ucap};
+    CU(cudaMemcpy(h->d.pool, next, sizeof next, cudaMemcpyHostToDevice));
     return BASKER_OK;
 }
 
@@ -197,11 +205,21 @@ int setup_device(basker_t h)
     TRY(dalloc(h, (int32_t **)&d.pref, (size_t)n));
     TRY(dalloc(h, &d.Lcnt, (size_t)n, true));
     TRY(dalloc(h, &d.Ucnt, (size_t)n, true));
+    TRY(dalloc(h, &d.pool, 2, true));
     TRY(alloc_factors(h));
     TRY(dalloc(h, &d.status, 1, true));
     TRY(dalloc(h, &d.col_over, (size_t)n, true));
     TRY(dalloc(h, &d.task_stop, pl.tasks.size(), true));
     TRY(dalloc(h, &d.task_fail, pl.tasks.size()));
+    TRY(dalloc(h, &d.col_fail, (size_t)n, true));
+    TRY(dalloc(h, &d.dd_start, pl.tasks.size(), true));
+    TRY(dalloc(h, &d.dd_flags, pl.tasks.size(), true));
+    TRY(dalloc(h, &d.touch, (size_t)n, true));
+    TRY(dalloc(h, &d.dirty_ep, (size_t)n, true));
+    TRY(dalloc(h, &d.pchg_ep, (size_t)n, true));
+    TRY(dalloc(h, &d.touch_ref, (size_t)n, true));
+    TRY(dalloc(h, &d.dirty_ref, (size_t)n, true));
+    TRY(dalloc(h, &d.pchg_ref, (size_t)n, true));
     TRY(dalloc(h, &d.ws, (size_t)std::max<int64_t>(pl.ws_bytes, 256), true));
     TRY(dalloc(h, &d.done, (size_t)n, true));
     TRY(dalloc(h, &d.order, (size_t)n));
@@ -291,11 +309,18 @@ int read_status(basker_t h, cudaStream_t s)
     const bk_status &st = *h->h_status;
     h->info.failed_column = -1;
     if (st.timeout) { h->ws_dirty = true; return BASKER_ERR_TIMEOUT; }
+    // an overflow stops its task midway, which later kernels may see as an
+    // inconsistency: the regrow and full recomputation come first
+    if (st.capacity) { h->ws_dirty = true; return -1; }
     if (st.first_fail != ~0ull) {
         h->ws_dirty = true;
         h->info.failed_column = (int32_t)(st.first_fail >> 8);
         const unsigned code = (unsigned)(st.first_fail & 0xff);
-        if (code == BK_CODE_INTERNAL) return BASKER_ERR_INVALID_ARG;
+        if (code == BK_CODE_INTERNAL) {
+            h->info.internal_site = st.internal_site;
+            h->info.internal_col = st.internal_col;
+            return BASKER_ERR_INVALID_ARG;
+        }
         return code == BK_CODE_NAN ? BASKER_ERR_NAN : BASKER_ERR_SINGULAR;
     }
     if (st.capacity) { h->ws_dirty = true; return -1; }
@@ -339,64 +364,86 @@ int launch_full_gp(basker_t h, cudaStream_t s, int pref_mode)
     return BASKER_OK;
 }
 
-// Redo the tasks with start[t] < hi from that column (refactor after a rejected
-// preferred pivot), with the previous pivots preferred.
-int launch_redo(basker_t h, cudaStream_t s, const std::vector<int32_t> &start)
+// Upload a list of ints through the pinned staging buffer (at offset off ints).
+int stage_upload(basker_t h, cudaStream_t s, int32_t *dst, const std::vector<int32_t> &v, size_t off)
+{
+    if (v.empty()) return BASKER_OK;
+    std::memcpy(h->h_stage + off, v.data(), v.size() * 4);
+    CU(cudaMemcpyAsync(dst, h->h_stage + off, v.size() * 4, cudaMemcpyHostToDevice, s));
+    return BASKER_OK;
+}
+
+// After a stored-pattern pass that rejected some preferred pivots (first
+// rejection per task in h_task_fail): level by level up the ND tree, rounds of the
+// dirty-dataflow kernel.  A task with a rejected column f starts a round at f
+// (resolve); a separator whose descendants changed starts at its first column
+// (force); after a round, each task that rejected a speculated pivot at f' runs
+// another round from f'.
+int launch_redo(basker_t h, cudaStream_t s)
 {
     bk_plan &pl = h->pl;
     const double tau = h->opt.tau;
-    std::vector<int32_t> ids, c0;
-    for (size_t t = 0; t < pl.tasks.size(); t++)
-        if (start[t] < pl.tasks[t].hi) { ids.push_back((int32_t)t); c0.push_back(start[t]); }
-    if (ids.empty()) return BASKER_OK;
-    const size_t nt = ids.size();
-    std::memcpy(h->h_stage, ids.data(), nt * 4);
-    std::memcpy(h->h_stage + nt, c0.data(), nt * 4);
-    CU(cudaMemcpyAsync(h->rd_tasks, h->h_stage, nt * 4, cudaMemcpyHostToDevice, s));
-    CU(cudaMemcpyAsync(h->rd_c0, h->h_stage + nt, nt * 4, cudaMemcpyHostToDevice, s));
-    tbeg(h, KT_RESET, s, 1);
-    bk_launch_reset_pivots(h->d, h->rd_tasks, h->rd_c0, (int32_t)nt, s);
-    tend(h, s);
-    h->launches++;
-    // group by level: tasks are ordered by level within the lists below
+    const size_t nt = pl.tasks.size();
+    std::vector<int32_t> fail(h->h_task_fail, h->h_task_fail + nt);
+    std::vector<char> desc_changed(nt, 0);
+    std::vector<int32_t> start(nt, 0), flags(nt, 0);
     int32_t redone = 0;
-    std::vector<int32_t> cols;
+    h->info.last_rounds = 0;
+    auto mark_ancestors = [&](size_t t) {
+        const bk_task &T = pl.tasks[t];
+        for (int32_t a = 0; a < T.nanc; a++) desc_changed[(size_t)pl.col_task[(size_t)T.anc_lo[a]]] = 1;
+    };
     for (size_t l = 0; l < pl.level_tasks.size(); l++) {
-        std::vector<int32_t> lid, lc0;
-        cols.clear();
-        size_t sm = 0;
-        for (size_t k = 0; k < nt; k++) {
-            const bk_task &T = pl.tasks[(size_t)ids[k]];
-            if ((size_t)T.level != l) continue;
-            lid.push_back(ids[k]);
-            lc0.push_back(c0[k]);
-            redone += T.hi - c0[k];
-            if (T.wsoff < 0) sm = std::max(sm, bk_task_smem_bytes(T));
-            if (T.sp_lo < T.lo)
-                for (int32_t c = c0[k]; c < T.hi; c++) cols.push_back(c);
+        std::vector<int32_t> active;
+        for (int32_t t : pl.level_tasks[l]) {
+            const bk_task &T = pl.tasks[(size_t)t];
+            if (desc_changed[(size_t)t]) {
+                active.push_back(t);
+                start[(size_t)t] = T.lo;
+                flags[(size_t)t] = BK_DD_DESC;
+            } else if (fail[(size_t)t] >= T.lo && fail[(size_t)t] < T.hi) {
+                active.push_back(t);
+                start[(size_t)t] = fail[(size_t)t];
+                flags[(size_t)t] = BK_DD_RESOLVE;
+            }
         }
-        if (lid.empty()) continue;
-        // stage: [tasks | c0 | cols] after the first 2*nt ints of the staging buffer
-        int32_t *st = h->h_stage + 2 * nt;
-        const size_t m = lid.size();
-        CU(cudaStreamSynchronize(s));     // the staging buffer is reused per level
-        std::memcpy(st, lid.data(), m * 4);
-        std::memcpy(st + m, lc0.data(), m * 4);
-        CU(cudaMemcpyAsync(h->rd_tasks, st, m * 4, cudaMemcpyHostToDevice, s));
-        CU(cudaMemcpyAsync(h->rd_c0, st + m, m * 4, cudaMemcpyHostToDevice, s));
-        if (!cols.empty()) {
-            CU(cudaMemcpyAsync(h->rd_cols, cols.data(), cols.size() * 4, cudaMemcpyHostToDevice, s));
+        for (int32_t t : active) mark_ancestors((size_t)t);
+        for (int round = 0; !active.empty(); round++) {
+            if (round > 4 * (int)pl.n + 8) return BASKER_ERR_INVALID_ARG;   // cannot happen: each round resolves a column
+            std::vector<int32_t> cols;
+            for (int32_t t : active)
+                for (int32_t c = start[(size_t)t]; c < pl.tasks[(size_t)t].hi; c++) cols.push_back(c);
+            CU(cudaStreamSynchronize(s));       // the staging buffer is reused
+            std::memcpy(h->h_stage, start.data(), nt * 4);
+            std::memcpy(h->h_stage + nt, flags.data(), nt * 4);
+            CU(cudaMemcpyAsync(h->d.dd_start, h->h_stage, nt * 4, cudaMemcpyHostToDevice, s));
+            CU(cudaMemcpyAsync(h->d.dd_flags, h->h_stage + nt, nt * 4, cudaMemcpyHostToDevice, s));
+            TRY(stage_upload(h, s, h->rd_cols, cols, 2 * nt));
+            CU(cudaMemsetAsync(h->d.task_fail, 0x7f, sizeof(int32_t) * nt, s));
             CU(cudaMemsetAsync(h->d.counter + 3, 0, sizeof(int32_t), s));
-            tbeg(h, KT_DESC, s, 1);
-            bk_launch_gp_desc(h->d, h->rd_cols, (int32_t)cols.size(), h->d.counter + 3, s);
+            h->epoch++;
+            tbeg(h, KT_SPEC, s, 1);
+            bk_launch_dd(h->d, h->rd_cols, (int32_t)cols.size(), h->d.counter + 3, tau, h->epoch,
+                         h->opt.wait_budget_cycles, h->refno, s);
             tend(h, s);
             h->launches++;
-            CU(cudaStreamSynchronize(s));  // cols is pageable host memory
+            h->info.last_rounds++;
+            redone += (int32_t)cols.size();
+            CU(cudaMemcpyAsync(h->h_task_fail, h->d.task_fail, sizeof(int32_t) * nt, cudaMemcpyDeviceToHost, s));
+            const int st = read_status(h, s);
+            if (st != BASKER_OK) return st;
+            std::vector<int32_t> next;
+            for (int32_t t : active) {
+                const bk_task &T = pl.tasks[(size_t)t];
+                const int32_t f = h->h_task_fail[(size_t)t];
+                if (f >= T.lo && f < T.hi) {
+                    next.push_back(t);
+                    start[(size_t)t] = f;
+                    flags[(size_t)t] = BK_DD_RESOLVE;
+                }
+            }
+            active.swap(next);
         }
-        tbeg(h, KT_GP, s, 1);
-        bk_launch_gp_tasks(h->d, h->rd_tasks, h->rd_c0, (int32_t)m, (sm + 15) & ~(size_t)15, tau, 1, s);
-        tend(h, s);
-        h->launches++;
     }
     h->info.last_repivot_columns = redone;
     CU(cudaGetLastError());
@@ -429,27 +476,6 @@ int static_pass(basker_t h, cudaStream_t s)
     return BASKER_OK;
 }
 
-// After a static pass: which tasks must be redone, and from which column.
-void redo_set(basker_t h, std::vector<int32_t> &start)
-{
-    bk_plan &pl = h->pl;
-    const size_t nt = pl.tasks.size();
-    start.assign(nt, INT_MAX);
-    for (size_t t = 0; t < nt; t++) {
-        const int32_t f = h->h_task_fail[t];
-        if (f >= pl.tasks[t].lo && f < pl.tasks[t].hi) start[t] = f;
-    }
-    // every ancestor of a redone ND node is redone from its first column
-    for (size_t t = 0; t < nt; t++) {
-        if (start[t] == INT_MAX || pl.tasks[t].node < 0) continue;
-        const bk_task &T = pl.tasks[t];
-        for (int32_t a = 0; a < T.nanc; a++) {
-            const int32_t tid = pl.col_task[(size_t)T.anc_lo[a]];
-            start[(size_t)tid] = pl.tasks[(size_t)tid].lo;
-        }
-    }
-}
-
 int factor_impl(basker_t h, const double *values, cudaStream_t s, bool refactor)
 {
     h->launches = 0;
@@ -459,6 +485,7 @@ int factor_impl(basker_t h, const double *values, cudaStream_t s, bool refactor)
     tend(h, s);
     h->launches++;
     if (refactor) {
+        h->refno++;
         CU(cudaMemcpyAsync((void *)h->d.pref, h->d.prow, sizeof(int32_t) * (size_t)h->pl.n,
                            cudaMemcpyDeviceToDevice, s));
         if (!h->schedule_valid) TRY(compute_schedule(h, s));
@@ -468,11 +495,10 @@ int factor_impl(basker_t h, const double *values, cudaStream_t s, bool refactor)
         int st = read_status(h, s);
         if (st == BASKER_ERR_TIMEOUT) return st;
         h->info.last_repivot_columns = 0;
+        h->info.last_rounds = 0;
         if (h->h_status->static_fail) {
-            std::vector<int32_t> start;
-            redo_set(h, start);
-            TRY(launch_redo(h, s, start));
-            st = read_status(h, s);
+            st = launch_redo(h, s);
+            if (st == BASKER_OK) st = read_status(h, s);
             h->schedule_valid = false;
             if (st == -1) {
                 // the new pivots need more room: grow and run Algorithm 1 everywhere
@@ -709,7 +735,7 @@ int basker_info(basker_t h, basker_info_t *out)
         // flops: sum_j l_j (2 u_j + 1), u_j = entries right of the diagonal in row j of U
         std::vector<int64_t> ub(n + 1);
         CU(cudaMemcpy(ub.data(), h->d.Ubeg, (n + 1) * 8, cudaMemcpyDeviceToHost));
-        std::vector<int32_t> ui((size_t)h->pl.ucap);
+        std::vector<int32_t> ui((size_t)h->d.upool_end);
         CU(cudaMemcpy(ui.data(), h->d.Ui, ui.size() * 4, cudaMemcpyDeviceToHost));
         std::vector<int32_t> urow(n, 0);
         for (size_t c = 0; c < n; c++)
@@ -746,8 +772,8 @@ int basker_export(basker_t h, int32_t *prow, int64_t *Lp, int32_t *Li, double *L
     *nnz_u = nu;
     if (!Li) return BASKER_OK;
     if (!prow || !Lp || !Lx || !Up || !Ui || !Ux) return BASKER_ERR_INVALID_ARG;
-    std::vector<int32_t> li((size_t)h->pl.lcap), ui((size_t)h->pl.ucap);
-    std::vector<double> lx((size_t)h->pl.lcap), ux((size_t)h->pl.ucap);
+    std::vector<int32_t> li((size_t)h->d.lpool_end), ui((size_t)h->d.upool_end);
+    std::vector<double> lx((size_t)h->d.lpool_end), ux((size_t)h->d.upool_end);
     CU(cudaMemcpy(li.data(), h->d.Li, li.size() * 4, cudaMemcpyDeviceToHost));
     CU(cudaMemcpy(lx.data(), h->d.Lx, lx.size() * 8, cudaMemcpyDeviceToHost));
     CU(cudaMemcpy(ui.data(), h->d.Ui, ui.size() * 4, cudaMemcpyDeviceToHost));

@@ -53,9 +53,12 @@ struct bk_status {
     int32_t timeout;                 // nonzero: a wait gave up
     int32_t static_fail;             // nonzero: a column rejected its preferred pivot
     int32_t offdiag;                 // number of columns pivoting off the natural row
+    int32_t internal_site;           // first internal-consistency check that fired (0 = none)
+    int32_t internal_col;            // and its column
 };
 
 enum { BK_CODE_SINGULAR = 1, BK_CODE_NAN = 2, BK_CODE_INTERNAL = 3 };  // INTERNAL: an index outside its space
+enum { BK_DD_RESOLVE = 1, BK_DD_DESC = 2 };    // refactor round flags of a task
 
 // Everything the kernels read, as raw device pointers (passed by value).
 struct bk_dev {
@@ -66,14 +69,23 @@ struct bk_dev {
     bk_task *tasks;
     int32_t *prow, *pinv;
     const int32_t *pref;             // refactor: the previous pivot rows, preferred
-    int64_t *Lbeg, *Ubeg;
+    int64_t *Lbeg, *Ubeg;            // per column: region start
+    int64_t *Lend, *Uend;            // per column: region end (capacity)
     int32_t *Lcnt, *Ucnt;
+    unsigned long long *pool;        // [0] next free L entry, [1] next free U entry (spill pools)
+    int64_t lpool_end, upool_end;    // array sizes: regions of the layout, then the pools
     int32_t *Li, *Ui;
     double *Lx, *Ux;
     bk_status *status;
     int32_t *col_over;               // per column: 1 = its L region overflowed, 2 = its U region
     int32_t *task_stop;              // per task: nonzero once it or a descendant ran out of room
     int32_t *task_fail;              // per task: first column that rejected its preferred pivot
+    int32_t *col_fail;               // per column: 1 if it rejected its preferred pivot
+    int32_t *dd_start, *dd_flags;    // per task: first column and flags of the current round
+    int32_t *touch;                  // per row: epoch of the round that changed its pivot status
+    int32_t *dirty_ep;               // per column: epoch of the round that recomputed it
+    int32_t *pchg_ep;                // per column: epoch of the round that recomputed it by the reach
+    int32_t *touch_ref, *dirty_ref, *pchg_ref;   // the same, numbered by refactorization
     unsigned char *ws;               // global workspace (zero between uses)
     int32_t *done;                   // per column: epoch of its last completion (static kernel)
     int32_t *order;                  // static kernel claim order (topological)
@@ -108,6 +120,7 @@ struct bk_plan {
     std::vector<int32_t> sLcnt, sUcnt, sLi, sUi, sprow;
     std::vector<int32_t> slevel, sorder;              // static DAG levels and claim order
     int64_t lcap = 0, ucap = 0, nnz_l_sym = 0, nnz_u_sym = 0;
+    int64_t lpool = 0, upool = 0;                     // spill pools after the layout's regions
     int64_t ws_bytes = 0;                             // GP global workspace
     int64_t ahat_doubles = 0, ahat_words = 0;         // separator A-hat scratch
     int64_t wsd_slice = 0;                            // descendant-phase slice (bytes)
@@ -133,6 +146,8 @@ void bk_launch_gp_tasks(const bk_dev &d, const int32_t *task_ids, const int32_t 
                         int32_t ntasks, size_t smem, double tau, int pref_mode, void *stream);
 void bk_launch_gp_desc(const bk_dev &d, const int32_t *cols, int32_t ncols, int32_t *counter,
                        void *stream);
+void bk_launch_dd(const bk_dev &d, const int32_t *cols, int32_t ncols, int32_t *counter, double tau,
+                  int32_t epoch, long long budget, int32_t refno, void *stream);
 void bk_launch_reset_pivots(const bk_dev &d, const int32_t *task_ids, const int32_t *task_c0,
                             int32_t ntasks, void *stream);
 void bk_launch_static(const bk_dev &d, int32_t ncols, double tau, int32_t epoch,

@@ -109,6 +109,13 @@ __device__ __forceinline__ void report_fail(bk_status *st, int c, int code)
     atomicMin(&st->first_fail, ((unsigned long long)(unsigned)c << 8) | (unsigned)code);
 }
 
+// An index outside its space (never valid input): record where, then fail.
+__device__ __forceinline__ void report_internal(bk_status *st, int c, int site)
+{
+    if (atomicCAS(&st->internal_site, 0, site) == 0) st->internal_col = c;
+    report_fail(st, c, BK_CODE_INTERNAL);
+}
+
 // Stop work on column c of task tid if an earlier (or the same) column already
 // failed, a wait gave up, or this task or one of its descendants ran out of L/U
 // room (the host regrows and starts over; independent tasks run on, so one
@@ -119,6 +126,14 @@ __device__ __forceinline__ bool should_stop(const bk_dev &d, int tid, int c)
     const int to = *reinterpret_cast<const volatile int *>(&d.status->timeout);
     const int ts = *reinterpret_cast<const volatile int *>(d.task_stop + tid);
     return ts != 0 || to != 0 || (long long)(f >> 8) <= (long long)c;
+}
+
+// A region of count entries from a spill pool; -1 if the pool is exhausted.
+__device__ __forceinline__ int64_t pool_alloc(unsigned long long *next, int64_t end, int64_t count)
+{
+    const unsigned long long cnt = (unsigned long long)((count + 3) & ~(int64_t)3);
+    const unsigned long long b = atomicAdd(next, cnt);
+    return (int64_t)(b + cnt) <= end ? (int64_t)b : -1;
 }
 
 // Column c of task T ran out of room (what: 1 = L, 2 = U): flag it for the

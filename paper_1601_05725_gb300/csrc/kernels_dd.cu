@@ -1,0 +1,408 @@
+// kernels_dd.cu -- the rounds of a refactorization after the stored-pattern pass.
+//
+// The stored-pattern pass computes every column with the previous pivots and
+// flags the columns whose preferred pivot Algorithm 1's pivot selection would
+// reject.  Within a task (BTF block or ND node) everything before the first such
+// column f is exact.  A round then processes each active task from its start
+// column s (one warp per column, claimed in ascending order, flags per column):
+//   * resolve (s = f): column s is recomputed by the reach of Algorithm 1 and
+//     takes the pivot the selection rule gives; its previous and new pivot rows
+//     are marked "touched" in this round;
+//   * every other column is classified from its stored pattern: kept if no row of
+//     it was touched and none of its stored steps was recomputed (in this round,
+//     or, in a separator's first round, anywhere below it during this
+//     refactorization) and it had not rejected its pivot; recomputed on its
+//     stored pattern if only values can differ (a step was recomputed with an
+//     unchanged pattern, or it rejected its pivot); recomputed by the reach if
+//     a row was touched or a step's pattern may have changed;
+//   * a recomputed column (other than the resolve column) keeps its previous
+//     pivot if the selection rule still accepts it; otherwise it is flagged and
+//     the next round resolves the task's first flagged column.
+// Recomputation uses the reach over the task's whole space (descendant steps and
+// own steps, ascending; own steps of this round are waited for), with a row
+// counted as pivoted at column c when 0 <= pinv[row] < c.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+
+#include "basker_internal.h"
+#include "column_static.cuh"
+#include "device_util.cuh"
+
+using namespace bk;
+
+namespace {
+
+__device__ __forceinline__ void set_bit(volatile uint32_t *bm, int i)
+{
+    atomicOr(const_cast<uint32_t *>(bm) + (i >> 5), 1u << (i & 31));
+}
+
+__device__ __forceinline__ int next_step_bit(const volatile uint32_t *bm, int nw, int &w0, int lane)
+{
+    while (w0 < nw) {
+        const uint32_t v = (w0 + lane < nw) ? bm[w0 + lane] : 0u;
+        const uint32_t ball = __ballot_sync(BK_FULL, v != 0u);
+        if (ball) {
+            const int l = __ffs(ball) - 1;
+            const uint32_t bits = __shfl_sync(BK_FULL, v, l);
+            w0 += l;
+            return (w0 << 5) + (__ffs(bits) - 1);
+        }
+        w0 += 32;
+    }
+    return -1;
+}
+
+// Bounded wait of one lane on a flag; false if the budget ran out (or another
+// warp already gave up).
+__device__ __forceinline__ bool lane_wait(const bk_dev &d, const int *flag, int epoch, long long budget)
+{
+    if (ld_acquire(flag) == epoch) return true;
+    const long long t0 = clock64();
+    while (ld_acquire(flag) != epoch) {
+        if (*reinterpret_cast<const volatile int *>(&d.status->timeout) || clock64() - t0 > budget) {
+            atomicExch(&d.status->timeout, 1);
+            return false;
+        }
+        __nanosleep(32);
+    }
+    return true;
+}
+
+__global__ void __launch_bounds__(128) bk_dd_kernel(bk_dev d, const int32_t *__restrict__ cols, int32_t ncols,
+                                                    int32_t *counter, double tau, int32_t epoch, long long budget,
+                                                    int32_t refno)
+{
+    __shared__ bk_task Ts[4];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int gw = blockIdx.x * 4 + wib;
+    if (gw >= d.wsd_warps) return;
+    bk_task &T = Ts[wib];
+    unsigned char *slice = d.wsd + (int64_t)gw * d.wsd_slice;
+    int cur_task = -1;
+    for (;;) {
+        int k = 0;
+        if (lane == 0) k = atomicAdd(counter, 1);
+        k = __shfl_sync(BK_FULL, k, 0);
+        if (k >= ncols) break;
+        const int c = cols[k];
+        const int tid = d.col_task[c];
+        if (__shfl_sync(BK_FULL, (int)should_stop(d, tid, c), 0)) {
+            if (lane == 0) st_release(d.done + c, epoch);
+            continue;
+        }
+        if (tid != cur_task) {
+            load_task(T, d.tasks + tid, lane);
+            cur_task = tid;
+        }
+        const int s0 = d.dd_start[tid];
+        const int fl = d.dd_flags[tid];
+        const bool resolve = (fl & BK_DD_RESOLVE) && c == s0;
+        // the resolve column's touched rows must be visible before deciding
+        if ((fl & BK_DD_RESOLVE) && c > s0) {
+            int ok = lane == 0 ? (int)lane_wait(d, d.done + s0, epoch, budget) : 1;
+            if (!__shfl_sync(BK_FULL, ok, 0)) return;
+        }
+        int64_t ub = d.Ubeg[c], ue = d.Uend[c];
+        int64_t lb = d.Lbeg[c], le = d.Lend[c];
+        // Recompute on the stored pattern unless the pattern may change: a row of
+        // it was touched (this round; or, in a separator's first round, anywhere
+        // below during this refactorization), or one of its steps was recomputed
+        // by the reach (checked as the steps are reached).
+        int mode = resolve ? 2 : 1;
+        if (!resolve) {
+            if (lane == 0) {
+                const int r = d.prow[c];
+                if (__ldcg(d.touch + r) == epoch) mode = 2;
+                if ((fl & BK_DD_DESC) && __ldcg(d.touch_ref + r) == refno) mode = 2;
+            }
+            const int uc = d.Ucnt[c];
+            for (int q = lane; q < uc - 1; q += 32) {
+                const int j = d.Ui[ub + q];
+                const int r = __ldcg(d.prow + j);
+                if (__ldcg(d.touch + r) == epoch) mode = 2;
+                if ((fl & BK_DD_DESC) && (__ldcg(d.touch_ref + r) == refno ||
+                                          (d.col_task[j] != tid && __ldcg(d.pchg_ref + j) == refno)))
+                    mode = 2;
+            }
+            const int lc = d.Lcnt[c];
+            for (int q = lane; q < lc; q += 32) {
+                const int r = d.Li[lb + q];
+                if (__ldcg(d.touch + r) == epoch) mode = 2;
+                if ((fl & BK_DD_DESC) && __ldcg(d.touch_ref + r) == refno) mode = 2;
+            }
+            mode = warp_max_i(mode);
+            if (mode == 1) {
+                bool ok = false, bad = false, broken = false, aborted = false;
+                double *xs = reinterpret_cast<double *>(slice);
+                if (!static_column(d, T, tid, xs, c, epoch, budget, tau, lane, false, s0, ok, bad, broken,
+                                   d.pchg_ep, &aborted))
+                    return;
+                if (!aborted) {
+                    __syncwarp();
+                    if (lane == 0) {
+                        if (broken) report_internal(d.status, c, 68);
+                        d.col_fail[c] = ok ? 0 : 1;
+                        if (!ok) atomicMin(d.task_fail + tid, c);
+                        d.dirty_ep[c] = epoch;
+                        d.dirty_ref[c] = refno;
+                        __threadfence();
+                        st_release(d.done + c, epoch);
+                    }
+                    __syncwarp();
+                    if (broken) return;
+                    continue;
+                }
+            }
+        }
+
+        // ---- recompute column c by the reach over the task's space
+        const int base = T.sp_lo;
+        const int nsteps = T.hi - T.sp_lo;
+        const int ndesc = T.lo - T.sp_lo;
+        const int nown = T.hi - T.lo;
+        const int lsp = T.lspace;
+        const int nsw = (nsteps + 31) >> 5;
+        const int nrw = (lsp + 31) >> 5;
+        double *x = reinterpret_cast<double *>(slice);
+        volatile uint32_t *sb = reinterpret_cast<uint32_t *>(x + T.space);
+        volatile uint32_t *rb = sb + nsw;
+        bool bad = false, overflow = false;
+        int why = 0;
+        int nu = 0;
+
+        const int e1 = d.Bp[c + 1];
+        for (int e = d.dstart[c] + lane; e < e1; e += 32) {
+            const int r = d.Bi[e];
+            const int s = slot_of(T, base, r);
+            if (s < 0) { if (!why) why = 61; continue; }
+            x[s] = d.Bx[e];
+            const int p = s < T.hi - base ? __ldcg(d.pinv + r) : -1;
+            if (p >= 0 && p < c && p >= base) set_bit(sb, p - base);
+            else if (s >= ndesc) set_bit(rb, s - ndesc);
+            else if (!why) why = 62;                 // a descendant row is always pivoted
+        }
+        __syncwarp();
+        int w0 = 0;
+        for (int iter = 0;; iter++) {
+            const int jb = next_step_bit(sb, nsw, w0, lane);
+            if (jb < 0) break;
+            const int j = base + jb;
+            if (iter > nsteps || j >= c) { if (!why) why = 63; break; }
+            if (j >= s0 && d.col_task[j] == tid) {
+                int ok = lane == 0 ? (int)lane_wait(d, d.done + j, epoch, budget) : 1;
+                if (!__shfl_sync(BK_FULL, ok, 0)) return;
+            }
+            const int sp = slot_of(T, base, __ldcg(d.prow + j));
+            if (sp < 0) { if (!why) why = 64; break; }
+            const double m = x[sp];
+            __syncwarp();
+            if (lane == 0) {
+                atomicAnd(const_cast<uint32_t *>(sb) + (jb >> 5), ~(1u << (jb & 31)));
+                x[sp] = 0.0;
+            }
+            if (!isfinite(m)) bad = true;
+            if (!overflow && ub + nu + 2 > ue) {
+                const int64_t cap = (int64_t)(c - T.sp_lo) + 1;
+                int64_t nb = 0;
+                if (lane == 0) nb = pool_alloc(d.pool + 1, d.upool_end, cap);
+                nb = __shfl_sync(BK_FULL, nb, 0);
+                if (nb < 0) {
+                    overflow = true;
+                } else {
+                    for (int q = lane; q < nu; q += 32) {
+                        d.Ui[nb + q] = d.Ui[ub + q];
+                        d.Ux[nb + q] = d.Ux[ub + q];
+                    }
+                    __syncwarp();
+                    ub = nb;
+                    ue = nb + cap;
+                    if (lane == 0) {
+                        d.Ubeg[c] = ub;
+                        d.Uend[c] = ue;
+                    }
+                }
+            }
+            if (!overflow && lane == 0) {
+                d.Ui[ub + nu] = j;
+                d.Ux[ub + nu] = m;
+            }
+            nu++;
+            const int64_t jl = __ldcg(d.Lbeg + j);
+            const int jc = __ldcg(d.Lcnt + j);
+            for (int q = lane; q < jc; q += 32) {
+                const int r = __ldcg(d.Li + jl + q);
+                const double l = __ldcg(d.Lx + jl + q);
+                const int s = slot_of(T, base, r);
+                if (s < 0) { if (!why) why = 65; continue; }
+                x[s] = fma(-l, m, x[s]);
+                const int p = s < T.hi - base ? __ldcg(d.pinv + r) : -1;
+                if (p >= 0 && p < c) {
+                    if (p > j) set_bit(sb, p - base);
+                    else if (!why) why = 66;
+                } else if (s >= ndesc) {
+                    set_bit(rb, s - ndesc);
+                } else if (!why) {
+                    why = 67;
+                }
+            }
+            __syncwarp();
+        }
+        why = warp_max_i(why);
+        // Algorithm 1's pivot selection among the node's unpivoted rows
+        double amax = 0.0;
+        int ncand = 0;
+        for (int w = lane; w < nrw; w += 32) {
+            uint32_t bits = rb[w];
+            while (bits) {
+                const int b = __ffs(bits) - 1;
+                bits &= bits - 1;
+                const int ls = (w << 5) + b;
+                const double v = x[ndesc + ls];
+                if (!isfinite(v)) bad = true;
+                if (ls < nown) {
+                    ncand++;
+                    amax = fmax(amax, fabs(v));
+                }
+            }
+        }
+        amax = warp_max(amax);
+        ncand = warp_sum(ncand);
+        bad = __any_sync(BK_FULL, bad);
+        const int pcur = __ldcg(d.prow + c);
+        const int pref = resolve ? d.pref[c] : pcur;
+        auto in_pattern = [&](int r) -> bool {
+            const int ls = r - T.lo;
+            return (unsigned)ls < (unsigned)nown && ((rb[ls >> 5] >> (ls & 31)) & 1u);
+        };
+        int piv = -1;
+        bool ok = false;
+        if (!bad && ncand > 0 && amax > 0.0) {
+            if (in_pattern(pref) && fabs(x[ndesc + pref - T.lo]) >= tau * amax) {
+                piv = pref;
+                ok = true;
+            } else if (resolve) {
+                int best = INT_MAX;
+                const int nw_own = (nown + 31) >> 5;
+                for (int w = lane; w < nw_own; w += 32) {
+                    uint32_t bits = rb[w];
+                    while (bits) {
+                        const int b = __ffs(bits) - 1;
+                        bits &= bits - 1;
+                        const int ls = (w << 5) + b;
+                        if (ls < nown && fabs(x[ndesc + ls]) == amax) { best = ls; break; }
+                    }
+                    if (best != INT_MAX) break;
+                }
+                best = warp_min(best);
+                piv = T.lo + best;
+                ok = true;
+            }
+        }
+        if (resolve && piv < 0) {
+            // no acceptable pivot at an exact column: the matrix is singular here
+            if (lane == 0) report_fail(d.status, c, bad ? BK_CODE_NAN : BK_CODE_SINGULAR);
+        }
+        if (piv < 0) piv = pcur;                     // keep the speculation consistent
+        const int pls = piv - T.lo;
+        const bool pin = in_pattern(piv);
+        const double xp = pin ? x[ndesc + pls] : 0.0;
+        // L(:,c) = x / pivot over the pattern's unpivoted rows; clear the state
+        {
+            int cnt_all = 0;
+            for (int w = lane; w < nrw; w += 32) cnt_all += __popc(rb[w]);
+            cnt_all = warp_sum(cnt_all) - (pin ? 1 : 0);
+            if (!overflow && lb + cnt_all > le) {
+                const int64_t cap = max((long long)cnt_all,
+                                        min((long long)(2 * (int64_t)cnt_all + 16),
+                                            (long long)((T.hi - c - 1) + (lsp - nown))));
+                int64_t nb = 0;
+                if (lane == 0) nb = pool_alloc(d.pool, d.lpool_end, cap);
+                nb = __shfl_sync(BK_FULL, nb, 0);
+                if (nb < 0) {
+                    overflow = true;
+                } else {
+                    lb = nb;
+                    le = nb + cap;
+                    if (lane == 0) {
+                        d.Lbeg[c] = lb;
+                        d.Lend[c] = le;
+                    }
+                }
+            }
+        }
+        int64_t lpos = lb;
+        for (int wbase = 0; wbase < nrw; wbase += 32) {
+            const int w = wbase + lane;
+            uint32_t bits = w < nrw ? rb[w] : 0u;
+            if (w < nrw && bits) rb[w] = 0u;
+            if (pin && w == (pls >> 5)) bits &= ~(1u << (pls & 31));
+            const int cnt = __popc(bits);
+            const int pre = warp_exscan(cnt, lane);
+            const int tot = __shfl_sync(BK_FULL, pre + cnt, 31);
+            const bool room = !overflow && lpos + tot <= le;
+            int64_t q = lpos + pre;
+            while (bits) {
+                const int b = __ffs(bits) - 1;
+                bits &= bits - 1;
+                const int ls = (w << 5) + b;
+                if (room) {
+                    d.Li[q] = row_of_lslot(T, ls);
+                    d.Lx[q] = x[ndesc + ls] / xp;
+                }
+                x[ndesc + ls] = 0.0;
+                q++;
+            }
+            if (!room) overflow = true;
+            lpos += tot;
+        }
+        overflow = __any_sync(BK_FULL, overflow);
+        __syncwarp();
+        if (lane == 0) {
+            if (pin) x[ndesc + pls] = 0.0;
+            if (why) report_internal(d.status, c, why);
+            if (!overflow) {
+                d.Ui[ub + nu] = c;
+                d.Ux[ub + nu] = xp;
+                d.Ucnt[c] = nu + 1;
+                d.Lcnt[c] = (int)(lpos - lb);
+            } else {
+                report_overflow(d, T, tid, c, 3);
+            }
+            if (resolve && piv != pcur) {
+                if (__ldcg(d.pinv + pcur) == c) d.pinv[pcur] = -1;
+                d.pinv[piv] = c;
+                d.prow[c] = piv;
+                d.touch[pcur] = epoch;
+                d.touch[piv] = epoch;
+                d.touch_ref[pcur] = refno;
+                d.touch_ref[piv] = refno;
+                if (piv != c) atomicAdd(&d.status->offdiag, 1);
+            }
+            d.col_fail[c] = ok ? 0 : 1;
+            if (!ok && !resolve) atomicMin(d.task_fail + tid, c);
+            d.dirty_ep[c] = epoch;
+            d.dirty_ref[c] = refno;
+            d.pchg_ep[c] = epoch;
+            d.pchg_ref[c] = refno;
+            __threadfence();
+            st_release(d.done + c, epoch);
+        }
+        __syncwarp();
+        if (why) return;      // the workspace slice may hold stale values; the host clears it
+    }
+}
+
+}  // namespace
+
+void bk_launch_dd(const bk_dev &d, const int32_t *cols, int32_t ncols, int32_t *counter, double tau,
+                  int32_t epoch, long long budget, int32_t refno, void *stream)
+{
+    if (ncols <= 0) return;
+    int warps = std::min<int>(ncols, d.wsd_warps);
+    bk_dd_kernel<<<(warps + 3) / 4, 128, 0, (cudaStream_t)stream>>>(d, cols, ncols, counter, tau, epoch, budget,
+                                                                     refno);
+}

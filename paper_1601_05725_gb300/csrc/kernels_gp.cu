@@ -71,6 +71,12 @@ __device__ __forceinline__ int next_step_bit(const volatile uint32_t *bm, int nw
 //   x   dense values, zero outside the current column's pattern
 //   sb  bitmap of own pivot steps still to apply to the column
 //   rb  bitmap of L-space rows in the pattern that are not pivoted
+//   tb  (mode 2) own rows whose pivot status a recomputed column changed
+// A row counts as pivoted at column c when 0 <= pinv[row] < c, so that pinv may
+// still hold later columns' previous pivots during a redo.
+// pref_mode: 0 prefer the natural row; 1 prefer pref[c]; 2 a redo from task_c0
+// that recomputes only the columns whose stored pattern meets a touched row
+// (or that rejected their preferred pivot) and keeps the others.
 __global__ void __launch_bounds__(32) bk_gp_task_kernel(bk_dev d, const int32_t *__restrict__ task_ids,
                                                         const int32_t *__restrict__ task_c0, double tau,
                                                         int pref_mode)
@@ -85,28 +91,76 @@ __global__ void __launch_bounds__(32) bk_gp_task_kernel(bk_dev d, const int32_t 
     const int lsp = T.lspace;
     const int nsw = (nown + 31) >> 5;
     const int nrw = (lsp + 31) >> 5;
-    double *x;
-    volatile uint32_t *sb, *rb;
+    // layout (shared memory, or the task's global workspace slice):
+    //   x[lsp] | slbeg[nown] | sb[nsw] | rb[nrw] | tb[nsw] | spinv[nown] | sprow[nown] | slcnt[nown]
+    // spinv / sprow / slbeg / slcnt cache pinv, prow, Lbeg, Lcnt of the node's own
+    // rows and columns (written through to global memory when they change).
+    unsigned char *area = T.wsoff < 0 ? dsm : d.ws + T.wsoff;
+    double *x = reinterpret_cast<double *>(area);
+    int64_t *slbeg = reinterpret_cast<int64_t *>(x + lsp);
+    uint32_t *s32 = reinterpret_cast<uint32_t *>(slbeg + nown);
+    volatile uint32_t *sb = s32;
+    volatile uint32_t *rb = s32 + nsw;
+    volatile uint32_t *tb = rb + nrw;
+    int32_t *spinv = reinterpret_cast<int32_t *>(s32 + 2 * nsw + nrw);
+    int32_t *sprow = spinv + nown;
+    int32_t *slcnt = sprow + nown;
     if (T.wsoff < 0) {
-        x = reinterpret_cast<double *>(dsm);
-        uint32_t *s = reinterpret_cast<uint32_t *>(x + lsp);
         for (int i = lane; i < lsp; i += 32) x[i] = 0.0;
-        for (int i = lane; i < nsw + nrw; i += 32) s[i] = 0u;
-        sb = s;
-        rb = s + nsw;
-        __syncwarp();
-    } else {
-        x = reinterpret_cast<double *>(d.ws + T.wsoff);
-        sb = reinterpret_cast<uint32_t *>(x + lsp);
-        rb = sb + nsw;
+        for (int i = lane; i < nsw + nrw; i += 32) s32[i] = 0u;
     }
+    for (int i = lane; i < nsw; i += 32) tb[i] = 0u;
+    for (int i = lane; i < nown; i += 32) {
+        spinv[i] = d.pinv[T.lo + i];
+        sprow[i] = d.prow[T.lo + i];
+        slbeg[i] = d.Lbeg[T.lo + i];
+        slcnt[i] = d.Lcnt[T.lo + i];
+    }
+    __syncwarp();
     const bool sep = T.sp_lo < T.lo;               // continue a separator column from A-hat
     const int c_begin = task_c0 ? task_c0[blockIdx.x] : T.lo;
 
     for (int c = c_begin; c < T.hi; ++c) {
-        if (__shfl_sync(BK_FULL, (int)should_stop(d, tid, c), 0)) return;
-        const int64_t ub = d.Ubeg[c], ue = d.Ubeg[c + 1];
-        const int64_t lb = d.Lbeg[c], le = d.Lbeg[c + 1];
+        if (((c - c_begin) & 15) == 0 && __shfl_sync(BK_FULL, (int)should_stop(d, tid, c), 0)) return;
+        int64_t ub = d.Ubeg[c], ue = d.Uend[c];
+        int64_t lb = d.Lbeg[c], le = d.Lend[c];
+        if (pref_mode == 2) {
+            // keep a column whose stored pattern meets no touched row and that
+            // accepted its preferred pivot: its computation is unchanged
+            bool hit = c == c_begin || d.col_fail[c] != 0;
+            {
+                const int r0 = d.pref[c] - base;     // its own previous pivot row
+                if ((unsigned)r0 < (unsigned)nown && (tb[r0 >> 5] >> (r0 & 31)) & 1u) hit = true;
+            }
+            if (!hit) {
+                const int uc = d.Ucnt[c];
+                for (int k = lane; k < uc - 1 && !hit; k += 32) {
+                    const int j = d.Ui[ub + k];
+                    if (j >= T.lo) {
+                        const int r = d.pref[j] - base;
+                        if ((unsigned)r < (unsigned)nown && (tb[r >> 5] >> (r & 31)) & 1u) hit = true;
+                    }
+                }
+                const int lc = d.Lcnt[c];
+                for (int k = lane; k < lc && !hit; k += 32) {
+                    const int r = d.Li[lb + k] - base;
+                    if ((unsigned)r < (unsigned)nown && (tb[r >> 5] >> (r & 31)) & 1u) hit = true;
+                }
+            }
+            if (!__any_sync(BK_FULL, hit)) continue;
+            // recompute: the previous pivot row is touched and free again
+            if (lane == 0) {
+                const int r0 = d.pref[c];
+                if (r0 >= T.lo && r0 < T.hi) {
+                    atomicOr(const_cast<uint32_t *>(tb) + ((r0 - base) >> 5), 1u << ((r0 - base) & 31));
+                    if (spinv[r0 - base] == c) {
+                        spinv[r0 - base] = -1;
+                        d.pinv[r0] = -1;
+                    }
+                }
+            }
+            __syncwarp();
+        }
         int nu = 0;
         bool bad = false;
         if (sep) {
@@ -122,8 +176,8 @@ __global__ void __launch_bounds__(32) bk_gp_task_kernel(bk_dev d, const int32_t 
                     bits &= bits - 1;
                     const int ls = (w << 5) + b;
                     x[ls] = ah[ls];
-                    const int p = ls < nown ? d.pinv[base + ls] : -1;
-                    if (p >= 0 && (unsigned)(p - base) < (unsigned)nown) set_bit(sb, p - base);
+                    const int p = ls < nown ? spinv[ls] : -1;
+                    if (p >= 0 && p < c && p >= base) set_bit(sb, p - base);
                     else keep |= 1u << b;
                 }
                 if (keep) atomicOr(const_cast<uint32_t *>(rb) + w, keep);
@@ -133,12 +187,12 @@ __global__ void __launch_bounds__(32) bk_gp_task_kernel(bk_dev d, const int32_t 
             for (int e = d.dstart[c] + lane; e < e1; e += 32) {
                 const int r = d.Bi[e];
                 const int s = slot_of(T, base, r);
-                if (s < 0) { report_fail(d.status, c, BK_CODE_INTERNAL); continue; }
+                if (s < 0) { report_internal(d.status, c, 11); continue; }
                 x[s] = d.Bx[e];
-                const int p = s < nown ? d.pinv[r] : -1;
-                if (p >= 0) {
-                    if ((unsigned)(p - base) < (unsigned)nown) set_bit(sb, p - base);
-                    else report_fail(d.status, c, BK_CODE_INTERNAL);
+                const int p = s < nown ? spinv[s] : -1;
+                if (p >= 0 && p < c) {
+                    if (p >= base) set_bit(sb, p - base);
+                    else report_internal(d.status, c, 12);
                 } else {
                     set_bit(rb, s);
                 }
@@ -152,9 +206,9 @@ __global__ void __launch_bounds__(32) bk_gp_task_kernel(bk_dev d, const int32_t 
             const int jb = next_step_bit(sb, nsw, w0, lane);
             if (jb < 0) break;
             const int j = base + jb;
-            const int sp = d.prow[j] - base;      // a pivoted own row: slot = row - lo
+            const int sp = sprow[jb] - base;       // a pivoted own row: slot = row - lo
             if (iter > nown || j >= c || (unsigned)sp >= (unsigned)nown) {
-                if (lane == 0) report_fail(d.status, c, BK_CODE_INTERNAL);
+                if (lane == 0) report_internal(d.status, c, 13);
                 return;
             }
             const double m = x[sp];
@@ -165,26 +219,44 @@ __global__ void __launch_bounds__(32) bk_gp_task_kernel(bk_dev d, const int32_t 
             }
             if (!isfinite(m)) bad = true;
             if (ub + nu + 2 > ue) {
-                if (lane == 0) report_overflow(d, T, tid, c, 2);
-                return;
+                // move the column to a pool region of its largest possible size
+                const int64_t cap = (int64_t)(c - T.sp_lo) + 1;
+                int64_t nb = 0;
+                if (lane == 0) nb = pool_alloc(d.pool + 1, d.upool_end, cap);
+                nb = __shfl_sync(BK_FULL, nb, 0);
+                if (nb < 0) {
+                    if (lane == 0) report_overflow(d, T, tid, c, 2);
+                    return;
+                }
+                for (int k = lane; k < nu; k += 32) {
+                    d.Ui[nb + k] = d.Ui[ub + k];
+                    d.Ux[nb + k] = d.Ux[ub + k];
+                }
+                __syncwarp();
+                ub = nb;
+                ue = nb + cap;
+                if (lane == 0) {
+                    d.Ubeg[c] = ub;
+                    d.Uend[c] = ue;
+                }
             }
             if (lane == 0) {
                 d.Ui[ub + nu] = j;
                 d.Ux[ub + nu] = m;
             }
             nu++;
-            const int64_t jl = d.Lbeg[j];
-            const int jc = d.Lcnt[j];
+            const int64_t jl = slbeg[jb];
+            const int jc = slcnt[jb];
             for (int k = lane; k < jc; k += 32) {
                 const int r = d.Li[jl + k];
                 const double l = d.Lx[jl + k];
                 const int s = slot_of(T, base, r);
-                if (s < 0) { report_fail(d.status, c, BK_CODE_INTERNAL); continue; }
+                if (s < 0) { report_internal(d.status, c, 14); continue; }
                 x[s] = fma(-l, m, x[s]);
-                const int p = s < nown ? d.pinv[r] : -1;
-                if (p >= 0) {
-                    if (p > j && p < c) set_bit(sb, p - base);
-                    else report_fail(d.status, c, BK_CODE_INTERNAL);
+                const int p = s < nown ? spinv[s] : -1;
+                if (p >= 0 && p < c) {
+                    if (p > j) set_bit(sb, p - base);
+                    else report_internal(d.status, c, 15);
                 } else {
                     set_bit(rb, s);
                 }
@@ -215,7 +287,8 @@ __global__ void __launch_bounds__(32) bk_gp_task_kernel(bk_dev d, const int32_t 
         int piv = -1;
         if (!bad && ncand > 0 && amax > 0.0) {
             const int pref = pref_mode ? d.pref[c] : c;
-            if (pref >= T.lo && pref < T.hi && d.pinv[pref] < 0 && fabs(x[pref - base]) >= tau * amax) {
+            if (pref >= T.lo && pref < T.hi && (spinv[pref - base] < 0 || spinv[pref - base] >= c) &&
+                fabs(x[pref - base]) >= tau * amax) {
                 piv = pref;
             } else {
                 int best = INT_MAX;
@@ -245,8 +318,31 @@ __global__ void __launch_bounds__(32) bk_gp_task_kernel(bk_dev d, const int32_t 
             d.Ux[ub + nu] = xp;
         }
         nu++;
-        int64_t lpos = lb;
         const int pl = piv - base;
+        {
+            int cnt_all = 0;
+            for (int w = lane; w < nrw; w += 32) cnt_all += __popc(rb[w]);
+            cnt_all = warp_sum(cnt_all) - 1;          // without the pivot
+            if (lb + cnt_all > le) {
+                const int64_t cap = min((long long)(2 * (int64_t)cnt_all + 16),
+                                        (long long)((T.hi - c - 1) + (lsp - nown)));
+                int64_t nb = 0;
+                if (lane == 0) nb = pool_alloc(d.pool, d.lpool_end, cap);
+                nb = __shfl_sync(BK_FULL, nb, 0);
+                if (nb < 0) {
+                    if (lane == 0) report_overflow(d, T, tid, c, 1);
+                    return;
+                }
+                lb = nb;
+                le = nb + cap;
+                if (lane == 0) {
+                    d.Lbeg[c] = lb;
+                    d.Lend[c] = le;
+                    slbeg[c - base] = lb;
+                }
+            }
+        }
+        int64_t lpos = lb;
         for (int wbase = 0; wbase < nrw; wbase += 32) {
             const int w = wbase + lane;
             uint32_t bits = w < nrw ? rb[w] : 0u;
@@ -276,9 +372,13 @@ __global__ void __launch_bounds__(32) bk_gp_task_kernel(bk_dev d, const int32_t 
             x[pl] = 0.0;
             d.pinv[piv] = c;
             d.prow[c] = piv;
+            spinv[pl] = c;
+            sprow[c - base] = piv;
+            slcnt[c - base] = (int)(lpos - lb);
             d.Lcnt[c] = (int)(lpos - lb);
             d.Ucnt[c] = nu;
             if (piv != c) atomicAdd(&d.status->offdiag, 1);
+            if (pref_mode == 2) atomicOr(const_cast<uint32_t *>(tb) + (pl >> 5), 1u << (pl & 31));
         }
         __syncwarp();
     }
@@ -319,7 +419,7 @@ __global__ void __launch_bounds__(128) bk_gp_desc_kernel(bk_dev d, const int32_t
         double *x = reinterpret_cast<double *>(slice);
         volatile uint32_t *sb = reinterpret_cast<uint32_t *>(x + T.space);
         volatile uint32_t *rb = sb + nsw;
-        const int64_t ub = d.Ubeg[c], ue = d.Ubeg[c + 1];
+        int64_t ub = d.Ubeg[c], ue = d.Uend[c];
         bool bad = false;
         int nu = 0;
 
@@ -327,12 +427,12 @@ __global__ void __launch_bounds__(128) bk_gp_desc_kernel(bk_dev d, const int32_t
         for (int e = d.dstart[c] + lane; e < e1; e += 32) {
             const int r = d.Bi[e];
             const int s = slot_of(T, base, r);
-            if (s < 0) { report_fail(d.status, c, BK_CODE_INTERNAL); continue; }
+            if (s < 0) { report_internal(d.status, c, 16); continue; }
             x[s] = d.Bx[e];
             if (s < ndesc) {
                 const int p = d.pinv[r];            // descendant rows are all pivoted
                 if ((unsigned)(p - base) < (unsigned)ndesc) set_bit(sb, p - base);
-                else report_fail(d.status, c, BK_CODE_INTERNAL);
+                else report_internal(d.status, c, 17);
             } else {
                 set_bit(rb, s - ndesc);
             }
@@ -353,7 +453,27 @@ __global__ void __launch_bounds__(128) bk_gp_desc_kernel(bk_dev d, const int32_t
                 x[sp] = 0.0;
             }
             if (!isfinite(m)) bad = true;
-            if (ub + nu + 2 > ue) overflow = true;
+            if (!overflow && ub + nu + 2 > ue) {
+                const int64_t cap = (int64_t)(c - T.sp_lo) + 1;
+                int64_t nb = 0;
+                if (lane == 0) nb = pool_alloc(d.pool + 1, d.upool_end, cap);
+                nb = __shfl_sync(BK_FULL, nb, 0);
+                if (nb < 0) {
+                    overflow = true;
+                } else {
+                    for (int k = lane; k < nu; k += 32) {
+                        d.Ui[nb + k] = d.Ui[ub + k];
+                        d.Ux[nb + k] = d.Ux[ub + k];
+                    }
+                    __syncwarp();
+                    ub = nb;
+                    ue = nb + cap;
+                    if (lane == 0) {
+                        d.Ubeg[c] = ub;
+                        d.Uend[c] = ue;
+                    }
+                }
+            }
             if (!overflow && lane == 0) {
                 d.Ui[ub + nu] = j;
                 d.Ux[ub + nu] = m;
@@ -365,12 +485,12 @@ __global__ void __launch_bounds__(128) bk_gp_desc_kernel(bk_dev d, const int32_t
                 const int r = d.Li[jl + q];
                 const double l = d.Lx[jl + q];
                 const int s = slot_of(T, base, r);
-                if (s < 0) { report_fail(d.status, c, BK_CODE_INTERNAL); continue; }
+                if (s < 0) { report_internal(d.status, c, 18); continue; }
                 x[s] = fma(-l, m, x[s]);
                 if (s < ndesc) {
                     const int p = d.pinv[r];
                     if (p > j && p < T.lo) set_bit(sb, p - base);
-                    else report_fail(d.status, c, BK_CODE_INTERNAL);
+                    else report_internal(d.status, c, 19);
                 } else {
                     set_bit(rb, s - ndesc);
                 }
@@ -396,7 +516,7 @@ __global__ void __launch_bounds__(128) bk_gp_desc_kernel(bk_dev d, const int32_t
         if (broken) {
             // an impossible step (a bug, never valid input): report it; this warp's
             // workspace slice is no longer clean, the host clears it on error
-            if (lane == 0) report_fail(d.status, c, BK_CODE_INTERNAL);
+            if (lane == 0) report_internal(d.status, c, 20);
             return;
         }
         if (lane == 0) {
@@ -422,7 +542,7 @@ __global__ void bk_reset_pivots_kernel(bk_dev d, const int32_t *__restrict__ tas
 
 }  // namespace
 
-size_t bk_gp_smem_limit() { return 160 * 1024; }
+size_t bk_gp_smem_limit() { return 220 * 1024; }
 
 void bk_launch_gather(const bk_dev &d, const double *values, int64_t nnz, void *stream)
 {

@@ -86,7 +86,7 @@ __device__ void forward_sweep(const bk_dev &d, const bk_solve_dev &s, const bk_t
             } else {
                 const int a = acc ? anc_slot(T, i) : -1;
                 if (a >= 0) acc[a] = fma(l, wk, acc[a]);
-                else report_fail(d.status, k, BK_CODE_INTERNAL);
+                else report_internal(d.status, k, 51);
             }
         }
         __syncwarp();

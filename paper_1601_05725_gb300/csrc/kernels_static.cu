@@ -21,36 +21,12 @@
 #include <algorithm>
 
 #include "basker_internal.h"
+#include "column_static.cuh"
 #include "device_util.cuh"
 
 using namespace bk;
 
 namespace {
-
-// Wait until flag == epoch (lane 0 spins, the warp follows).  Returns false if the
-// budget ran out or another warp already gave up.
-__device__ __forceinline__ bool wait_flag(const bk_dev &d, const int *flag, int epoch, long long budget,
-                                          int lane)
-{
-    int ok = 1;
-    if (lane == 0) {
-        if (ld_acquire(flag) != epoch) {
-            const long long t0 = clock64();
-            for (;;) {
-                if (ld_acquire(flag) == epoch) break;
-                if (*reinterpret_cast<const volatile int *>(&d.status->timeout)) { ok = 0; break; }
-                if (clock64() - t0 > budget) {
-                    atomicExch(&d.status->timeout, 1);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(64);
-            }
-        }
-    }
-    ok = __shfl_sync(BK_FULL, ok, 0);
-    return ok != 0;
-}
 
 __global__ void __launch_bounds__(128) bk_static_kernel(bk_dev d, int32_t ncols, double tau, int32_t epoch,
                                                         long long budget)
@@ -74,66 +50,13 @@ __global__ void __launch_bounds__(128) bk_static_kernel(bk_dev d, int32_t ncols,
             load_task(T, d.tasks + tid, lane);
             cur = tid;
         }
-        const int base = T.sp_lo;
-        const int e1 = d.Bp[c + 1];
-        bool broken = false;
-        for (int e = d.dstart[c] + lane; e < e1; e += 32) {
-            const int s = slot_of(T, base, d.Bi[e]);
-            if (s < 0) { broken = true; continue; }
-            x[s] = d.Bx[e];
-        }
-        __syncwarp();
-        const int64_t ub = d.Ubeg[c];
-        const int uc = d.Ucnt[c];
-        bool bad = false;
-        for (int q = 0; q < uc - 1; ++q) {
-            const int j = d.Ui[ub + q];
-            if (!wait_flag(d, d.done + j, epoch, budget, lane)) return;
-            const int sp = slot_of(T, base, d.prow[j]);
-            if (sp < 0) { broken = true; continue; }
-            const double m = x[sp];
-            __syncwarp();
-            if (lane == 0) {
-                x[sp] = 0.0;
-                d.Ux[ub + q] = m;
-            }
-            if (!isfinite(m)) bad = true;
-            const int64_t jl = d.Lbeg[j];
-            const int jc = d.Lcnt[j];
-            for (int t = lane; t < jc; t += 32) {
-                const int s = slot_of(T, base, d.Li[jl + t]);
-                if (s < 0) { broken = true; continue; }
-                x[s] = fma(-__ldcg(d.Lx + jl + t), m, x[s]);
-            }
-            __syncwarp();
-        }
-        const int p = d.prow[c];
-        int sp = slot_of(T, base, p);
-        if (sp < 0) { broken = true; sp = 0; }
-        const double xp = x[sp];
-        double amax = fabs(xp);
-        if (!isfinite(xp)) bad = true;
-        const int64_t lb = d.Lbeg[c];
-        const int lc = d.Lcnt[c];
-        for (int t = lane; t < lc; t += 32) {
-            const int r = d.Li[lb + t];
-            const int s = slot_of(T, base, r);
-            if (s < 0) { broken = true; continue; }
-            const double v = x[s];
-            x[s] = 0.0;
-            if (!isfinite(v)) bad = true;
-            if (r >= T.lo && r < T.hi) amax = fmax(amax, fabs(v));
-            d.Lx[lb + t] = v / xp;
-        }
-        amax = warp_max(amax);
-        bad = __any_sync(BK_FULL, bad);
-        if (__any_sync(BK_FULL, broken) && lane == 0) report_fail(d.status, c, BK_CODE_INTERNAL);
-        const bool ok = !bad && amax > 0.0 && fabs(xp) >= tau * amax;
+        bool ok = false, bad = false, broken = false;
+        if (!static_column(d, T, tid, x, c, epoch, budget, tau, lane, true, 0, ok, bad, broken)) return;
+        if (broken && lane == 0) report_internal(d.status, c, 41);
         __syncwarp();
         __threadfence();
         if (lane == 0) {
-            x[sp] = 0.0;
-            d.Ux[ub + uc - 1] = xp;
+            d.col_fail[c] = ok ? 0 : 1;
             if (!ok) {
                 atomicMin(d.task_fail + tid, c);
                 atomicExch(&d.status->static_fail, 1);

@@ -46,12 +46,15 @@ int32_t number_tree(int32_t height, int32_t &next, std::vector<int32_t> &first,
 
 }  // namespace
 
-// Column state of the in-node kernel: x over the L-space, a bitmap of own steps
-// and a bitmap of L-space rows.
+// Column state of the in-node kernel: x over the L-space, a bitmap of own steps,
+// a bitmap of L-space rows, a bitmap of own rows touched by a redo, and caches of
+// the node's own pivots and L offsets.
 size_t bk_task_smem_bytes(const bk_task &t)
 {
     size_t own = (size_t)(t.hi - t.lo);
-    return (size_t)t.lspace * 8 + ((own + 31) / 32) * 4 + (((size_t)t.lspace + 31) / 32) * 4 + 16;
+    // x, cached L offsets, step / row / touched bitmaps, cached pinv, prow, Lcnt
+    return (size_t)t.lspace * 8 + own * 8 + 2 * ((own + 31) / 32) * 4 + (((size_t)t.lspace + 31) / 32) * 4 +
+           3 * own * 4 + 16;
 }
 
 bool bk_task_fits_smem(const bk_task &t) { return bk_task_smem_bytes(t) <= bk_gp_smem_limit(); }
@@ -330,6 +333,9 @@ static void prefix_layout(bk_plan &pl)
     }
     pl.lcap = pl.sLbeg[(size_t)n];
     pl.ucap = pl.sUbeg[(size_t)n];
+    // a column that outgrows its region moves to a region of the spill pool
+    pl.lpool = pl.lcap / 2 + (1 << 20);
+    pl.upool = pl.ucap / 2 + (1 << 20);
 }
 
 // After an overflow: a column that overflowed gets its exact upper bound, the
@@ -374,25 +380,29 @@ void bk_plan_layout(bk_plan &pl)
     }
     // separators: A-hat scratch (dense over the L-space per column) and the
     // descendant-phase slice (x over the whole space plus two bitmaps)
+    // column-per-warp kernels (separator descendant phase, refactor rounds): one
+    // slice per warp holding x over a task's whole space and its step / row bitmaps
     int64_t ah = 0, ab = 0, slice = 0;
     std::vector<int64_t> level_cols(pl.level_tasks.size(), 0);
     for (auto &T : pl.tasks) {
         T.ahoff = T.aboff = 0;
-        if (T.sp_lo >= T.lo) continue;
         const int64_t own = T.hi - T.lo, words = (T.lspace + 31) / 32;
+        int64_t sl = (int64_t)T.space * 8 + ((int64_t)(T.hi - T.sp_lo) + 31) / 32 * 4 + words * 4;
+        slice = std::max(slice, (sl + 255) & ~(int64_t)255);
+        level_cols[(size_t)T.level] += own;
+        if (T.sp_lo >= T.lo) continue;
         T.ahoff = ah;
         T.aboff = ab;
         ah += own * T.lspace;
         ab += own * words;
-        int64_t sl = (int64_t)T.space * 8 + ((int64_t)(T.lo - T.sp_lo) + 31) / 32 * 4 + words * 4;
-        slice = std::max(slice, (sl + 255) & ~(int64_t)255);
-        level_cols[(size_t)T.level] += own;
     }
     pl.ahat_doubles = std::max<int64_t>(ah, 1);
     pl.ahat_words = std::max<int64_t>(ab, 1);
     pl.wsd_slice = std::max<int64_t>(slice, 256);
     int64_t wmax = 1;
     for (int64_t v : level_cols) wmax = std::max(wmax, v);
-    pl.wsd_warps = (int32_t)std::min<int64_t>(wmax, 152 * 16);
+    // at most 152 SMs x 16 warps, and at most 8 GiB of slices
+    const int64_t by_mem = std::max<int64_t>(1, ((int64_t)8 << 30) / pl.wsd_slice);
+    pl.wsd_warps = (int32_t)std::min<int64_t>(std::min<int64_t>(wmax, 152 * 16), by_mem);
     pl.ws_bytes = off;
 }
