@@ -151,6 +151,9 @@ int alloc_factors(basker_t h)
     h->d.lpool_end = pl.lcap + pl.lpool;
     h->d.upool_end = pl.ucap + pl.upool;
     TRY(dalloc(h, &h->d.Li, (size_t)h->d.lpool_end));
+    dfree(h, (void *)h->sd.Ls);
+    h->sd.Ls = nullptr;
+    TRY(dalloc(h, (int32_t **)&h->sd.Ls, (size_t)h->d.lpool_end));
     TRY(dalloc(h, &h->d.Lx, (size_t)h->d.lpool_end));
     TRY(dalloc(h, &h->d.Ui, (size_t)h->d.upool_end));
     TRY(dalloc(h, &h->d.Ux, (size_t)h->d.upool_end));
@@ -280,6 +283,7 @@ int setup_device(basker_t h)
     TRY(upload(h, (int32_t **)&s.offpos, h->sp.offpos));
     TRY(upload(h, (int64_t **)&s.acc_off, h->sp.acc_off));
     s.acc_stride = h->sp.acc_stride;
+    s.smem_bytes = h->sp.smem_bytes;
     TRY(upload_symbolic_pattern(h));
     h->schedule_valid = true;
     return BASKER_OK;
@@ -511,6 +515,9 @@ int factor_impl(basker_t h, const double *values, cudaStream_t s, bool refactor)
             }
         }
         if (st != BASKER_OK) { h->factored = false; return st == -1 ? BASKER_ERR_OOM : st; }
+        tbeg(h, KT_SOLVE, s, 1);
+        bk_launch_lsteps(h->d, (int *)h->sd.Ls, s);
+        tend(h, s);
         h->factored = true;
         return BASKER_OK;
     }
@@ -528,6 +535,9 @@ int factor_impl(basker_t h, const double *values, cudaStream_t s, bool refactor)
         if (st != -1) break;
     }
     if (st != BASKER_OK) { h->factored = false; return st == -1 ? BASKER_ERR_OOM : st; }
+    tbeg(h, KT_SOLVE, s, 1);
+    bk_launch_lsteps(h->d, (int *)h->sd.Ls, s);
+    tend(h, s);
     h->info.off_diagonal_pivots = h->h_status->offdiag;
     // with the natural pivots everywhere the pattern is the symbolic one, whose
     // static schedule is already on the device

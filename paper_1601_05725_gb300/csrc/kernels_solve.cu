@@ -70,59 +70,87 @@ __device__ __forceinline__ double init_row(const bk_dev &d, const bk_solve_dev &
     return v;
 }
 
-__device__ void forward_sweep(const bk_dev &d, const bk_solve_dev &s, const bk_task &T, int q,
+// Forward sweep over the node's own columns: wl holds the node's own rows (in
+// shared memory when they fit), acc its ancestors' rows.  The first 32 entries
+// of the next column are loaded while the current one is applied.
+__device__ void forward_sweep(const bk_dev &d, const bk_solve_dev &s, const bk_task &T, double *wl,
                               double *acc, int lane)
 {
-    double *w = s.w + (int64_t)q * d.n;
-    for (int k = T.lo; k < T.hi; k++) {
-        const double wk = __ldcg(w + k);
-        const int64_t lb = d.Lbeg[k];
-        const int lc = d.Lcnt[k];
-        for (int t = lane; t < lc; t += 32) {
-            const int i = d.pinv[d.Li[lb + t]];
-            const double l = d.Lx[lb + t];
-            if (i > k && i < T.hi) {
-                w[i] = fma(-l, wk, __ldcg(w + i));
+    const int lo = T.lo, hi = T.hi;
+    int64_t nb = d.Lbeg[lo];
+    int nc = d.Lcnt[lo];
+    int ni = lane < nc ? s.Ls[nb + lane] : -1;
+    double nv = lane < nc ? d.Lx[nb + lane] : 0.0;
+    for (int k = lo; k < hi; k++) {
+        const int64_t lb = nb;
+        const int lc = nc;
+        const int ci = ni;
+        const double cv = nv;
+        if (k + 1 < hi) {
+            nb = d.Lbeg[k + 1];
+            nc = d.Lcnt[k + 1];
+            ni = lane < nc ? s.Ls[nb + lane] : -1;
+            nv = lane < nc ? d.Lx[nb + lane] : 0.0;
+        }
+        const double wk = wl[k - lo];
+        auto apply = [&](int i, double l) {
+            if (i > k && i < hi) {
+                wl[i - lo] = fma(-l, wk, wl[i - lo]);
             } else {
                 const int a = acc ? anc_slot(T, i) : -1;
                 if (a >= 0) acc[a] = fma(l, wk, acc[a]);
                 else report_internal(d.status, k, 51);
             }
-        }
+        };
+        if (lane < lc) apply(ci, cv);
+        for (int t = 32 + lane; t < lc; t += 32) apply(s.Ls[lb + t], d.Lx[lb + t]);
         __syncwarp();
     }
 }
 
-__device__ void backward_sweep(const bk_dev &d, const bk_solve_dev &s, const bk_task &T, int q,
-                               double *x, int ldx, int lane)
+// Backward sweep: z_k = w_k / U(k,k), then w -= U(:,k) z_k; own rows in wl, the
+// descendants' rows (separators only) in global memory.
+__device__ void backward_sweep(const bk_dev &d, const bk_solve_dev &s, const bk_task &T, double *wl,
+                               double *wg, int lane)
 {
-    double *w = s.w + (int64_t)q * d.n;
-    for (int k = T.hi - 1; k >= T.lo; k--) {
-        const int64_t ub = d.Ubeg[k];
-        const int uc = d.Ucnt[k];
-        const double zk = __ldcg(w + k) / d.Ux[ub + uc - 1];
-        for (int t = lane; t < uc - 1; t += 32) {
-            const int i = d.Ui[ub + t];
-            w[i] = fma(-d.Ux[ub + t], zk, __ldcg(w + i));
+    const int lo = T.lo, hi = T.hi;
+    int64_t nb = d.Ubeg[hi - 1];
+    int nc = d.Ucnt[hi - 1];
+    int ni = lane < nc ? d.Ui[nb + lane] : -1;
+    double nv = lane < nc ? d.Ux[nb + lane] : 0.0;
+    for (int k = hi - 1; k >= lo; k--) {
+        const int64_t ub = nb;
+        const int uc = nc;
+        const int ci = ni;
+        const double cv = nv;
+        if (k > lo) {
+            nb = d.Ubeg[k - 1];
+            nc = d.Ucnt[k - 1];
+            ni = lane < nc ? d.Ui[nb + lane] : -1;
+            nv = lane < nc ? d.Ux[nb + lane] : 0.0;
         }
+        const double zk = wl[k - lo] / d.Ux[ub + uc - 1];
+        auto apply = [&](int i, double u) {
+            if (i >= lo) wl[i - lo] = fma(-u, zk, wl[i - lo]);
+            else wg[i] = fma(-u, zk, __ldcg(wg + i));
+        };
+        if (lane < uc - 1) apply(ci, cv);
+        for (int t = 32 + lane; t < uc - 1; t += 32) apply(d.Ui[ub + t], d.Ux[ub + t]);
         __syncwarp();
-        if (lane == 0) w[k] = zk;
+        if (lane == 0) wl[k - lo] = zk;
         __syncwarp();
     }
-    for (int k = T.lo + lane; k < T.hi; k += 32) x[(int64_t)q * ldx + d.Q[k]] = __ldcg(w + k);
 }
 
-__global__ void __launch_bounds__(128) bk_solve_kernel(bk_dev d, bk_solve_dev s, int32_t nrhs,
-                                                       const double *__restrict__ b, int32_t ldb,
-                                                       double *x, int32_t ldx, int32_t epoch,
-                                                       long long budget)
+__global__ void __launch_bounds__(32) bk_solve_kernel(bk_dev d, bk_solve_dev s, int32_t nrhs,
+                                                      const double *__restrict__ b, int32_t ldb,
+                                                      double *x, int32_t ldx, int32_t epoch,
+                                                      long long budget)
 {
-    __shared__ bk_task Ts[4];
-    __shared__ bk_task Us[4];
-    const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
-    bk_task &T = Ts[wib];
-    bk_task &U = Us[wib];
+    extern __shared__ __align__(16) double sw[];
+    __shared__ bk_task T;
+    __shared__ bk_task U;
+    const int lane = threadIdx.x;
     for (;;) {
         int k = 0;
         if (lane == 0) k = atomicAdd(d.counter + 2, 1);
@@ -131,19 +159,20 @@ __global__ void __launch_bounds__(128) bk_solve_kernel(bk_dev d, bk_solve_dev s,
         const bk_sitem it = s.items[k];
         if (!wait_items(d, s, it, epoch, budget, lane)) return;
         load_task(T, d.tasks + it.task, lane);
+        const int nown = T.hi - T.lo;
+        const int na = it.type == BK_ITEM_BLOCK ? 0 : T.lspace - nown;
+        const bool fits = (int64_t)(nown + na) * 8 <= s.smem_bytes;
         for (int q = 0; q < nrhs; q++) {
             double *w = s.w + (int64_t)q * d.n;
+            double *wl = fits ? sw : w + T.lo;
+            double *accg = s.acc + (int64_t)q * s.acc_stride + s.acc_off[it.task];
+            double *acc = it.type == BK_ITEM_FWD ? (fits ? sw + nown : accg) : nullptr;
             if (it.type == BK_ITEM_BLOCK || it.type == BK_ITEM_FWD) {
-                for (int kk = T.lo + lane; kk < T.hi; kk += 32) {
-                    double v = init_row(d, s, kk, q, b, ldb);
-                    w[kk] = v;
-                }
-                double *acc = nullptr;
-                if (it.type == BK_ITEM_FWD) {
-                    acc = s.acc + (int64_t)q * s.acc_stride + s.acc_off[it.task];
-                    const int na = T.lspace - (T.hi - T.lo);
+                for (int kk = T.lo + lane; kk < T.hi; kk += 32) wl[kk - T.lo] = init_row(d, s, kk, q, b, ldb);
+                if (acc)
                     for (int a = lane; a < na; a += 32) acc[a] = 0.0;
-                    __syncwarp();
+                __syncwarp();
+                if (it.type == BK_ITEM_FWD) {
                     // contributions of every descendant (fixed order: postorder)
                     for (int u = it.desc_beg; u < it.desc_end; u++) {
                         const int ut = s.desc[u];
@@ -151,22 +180,45 @@ __global__ void __launch_bounds__(128) bk_solve_kernel(bk_dev d, bk_solve_dev s,
                         const double *au = s.acc + (int64_t)q * s.acc_stride + s.acc_off[ut];
                         for (int kk = T.lo + lane; kk < T.hi; kk += 32) {
                             const int a = anc_slot(U, kk);
-                            if (a >= 0) w[kk] -= __ldcg(au + a);
+                            if (a >= 0) wl[kk - T.lo] -= __ldcg(au + a);
                         }
                         __syncwarp();
                     }
                 }
-                __syncwarp();
-                forward_sweep(d, s, T, q, acc, lane);
-                if (it.type == BK_ITEM_BLOCK) backward_sweep(d, s, T, q, x, ldx, lane);
+                forward_sweep(d, s, T, wl, acc, lane);
+                if (it.type == BK_ITEM_BLOCK) backward_sweep(d, s, T, wl, w, lane);
+                if (fits && acc)
+                    for (int a = lane; a < na; a += 32) accg[a] = acc[a];
             } else {
-                backward_sweep(d, s, T, q, x, ldx, lane);
+                // own rows were written by other warps: read them through L2 (and
+                // rewrite them in place when they stay in global memory)
+                for (int kk = T.lo + lane; kk < T.hi; kk += 32) wl[kk - T.lo] = __ldcg(w + kk);
+                __syncwarp();
+                backward_sweep(d, s, T, wl, w, lane);
             }
+            __syncwarp();
+            if (fits)
+                for (int kk = T.lo + lane; kk < T.hi; kk += 32) w[kk] = wl[kk - T.lo];
+            if (it.type != BK_ITEM_FWD)
+                for (int kk = T.lo + lane; kk < T.hi; kk += 32) x[(int64_t)q * ldx + d.Q[kk]] = wl[kk - T.lo];
             __syncwarp();
         }
         __threadfence();
         __syncwarp();
         if (lane == 0) st_release(s.item_done + k, epoch);
+    }
+}
+
+// L's row indices as pivot steps (for the solve), after every factorization.
+__global__ void bk_lsteps_kernel(bk_dev d, int *Ls)
+{
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int c = warp; c < d.n; c += nwarps) {
+        const int64_t lb = d.Lbeg[c];
+        const int lc = d.Lcnt[c];
+        for (int t = lane; t < lc; t += 32) Ls[lb + t] = d.pinv[d.Li[lb + t]];
     }
 }
 
@@ -179,7 +231,20 @@ void bk_launch_solve(const bk_dev &d, const bk_solve_dev &s, int32_t nrhs, const
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int warps = std::min<int>(s.nitems, std::max(1, sms) * 8);
-    bk_solve_kernel<<<(warps + 3) / 4, 128, 0, (cudaStream_t)stream>>>(d, s, nrhs, b, ldb, x, ldx, epoch,
-                                                                        budget);
+    static int attr_set = -1;
+    if (attr_set != (int)s.smem_bytes) {
+        cudaFuncSetAttribute(bk_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.smem_bytes);
+        attr_set = (int)s.smem_bytes;
+    }
+    const int per_sm = s.smem_bytes > 0 ? std::max<int>(1, std::min<int>(16, (int)(200 * 1024 / s.smem_bytes))) : 16;
+    const int ctas = std::min<int>(s.nitems, std::max(1, sms) * per_sm);
+    bk_solve_kernel<<<ctas, 32, (size_t)s.smem_bytes, (cudaStream_t)stream>>>(d, s, nrhs, b, ldb, x, ldx, epoch,
+                                                                               budget);
+}
+
+void bk_launch_lsteps(const bk_dev &d, int *Ls, void *stream)
+{
+    if (d.n <= 0) return;
+    const int blocks = std::max(1, std::min((d.n + 7) / 8, 152 * 8));
+    bk_lsteps_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(d, Ls);
 }

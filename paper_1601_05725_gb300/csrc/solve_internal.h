@@ -26,6 +26,8 @@ struct bk_solve_dev {
     int64_t acc_stride;                    // slots per right-hand side
     double *acc;
     double *w;                             // n x nrhs, indexed by pivot step
+    const int32_t *Ls;                     // L's row indices as pivot steps
+    int64_t smem_bytes;                    // dynamic shared memory of the solve kernel
 };
 
 struct bk_solve_plan {
@@ -33,8 +35,10 @@ struct bk_solve_plan {
     std::vector<int32_t> deps, desc, offp, offj, offpos;
     std::vector<int64_t> acc_off;
     int64_t acc_stride = 0;
+    int64_t smem_bytes = 0;                // largest item (own rows + ancestor buffer), capped
 };
 
 void bk_solve_plan_build(const bk_plan &pl, bk_solve_plan &sp);
+void bk_launch_lsteps(const bk_dev &d, int *Ls, void *stream);
 void bk_launch_solve(const bk_dev &d, const bk_solve_dev &s, int32_t nrhs, const double *b, int32_t ldb,
                      double *x, int32_t ldx, int32_t epoch, long long budget, void *stream);

@@ -106,4 +106,14 @@ void bk_solve_plan_build(const bk_plan &pl, bk_solve_plan &sp)
         if (pl.tasks[t].node >= 0) off += pl.tasks[t].lspace - (pl.tasks[t].hi - pl.tasks[t].lo);
     }
     sp.acc_stride = std::max<int64_t>(off, 1);
+    // shared memory of one solve item: its own rows and its ancestor buffer
+    int64_t need = 0;
+    const int64_t cap = 200 * 1024;
+    for (const auto &it : sp.items) {
+        const bk_task &T = pl.tasks[(size_t)it.task];
+        const int64_t own = T.hi - T.lo, anc = it.type == BK_ITEM_BLOCK ? 0 : T.lspace - own;
+        const int64_t b = 8 * (own + anc);
+        if (b <= cap) need = std::max(need, b);
+    }
+    sp.smem_bytes = (need + 15) & ~(int64_t)15;
 }
