@@ -108,11 +108,12 @@ __global__ void __launch_bounds__(128) bk_dd_kernel(bk_dev d, const int32_t *__r
         }
         int64_t ub = d.Ubeg[c], ue = d.Uend[c];
         int64_t lb = d.Lbeg[c], le = d.Lend[c];
-        // Recompute on the stored pattern unless the pattern may change: a row of
-        // it was touched (this round; or, in a separator's first round, anywhere
-        // below during this refactorization), or one of its steps was recomputed
-        // by the reach (checked as the steps are reached).
-        int mode = resolve ? 2 : 1;
+        // A column is kept (resolve rounds), recomputed on its stored pattern, or
+        // recomputed by the reach when its pattern may change: a row of it was
+        // touched (this round; or, in a separator's first round, anywhere below
+        // during this refactorization), or one of its steps was recomputed by the
+        // reach (checked as the steps are reached).
+        int mode = resolve ? 2 : ((fl & BK_DD_DESC) ? 1 : 0);
         if (!resolve) {
             if (lane == 0) {
                 const int r = d.prow[c];
@@ -135,6 +136,46 @@ __global__ void __launch_bounds__(128) bk_dd_kernel(bk_dev d, const int32_t *__r
                 if ((fl & BK_DD_DESC) && __ldcg(d.touch_ref + r) == refno) mode = 2;
             }
             mode = warp_max_i(mode);
+            // a column that rejected its pivot in the previous round is revalidated
+            if (mode == 0 && __shfl_sync(BK_FULL, lane == 0 ? d.col_fail[c] : 0, 0)) mode = 1;
+            if (mode == 0 && (fl & BK_DD_RESOLVE)) {
+                // keep the column unless a step of it recomputed in this round; its
+                // steps are examined lowest first, deciding at the first done step
+                // that was recomputed, waiting only for the lowest unfinished one
+                int verdict = 0;                      // 0 keep, 1 stored pattern, 2 reach
+                for (int k0 = 0; k0 < uc - 1 && verdict == 0; k0 += 32) {
+                    const int q = k0 + lane;
+                    int j = -1;
+                    if (q < uc - 1) {
+                        const int jj = d.Ui[ub + q];
+                        if (jj >= s0 && jj < c && d.col_task[jj] == tid) j = jj;
+                    }
+                    uint32_t todo = __ballot_sync(BK_FULL, j >= 0);
+                    while (todo && verdict == 0) {
+                        bool done = false;
+                        int v = 0;
+                        if ((todo >> lane) & 1u) {
+                            done = ld_acquire(d.done + j) == epoch;
+                            if (done) v = __ldcg(d.pchg_ep + j) == epoch ? 2 : (__ldcg(d.dirty_ep + j) == epoch ? 1 : 0);
+                        }
+                        verdict = warp_max_i(v);
+                        if (verdict) break;
+                        todo &= ~__ballot_sync(BK_FULL, done);
+                        if (todo) {
+                            const int first = __ffs(todo) - 1;
+                            const int jw = __shfl_sync(BK_FULL, j, first);
+                            int okw = lane == 0 ? (int)lane_wait(d, d.done + jw, epoch, budget) : 1;
+                            if (!__shfl_sync(BK_FULL, okw, 0)) return;
+                        }
+                    }
+                }
+                mode = verdict;
+                if (mode == 0) {
+                    __syncwarp();
+                    if (lane == 0) st_release(d.done + c, epoch);
+                    continue;
+                }
+            }
             if (mode == 1) {
                 bool ok = false, bad = false, broken = false, aborted = false;
                 double *xs = reinterpret_cast<double *>(slice);
