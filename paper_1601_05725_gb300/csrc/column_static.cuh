@@ -202,3 +202,193 @@ __device__ __forceinline__ bool static_column(const bk_dev &d, const bk_task &T,
 }
 
 }  // namespace bk
+
+namespace bk {
+
+// The stored-pattern pass proper.  While it runs no pattern changes: only the
+// values of L and U are rewritten.  So the rows of every L(:,j) and of L(:,c) can
+// be read ahead, and the only reads that must follow a step's flag are its
+// values L(j+1:n, j).  Per step: the rows of L(:,j) (read during the previous
+// step), their x values and x(prow j) are loaded together once the previous
+// step's updates are stored; after the flag, L(:,j)'s values; then one fma per
+// entry in ascending step order (the same per-entry operation order as
+// Algorithm 1's update).  The first FIX_PF * 32 entries of a column live in
+// registers; longer columns take the rest in batches.  Outputs as static_column.
+constexpr int FIX_PF = 8;
+
+__device__ __forceinline__ bool fixed_column(const bk_dev &d, const bk_task &T, double *x, int c, int epoch,
+                                             long long budget, double tau, int lane, bool &ok_out, bool &bad_out,
+                                             bool &broken_out)
+{
+    const int base = T.sp_lo;
+    const int own_lo = T.lo - base, own_hi = T.hi - base;
+    bool broken = false, bad = false;
+    const int e1 = d.Bp[c + 1];
+    for (int e = d.dstart[c] + lane; e < e1; e += 32) {
+        const int s = slot_of(T, base, d.Bi[e]);
+        if (s < 0) { broken = true; continue; }
+        x[s] = d.Bx[e];
+    }
+    // rows of L(:,c) and the pivot row, for the selection at the end
+    const int64_t lb = d.Lbeg[c];
+    const int lc = d.Lcnt[c];
+    int fs[FIX_PF];
+#pragma unroll
+    for (int u = 0; u < FIX_PF; u++) {
+        const int q = lane + 32 * u;
+        fs[u] = -2;
+        if (q < lc) {
+            fs[u] = slot_of(T, base, d.Li[lb + q]);
+            if (fs[u] < 0) broken = true;
+        }
+    }
+    int sp_c = slot_of(T, base, __ldcg(d.prow + c));
+    if (sp_c < 0) { broken = true; sp_c = 0; }
+    __syncwarp();
+    const int64_t ub = d.Ubeg[c];
+    const int nsteps = d.Ucnt[c] - 1;
+    for (int k0 = 0; k0 < nsteps; k0 += 32) {
+        const int nin = min(32, nsteps - k0);
+        int j_l = 0, sp_l = -1, jc_l = 0;
+        int64_t jl_l = 0;
+        bool done_l = true;
+        if (lane < nin) {
+            j_l = d.Ui[ub + k0 + lane];
+            done_l = ld_acquire(d.done + j_l) == epoch;
+            sp_l = slot_of(T, base, __ldcg(d.prow + j_l));
+            jl_l = __ldcg(d.Lbeg + j_l);
+            jc_l = __ldcg(d.Lcnt + j_l);
+            if (sp_l < 0) broken = true;
+        }
+        const uint32_t pending = __ballot_sync(BK_FULL, !done_l);
+        // rows (and, for a finished step, values) of the chunk's first step
+        int rr[FIX_PF];
+        double ll[FIX_PF];
+        {
+            const int64_t jl0 = __shfl_sync(BK_FULL, jl_l, 0);
+            const int jc0 = __shfl_sync(BK_FULL, jc_l, 0);
+#pragma unroll
+            for (int u = 0; u < FIX_PF; u++) {
+                const int q = lane + 32 * u;
+                rr[u] = q < jc0 ? __ldcg(d.Li + jl0 + q) : -1;
+                ll[u] = (q < jc0 && !(pending & 1u)) ? __ldcg(d.Lx + jl0 + q) : 0.0;
+            }
+        }
+        for (int t = 0; t < nin; ++t) {
+            const int j = __shfl_sync(BK_FULL, j_l, t);
+            const int sp = __shfl_sync(BK_FULL, sp_l, t);
+            const int64_t jl = __shfl_sync(BK_FULL, jl_l, t);
+            const int jc = __shfl_sync(BK_FULL, jc_l, t);
+            // x(prow j) and the x values under L(:,j); all earlier steps are stored
+            int ss[FIX_PF];
+            double xv[FIX_PF];
+            const double m = sp >= 0 ? x[sp] : 0.0;
+#pragma unroll
+            for (int u = 0; u < FIX_PF; u++) {
+                ss[u] = rr[u] >= 0 ? slot_of(T, base, rr[u]) : -1;
+                if (rr[u] >= 0 && ss[u] < 0) broken = true;
+                xv[u] = ss[u] >= 0 ? x[ss[u]] : 0.0;
+            }
+            if ((pending >> t) & 1u) {
+                if (!flag_wait(d, d.done + j, epoch, budget, lane)) return false;
+#pragma unroll
+                for (int u = 0; u < FIX_PF; u++) {
+                    const int q = lane + 32 * u;
+                    if (q < jc) ll[u] = __ldcg(d.Lx + jl + q);
+                }
+            }
+            // the next step's rows and, if it has finished, values
+            int rn[FIX_PF];
+            double ln[FIX_PF];
+            {
+                const int tn = t + 1 < nin ? t + 1 : t;
+                const int64_t jln = __shfl_sync(BK_FULL, jl_l, tn);
+                const int jcn = t + 1 < nin ? __shfl_sync(BK_FULL, jc_l, tn) : 0;
+                const bool pn = (pending >> tn) & 1u;
+#pragma unroll
+                for (int u = 0; u < FIX_PF; u++) {
+                    const int q = lane + 32 * u;
+                    rn[u] = q < jcn ? __ldcg(d.Li + jln + q) : -1;
+                    ln[u] = (q < jcn && !pn) ? __ldcg(d.Lx + jln + q) : 0.0;
+                }
+            }
+            if (sp >= 0) {
+                __syncwarp();
+                if (lane == 0) {
+                    x[sp] = 0.0;
+                    d.Ux[ub + k0 + t] = m;
+                }
+                if (!isfinite(m)) bad = true;
+#pragma unroll
+                for (int u = 0; u < FIX_PF; u++)
+                    if (ss[u] >= 0) x[ss[u]] = fma(-ll[u], m, xv[u]);
+                // entries past the register window, in batches
+                for (int q0 = 32 * FIX_PF; q0 < jc; q0 += 32 * FIX_PF) {
+                    int sb[FIX_PF];
+                    double lb2[FIX_PF], xb[FIX_PF];
+#pragma unroll
+                    for (int u = 0; u < FIX_PF; u++) {
+                        const int q = q0 + lane + 32 * u;
+                        sb[u] = -1;
+                        lb2[u] = 0.0;
+                        if (q < jc) {
+                            sb[u] = slot_of(T, base, __ldcg(d.Li + jl + q));
+                            lb2[u] = __ldcg(d.Lx + jl + q);
+                            if (sb[u] < 0) broken = true;
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < FIX_PF; u++) xb[u] = sb[u] >= 0 ? x[sb[u]] : 0.0;
+#pragma unroll
+                    for (int u = 0; u < FIX_PF; u++)
+                        if (sb[u] >= 0) x[sb[u]] = fma(-lb2[u], m, xb[u]);
+                }
+            }
+            __syncwarp();
+#pragma unroll
+            for (int u = 0; u < FIX_PF; u++) {
+                rr[u] = rn[u];
+                ll[u] = ln[u];
+            }
+        }
+    }
+    // Algorithm 1's pivot selection, validated for the stored pivot row
+    const double xp = x[sp_c];
+    double amax = fabs(xp);
+    if (!isfinite(xp)) bad = true;
+    double v[FIX_PF];
+#pragma unroll
+    for (int u = 0; u < FIX_PF; u++) v[u] = fs[u] >= 0 ? x[fs[u]] : 0.0;
+#pragma unroll
+    for (int u = 0; u < FIX_PF; u++) {
+        if (fs[u] < 0) continue;
+        if (!isfinite(v[u])) bad = true;
+        if (fs[u] >= own_lo && fs[u] < own_hi) amax = fmax(amax, fabs(v[u]));
+        x[fs[u]] = 0.0;
+        d.Lx[lb + lane + 32 * u] = v[u] / xp;
+    }
+    for (int t = 32 * FIX_PF + lane; t < lc; t += 32) {
+        const int s = slot_of(T, base, d.Li[lb + t]);
+        if (s < 0) { broken = true; continue; }
+        const double w = x[s];
+        x[s] = 0.0;
+        if (!isfinite(w)) bad = true;
+        if (s >= own_lo && s < own_hi) amax = fmax(amax, fabs(w));
+        d.Lx[lb + t] = w / xp;
+    }
+    amax = warp_max(amax);
+    bad = __any_sync(BK_FULL, bad);
+    broken = __any_sync(BK_FULL, broken);
+    __syncwarp();
+    if (lane == 0) {
+        x[sp_c] = 0.0;
+        d.Ux[ub + nsteps] = xp;
+    }
+    __syncwarp();
+    ok_out = !bad && !broken && amax > 0.0 && fabs(xp) >= tau * amax;
+    bad_out = bad;
+    broken_out = broken;
+    return true;
+}
+
+}  // namespace bk

@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(128) bk_static_kernel(bk_dev d, int32_t ncols,
             cur = tid;
         }
         bool ok = false, bad = false, broken = false;
-        if (!static_column(d, T, tid, x, c, epoch, budget, tau, lane, true, 0, ok, bad, broken)) return;
+        if (!fixed_column(d, T, x, c, epoch, budget, tau, lane, ok, bad, broken)) return;
         if (broken && lane == 0) report_internal(d.status, c, 41);
         __syncwarp();
         __threadfence();
@@ -61,7 +61,6 @@ __global__ void __launch_bounds__(128) bk_static_kernel(bk_dev d, int32_t ncols,
                 atomicMin(d.task_fail + tid, c);
                 atomicExch(&d.status->static_fail, 1);
             }
-            __threadfence();
             st_release(d.done + c, epoch);
         }
     }
