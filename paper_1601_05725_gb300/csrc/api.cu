@@ -233,6 +233,7 @@ int setup_device(basker_t h)
     TRY(dalloc(h, &d.dcnt, (size_t)n, true));
     d.wsd_slice = pl.wsd_slice;
     d.wsd_warps = pl.wsd_warps;
+    d.dd_words = pl.dd_words;
     TRY(dalloc(h, &d.wsd, (size_t)(pl.wsd_slice * pl.wsd_warps), true));
     d.sx_warps = bk_static_blocks() * 4;
     d.sx_stride = ((int64_t)pl.max_space + 31) & ~(int64_t)31;

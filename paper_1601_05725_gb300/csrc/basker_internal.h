@@ -97,6 +97,7 @@ struct bk_dev {
     unsigned char *wsd;              // descendant-phase workspace, one slice per warp
     int64_t wsd_slice;               // bytes per slice
     int32_t wsd_warps;
+    int32_t dd_words;                // reach bitmaps per warp in shared memory (0: in the slice)
     double *sx;                      // static kernel: per-warp dense x slices
     int64_t sx_stride;               // doubles per warp slice
     int32_t sx_warps;
@@ -125,6 +126,7 @@ struct bk_plan {
     int64_t ahat_doubles = 0, ahat_words = 0;         // separator A-hat scratch
     int64_t wsd_slice = 0;                            // descendant-phase slice (bytes)
     int32_t wsd_warps = 0;                            // descendant-phase warps (max columns of a level)
+    int32_t dd_words = 0;                             // shared-memory reach bitmaps per warp (words)
     int32_t max_space = 0;
     int32_t symbolic_singular = -1;                   // first column without a structural pivot
     double slack = 0.5;

@@ -4,16 +4,8 @@
 // x(prow j), then x -= L(:,j) U(j,c); finally U(c,c) = x(prow c) and
 // L(:,c) = x / U(c,c) over the stored rows of L(:,c).  x is the warp's dense slice
 // over the task's space (base = sp_lo); it is zero outside the column before and
-// after.  Steps go in chunks of 32: lane t holds step k0+t's pivot slot, L(:,j)
-// extent and whether its flag was already set; the first 32 entries of the next
-// step's L(:,j) are loaded while the current step is applied, and the rest of a
-// long L(:,j) four independent loads at a time.  A step is waited for (flag ==
-// epoch) when wait_all, or when it is a column of the same task at or after
-// wait_lo.  Returns false when a wait ran out of budget.  Outputs: ok (Algorithm
-// 1's pivot selection keeps prow[c]), bad (a non-finite value), broken (an index
-// outside the space; never valid input).  With pchg != nullptr, a waited-for step
-// j with pchg[j] == epoch (its pattern may have changed) stops the computation:
-// x is cleared over the stored pattern and aborted is set.
+// after.  Used by the stored-pattern pass of a refactorization and by the rounds
+// that follow it (pattern_column below).
 #pragma once
 
 #include "basker_internal.h"
@@ -57,168 +49,29 @@ __device__ __forceinline__ void clear_stored(const bk_dev &d, const bk_task &T, 
     __syncwarp();
 }
 
-__device__ __forceinline__ bool static_column(const bk_dev &d, const bk_task &T, int tid, double *x, int c,
-                                              int epoch, long long budget, double tau, int lane, bool wait_all,
-                                              int wait_lo, bool &ok_out, bool &bad_out, bool &broken_out,
-                                              const int *pchg = nullptr, bool *aborted = nullptr)
-{
-    const int base = T.sp_lo;
-    const int e1 = d.Bp[c + 1];
-    bool broken = false, bad = false;
-    for (int e = d.dstart[c] + lane; e < e1; e += 32) {
-        const int s = slot_of(T, base, d.Bi[e]);
-        if (s < 0) { broken = true; continue; }
-        x[s] = d.Bx[e];
-    }
-    __syncwarp();
-    const int64_t ub = d.Ubeg[c];
-    const int nsteps = d.Ucnt[c] - 1;
-    for (int k0 = 0; k0 < nsteps; k0 += 32) {
-        const int nin = min(32, nsteps - k0);
-        int j_l = 0, sp_l = 0, jc_l = 0;
-        int64_t jl_l = 0;
-        bool done_l = true, changed = false;
-        if (lane < nin) {
-            j_l = d.Ui[ub + k0 + lane];
-            const bool must = wait_all || (j_l >= wait_lo && d.col_task[j_l] == tid);
-            done_l = !must || ld_acquire(d.done + j_l) == epoch;
-            if (pchg && must && done_l && __ldcg(pchg + j_l) == epoch) changed = true;
-            sp_l = slot_of(T, base, __ldcg(d.prow + j_l));
-            jl_l = __ldcg(d.Lbeg + j_l);
-            jc_l = __ldcg(d.Lcnt + j_l);
-            if (sp_l < 0) broken = true;
-        }
-        const uint32_t pending = __ballot_sync(BK_FULL, !done_l);
-        if (__any_sync(BK_FULL, changed)) {
-            clear_stored(d, T, x, c, lane);
-            *aborted = true;
-            return true;
-        }
-        __syncwarp();
-        int nr = 0;
-        double nl = 0.0;
-        {
-            const int64_t jl0 = __shfl_sync(BK_FULL, jl_l, 0);
-            const int jc0 = __shfl_sync(BK_FULL, jc_l, 0);
-            if (lane < jc0 && !(pending & 1u)) {
-                nr = __ldcg(d.Li + jl0 + lane);
-                nl = __ldcg(d.Lx + jl0 + lane);
-            }
-        }
-        for (int t = 0; t < nin; ++t) {
-            const int j = __shfl_sync(BK_FULL, j_l, t);
-            const int sp = __shfl_sync(BK_FULL, sp_l, t);
-            int64_t jl = __shfl_sync(BK_FULL, jl_l, t);
-            int jc = __shfl_sync(BK_FULL, jc_l, t);
-            int cr = nr;
-            double cl = nl;
-            if ((pending >> t) & 1u) {
-                // the step's column had not finished when the chunk started
-                if (!flag_wait(d, d.done + j, epoch, budget, lane)) return false;
-                if (pchg && __ldcg(pchg + j) == epoch) {
-                    clear_stored(d, T, x, c, lane);
-                    *aborted = true;
-                    return true;
-                }
-                jl = __ldcg(d.Lbeg + j);                 // it may have moved to the spill pool
-                jc = __ldcg(d.Lcnt + j);
-                if (lane < jc) {
-                    cr = __ldcg(d.Li + jl + lane);
-                    cl = __ldcg(d.Lx + jl + lane);
-                }
-            }
-            if (t + 1 < nin) {
-                const int64_t jln = __shfl_sync(BK_FULL, jl_l, t + 1);
-                const int jcn = __shfl_sync(BK_FULL, jc_l, t + 1);
-                if (lane < jcn && !((pending >> (t + 1)) & 1u)) {
-                    nr = __ldcg(d.Li + jln + lane);
-                    nl = __ldcg(d.Lx + jln + lane);
-                }
-            }
-            if (sp < 0) continue;
-            const double m = x[sp];
-            __syncwarp();
-            if (lane == 0) {
-                x[sp] = 0.0;
-                d.Ux[ub + k0 + t] = m;
-            }
-            if (!isfinite(m)) bad = true;
-            if (lane < jc) {
-                const int s0 = slot_of(T, base, cr);
-                if (s0 < 0) broken = true;
-                else x[s0] = fma(-cl, m, x[s0]);
-            }
-            for (int t0 = 32 + lane; t0 < jc; t0 += 128) {
-                int rr[4];
-                double ll[4];
-#pragma unroll
-                for (int u = 0; u < 4; u++) {
-                    const int q = t0 + 32 * u;
-                    rr[u] = q < jc ? __ldcg(d.Li + jl + q) : -1;
-                    ll[u] = q < jc ? __ldcg(d.Lx + jl + q) : 0.0;
-                }
-#pragma unroll
-                for (int u = 0; u < 4; u++) {
-                    if (rr[u] < 0) continue;
-                    const int s1 = slot_of(T, base, rr[u]);
-                    if (s1 < 0) { broken = true; continue; }
-                    x[s1] = fma(-ll[u], m, x[s1]);
-                }
-            }
-            __syncwarp();
-        }
-    }
-    const int p = __ldcg(d.prow + c);
-    int sp = slot_of(T, base, p);
-    if (sp < 0) { broken = true; sp = 0; }
-    const double xp = x[sp];
-    double amax = fabs(xp);
-    if (!isfinite(xp)) bad = true;
-    const int64_t lb = d.Lbeg[c];
-    const int lc = d.Lcnt[c];
-    for (int t = lane; t < lc; t += 32) {
-        const int r = d.Li[lb + t];
-        const int s = slot_of(T, base, r);
-        if (s < 0) { broken = true; continue; }
-        const double v = x[s];
-        x[s] = 0.0;
-        if (!isfinite(v)) bad = true;
-        if (r >= T.lo && r < T.hi) amax = fmax(amax, fabs(v));
-        d.Lx[lb + t] = v / xp;
-    }
-    amax = warp_max(amax);
-    bad = __any_sync(BK_FULL, bad);
-    broken = __any_sync(BK_FULL, broken);
-    __syncwarp();
-    if (lane == 0) {
-        x[sp] = 0.0;
-        d.Ux[ub + nsteps] = xp;
-    }
-    __syncwarp();
-    ok_out = !bad && !broken && amax > 0.0 && fabs(xp) >= tau * amax;
-    bad_out = bad;
-    broken_out = broken;
-    return true;
-}
 
-}  // namespace bk
-
-namespace bk {
-
-// The stored-pattern pass proper.  While it runs no pattern changes: only the
-// values of L and U are rewritten.  So the rows of every L(:,j) and of L(:,c) can
-// be read ahead, and the only reads that must follow a step's flag are its
-// values L(j+1:n, j).  Per step: the rows of L(:,j) (read during the previous
-// step), their x values and x(prow j) are loaded together once the previous
-// step's updates are stored; after the flag, L(:,j)'s values; then one fma per
-// entry in ascending step order (the same per-entry operation order as
-// Algorithm 1's update).  The first FIX_PF * 32 entries of a column live in
-// registers; longer columns take the rest in batches.  Outputs as static_column.
+// Column c on its stored pattern.  Within a pass no stored pattern changes
+// except, in a refactorization round, that of a step recomputed by the reach,
+// which is flagged (pchg[j] == epoch) before its done flag is released.  So the
+// rows of every L(:,j) and of L(:,c) are read ahead, and the only reads that must
+// follow a step's flag are its values L(j+1:n, j); a flagged step stops the
+// computation instead (x is cleared over the stored pattern, aborted is set).
+// Per step: the rows of L(:,j) (read during the previous step), their x values
+// and x(prow j) are loaded together once the previous step's updates are stored;
+// after the flag, L(:,j)'s values; then one fma per entry in ascending step order
+// (the same per-entry operation order as Algorithm 1's update).  The first
+// FIX_PF * 32 entries of a column live in registers; longer columns take the rest
+// in batches.  A step is waited for (done[j] == epoch) when wait_all, or when it
+// is a column of the same task at or after wait_lo.  Returns false when a wait
+// ran out of budget.  Outputs: ok (Algorithm 1's pivot selection keeps prow[c]),
+// bad (a non-finite value), broken (an index outside the space; never valid
+// input).
 constexpr int FIX_PF = 8;
 
-__device__ __forceinline__ bool fixed_column(const bk_dev &d, const bk_task &T, double *x, int c, int epoch,
-                                             long long budget, double tau, int lane, bool &ok_out, bool &bad_out,
-                                             bool &broken_out)
+__device__ __forceinline__ bool pattern_column(const bk_dev &d, const bk_task &T, int tid, double *x, int c,
+                                               int epoch, long long budget, double tau, int lane, bool wait_all,
+                                               int wait_lo, bool &ok_out, bool &bad_out, bool &broken_out,
+                                               const int *pchg = nullptr, bool *aborted = nullptr)
 {
     const int base = T.sp_lo;
     const int own_lo = T.lo - base, own_hi = T.hi - base;
@@ -251,16 +104,23 @@ __device__ __forceinline__ bool fixed_column(const bk_dev &d, const bk_task &T, 
         const int nin = min(32, nsteps - k0);
         int j_l = 0, sp_l = -1, jc_l = 0;
         int64_t jl_l = 0;
-        bool done_l = true;
+        bool done_l = true, changed = false;
         if (lane < nin) {
             j_l = d.Ui[ub + k0 + lane];
-            done_l = ld_acquire(d.done + j_l) == epoch;
+            const bool must = wait_all || (j_l >= wait_lo && d.col_task[j_l] == tid);
+            done_l = !must || ld_acquire(d.done + j_l) == epoch;
+            if (pchg && must && done_l && __ldcg(pchg + j_l) == epoch) changed = true;
             sp_l = slot_of(T, base, __ldcg(d.prow + j_l));
             jl_l = __ldcg(d.Lbeg + j_l);
             jc_l = __ldcg(d.Lcnt + j_l);
             if (sp_l < 0) broken = true;
         }
         const uint32_t pending = __ballot_sync(BK_FULL, !done_l);
+        if (__any_sync(BK_FULL, changed)) {
+            clear_stored(d, T, x, c, lane);
+            *aborted = true;
+            return true;
+        }
         // rows (and, for a finished step, values) of the chunk's first step
         int rr[FIX_PF];
         double ll[FIX_PF];
@@ -291,6 +151,11 @@ __device__ __forceinline__ bool fixed_column(const bk_dev &d, const bk_task &T, 
             }
             if ((pending >> t) & 1u) {
                 if (!flag_wait(d, d.done + j, epoch, budget, lane)) return false;
+                if (pchg && __ldcg(pchg + j) == epoch) {
+                    clear_stored(d, T, x, c, lane);
+                    *aborted = true;
+                    return true;
+                }
 #pragma unroll
                 for (int u = 0; u < FIX_PF; u++) {
                     const int q = lane + 32 * u;

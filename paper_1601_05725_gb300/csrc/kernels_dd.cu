@@ -76,12 +76,17 @@ __global__ void __launch_bounds__(128) bk_dd_kernel(bk_dev d, const int32_t *__r
                                                     int32_t refno)
 {
     __shared__ bk_task Ts[4];
+    extern __shared__ uint32_t dd_bits[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int gw = blockIdx.x * 4 + wib;
     if (gw >= d.wsd_warps) return;
     bk_task &T = Ts[wib];
     unsigned char *slice = d.wsd + (int64_t)gw * d.wsd_slice;
+    // the reach's bitmaps, when they fit in shared memory; zero between columns
+    uint32_t *wbits = dd_bits + (int64_t)wib * d.dd_words;
+    for (int i = lane; i < d.dd_words; i += 32) wbits[i] = 0u;
+    __syncwarp();
     int cur_task = -1;
     for (;;) {
         int k = 0;
@@ -179,7 +184,7 @@ __global__ void __launch_bounds__(128) bk_dd_kernel(bk_dev d, const int32_t *__r
             if (mode == 1) {
                 bool ok = false, bad = false, broken = false, aborted = false;
                 double *xs = reinterpret_cast<double *>(slice);
-                if (!static_column(d, T, tid, xs, c, epoch, budget, tau, lane, false, s0, ok, bad, broken,
+                if (!pattern_column(d, T, tid, xs, c, epoch, budget, tau, lane, false, s0, ok, bad, broken,
                                    d.pchg_ep, &aborted))
                     return;
                 if (!aborted) {
@@ -209,11 +214,15 @@ __global__ void __launch_bounds__(128) bk_dd_kernel(bk_dev d, const int32_t *__r
         const int nsw = (nsteps + 31) >> 5;
         const int nrw = (lsp + 31) >> 5;
         double *x = reinterpret_cast<double *>(slice);
-        volatile uint32_t *sb = reinterpret_cast<uint32_t *>(x + T.space);
+        volatile uint32_t *sb = d.dd_words ? wbits : reinterpret_cast<uint32_t *>(x + T.space);
         volatile uint32_t *rb = sb + nsw;
         bool bad = false, overflow = false;
         int why = 0;
         int nu = 0;
+        // the stored pattern, to tell whether the recomputed one differs
+        const int old_uc = d.Ucnt[c], old_lc = d.Lcnt[c];
+        const int64_t old_ub = ub, old_lb = lb;
+        bool same = true;
 
         const int e1 = d.Bp[c + 1];
         for (int e = d.dstart[c] + lane; e < e1; e += 32) {
@@ -268,6 +277,7 @@ __global__ void __launch_bounds__(128) bk_dd_kernel(bk_dev d, const int32_t *__r
                 }
             }
             if (!overflow && lane == 0) {
+                if (ub != old_ub || nu >= old_uc - 1 || d.Ui[ub + nu] != j) same = false;
                 d.Ui[ub + nu] = j;
                 d.Ux[ub + nu] = m;
             }
@@ -391,7 +401,9 @@ __global__ void __launch_bounds__(128) bk_dd_kernel(bk_dev d, const int32_t *__r
                 bits &= bits - 1;
                 const int ls = (w << 5) + b;
                 if (room) {
-                    d.Li[q] = row_of_lslot(T, ls);
+                    const int r = row_of_lslot(T, ls);
+                    if (lb != old_lb || q - lb >= old_lc || d.Li[q] != r) same = false;
+                    d.Li[q] = r;
                     d.Lx[q] = x[ndesc + ls] / xp;
                 }
                 x[ndesc + ls] = 0.0;
@@ -401,6 +413,7 @@ __global__ void __launch_bounds__(128) bk_dd_kernel(bk_dev d, const int32_t *__r
             lpos += tot;
         }
         overflow = __any_sync(BK_FULL, overflow);
+        same = __all_sync(BK_FULL, same) && !overflow && nu + 1 == old_uc && lpos - lb == old_lc;
         __syncwarp();
         if (lane == 0) {
             if (pin) x[ndesc + pls] = 0.0;
@@ -427,8 +440,11 @@ __global__ void __launch_bounds__(128) bk_dd_kernel(bk_dev d, const int32_t *__r
             if (!ok && !resolve) atomicMin(d.task_fail + tid, c);
             d.dirty_ep[c] = epoch;
             d.dirty_ref[c] = refno;
-            d.pchg_ep[c] = epoch;
-            d.pchg_ref[c] = refno;
+            // dependents take the reach only if this column's pattern or pivot changed
+            if (!same || (resolve && piv != pcur)) {
+                d.pchg_ep[c] = epoch;
+                d.pchg_ref[c] = refno;
+            }
             __threadfence();
             st_release(d.done + c, epoch);
         }
@@ -444,6 +460,9 @@ void bk_launch_dd(const bk_dev &d, const int32_t *cols, int32_t ncols, int32_t *
 {
     if (ncols <= 0) return;
     int warps = std::min<int>(ncols, d.wsd_warps);
-    bk_dd_kernel<<<(warps + 3) / 4, 128, 0, (cudaStream_t)stream>>>(d, cols, ncols, counter, tau, epoch, budget,
-                                                                     refno);
+    const size_t smem = (size_t)4 * d.dd_words * sizeof(uint32_t);
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(bk_dd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    bk_dd_kernel<<<(warps + 3) / 4, 128, smem, (cudaStream_t)stream>>>(d, cols, ncols, counter, tau, epoch,
+                                                                        budget, refno);
 }

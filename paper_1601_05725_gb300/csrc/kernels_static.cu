@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(128) bk_static_kernel(bk_dev d, int32_t ncols,
             cur = tid;
         }
         bool ok = false, bad = false, broken = false;
-        if (!fixed_column(d, T, x, c, epoch, budget, tau, lane, ok, bad, broken)) return;
+        if (!pattern_column(d, T, tid, x, c, epoch, budget, tau, lane, true, 0, ok, bad, broken)) return;
         if (broken && lane == 0) report_internal(d.status, c, 41);
         __syncwarp();
         __threadfence();

@@ -399,6 +399,11 @@ void bk_plan_layout(bk_plan &pl)
     pl.ahat_doubles = std::max<int64_t>(ah, 1);
     pl.ahat_words = std::max<int64_t>(ab, 1);
     pl.wsd_slice = std::max<int64_t>(slice, 256);
+    // the reach's step and row bitmaps fit in shared memory for four warps a block
+    int64_t bw = 0;
+    for (auto &T : pl.tasks) bw = std::max<int64_t>(bw, ((int64_t)(T.hi - T.sp_lo) + 31) / 32 + (T.lspace + 31) / 32);
+    bw = (bw + 3) & ~(int64_t)3;
+    pl.dd_words = 4 * bw * 4 <= 160 * 1024 ? (int32_t)bw : 0;
     int64_t wmax = 1;
     for (int64_t v : level_cols) wmax = std::max(wmax, v);
     // at most 152 SMs x 16 warps, and at most 8 GiB of slices
