@@ -71,11 +71,94 @@ __device__ __forceinline__ bool lane_wait(const bk_dev &d, const int *flag, int 
     return true;
 }
 
+// Row slots of the pattern, listed in ascending order: one segment of set bits
+// of rb starting at word wcur (advanced past the words listed).  A segment holds
+// whole groups of 32 words, at most RLIST slots; 32 words hold at most RLIST.
+constexpr int RLIST = 1024;
+constexpr int RL_PF = 8;
+
+__device__ __forceinline__ int build_list(const volatile uint32_t *rb, int nrw, int &wcur, int *list, int lane)
+{
+    int filled = 0;
+    while (wcur < nrw) {
+        const int w = wcur + lane;
+        uint32_t bits = w < nrw ? rb[w] : 0u;
+        const int cnt = __popc(bits);
+        const int pre = warp_exscan(cnt, lane);
+        const int tot = __shfl_sync(BK_FULL, pre + cnt, 31);
+        if (filled + tot > RLIST) break;
+        int q = filled + pre;
+        while (bits) {
+            const int b = __ffs(bits) - 1;
+            bits &= bits - 1;
+            list[q++] = (w << 5) + b;
+        }
+        filled += tot;
+        wcur += 32;
+    }
+    __syncwarp();
+    return filled;
+}
+
+// One step of the reach, read ahead: its pivot slot, L(:,j)'s extent, and the
+// first RSTEP_PF * 32 entries of L(:,j) with their slots, values and what each
+// row adds (a step bit >= 0, a row bit encoded -2 - bit, or -1).  Entries are
+// read only when column j is final in this round (full); pinv of the rows is
+// final for every column after the round's resolve column.
+constexpr int RSTEP_PF = 4;
+struct RStep {
+    int sp, jc, why;
+    int64_t jl;
+    bool full;
+    int s[RSTEP_PF], bit[RSTEP_PF];
+    double l[RSTEP_PF];
+};
+
+__device__ __forceinline__ void read_step(const bk_dev &d, const bk_task &T, RStep &st, int j, int c, int s0,
+                                          int epoch, int lane, int ndesc, bool after_wait = false)
+{
+    const int base = T.sp_lo;
+    const bool inround = j >= s0 && j < T.hi;
+    int dn = 1;
+    if (inround && !after_wait) {
+        dn = lane == 0 ? (ld_acquire(d.done + j) == epoch) : 0;
+        dn = __shfl_sync(BK_FULL, dn, 0);
+    }
+    st.sp = slot_of(T, base, __ldcg(d.prow + j));
+    st.jl = __ldcg(d.Lbeg + j);
+    st.jc = __ldcg(d.Lcnt + j);
+    st.full = dn != 0;
+    st.why = 0;
+#pragma unroll
+    for (int u = 0; u < RSTEP_PF; u++) {
+        const int q = lane + 32 * u;
+        st.s[u] = -1;
+        st.bit[u] = -1;
+        st.l[u] = 0.0;
+        if (!dn || q >= st.jc) continue;
+        const int r = __ldcg(d.Li + st.jl + q);
+        st.l[u] = __ldcg(d.Lx + st.jl + q);
+        const int s = slot_of(T, base, r);
+        if (s < 0) { st.why = 65; continue; }
+        st.s[u] = s;
+        const int p = s < T.hi - base ? __ldcg(d.pinv + r) : -1;
+        if (p >= 0 && p < c) {
+            if (p > j) st.bit[u] = p - base;
+            else st.why = 66;
+        } else if (s >= ndesc) {
+            st.bit[u] = -2 - (s - ndesc);
+        } else {
+            st.why = 67;
+        }
+    }
+}
+
 __global__ void __launch_bounds__(128) bk_dd_kernel(bk_dev d, const int32_t *__restrict__ cols, int32_t ncols,
                                                     int32_t *counter, double tau, int32_t epoch, long long budget,
                                                     int32_t refno)
 {
     __shared__ bk_task Ts[4];
+    __shared__ int rlist[4 * RLIST];
     extern __shared__ uint32_t dd_bits[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
@@ -236,24 +319,36 @@ __global__ void __launch_bounds__(128) bk_dd_kernel(bk_dev d, const int32_t *__r
             else if (!why) why = 62;                 // a descendant row is always pivoted
         }
         __syncwarp();
+        // Steps in ascending order: the lowest set bit of sb.  The step after the
+        // current one is predicted (the lowest set bit once the current one is
+        // cleared) and its data read while the current step is applied; a step
+        // that the current one adds below the prediction is read when it is found.
         int w0 = 0;
-        for (int iter = 0;; iter++) {
-            const int jb = next_step_bit(sb, nsw, w0, lane);
-            if (jb < 0) break;
+        int jb = next_step_bit(sb, nsw, w0, lane);
+        RStep cur, nxt;
+        if (jb >= 0) read_step(d, T, cur, base + jb, c, s0, epoch, lane, ndesc);
+        for (int iter = 0; jb >= 0; iter++) {
             const int j = base + jb;
             if (iter > nsteps || j >= c) { if (!why) why = 63; break; }
-            if (j >= s0 && d.col_task[j] == tid) {
+            if (lane == 0) atomicAnd(const_cast<uint32_t *>(sb) + (jb >> 5), ~(1u << (jb & 31)));
+            __syncwarp();
+            int wp = w0;
+            const int jbp = next_step_bit(sb, nsw, wp, lane);
+            if (jbp >= 0 && base + jbp < c) read_step(d, T, nxt, base + jbp, c, s0, epoch, lane, ndesc);
+            if (!cur.full) {
                 int ok = lane == 0 ? (int)lane_wait(d, d.done + j, epoch, budget) : 1;
                 if (!__shfl_sync(BK_FULL, ok, 0)) return;
+                read_step(d, T, cur, j, c, s0, epoch, lane, ndesc, true);
             }
-            const int sp = slot_of(T, base, __ldcg(d.prow + j));
+            const int sp = cur.sp;
             if (sp < 0) { if (!why) why = 64; break; }
             const double m = x[sp];
+            double xv[RSTEP_PF];
+#pragma unroll
+            for (int u = 0; u < RSTEP_PF; u++) xv[u] = cur.s[u] >= 0 ? x[cur.s[u]] : 0.0;
+            const int oldu = (lane == 0 && ub == old_ub && nu < old_uc - 1) ? d.Ui[ub + nu] : -1;
             __syncwarp();
-            if (lane == 0) {
-                atomicAnd(const_cast<uint32_t *>(sb) + (jb >> 5), ~(1u << (jb & 31)));
-                x[sp] = 0.0;
-            }
+            if (lane == 0) x[sp] = 0.0;
             if (!isfinite(m)) bad = true;
             if (!overflow && ub + nu + 2 > ue) {
                 const int64_t cap = (int64_t)(c - T.sp_lo) + 1;
@@ -277,48 +372,72 @@ __global__ void __launch_bounds__(128) bk_dd_kernel(bk_dev d, const int32_t *__r
                 }
             }
             if (!overflow && lane == 0) {
-                if (ub != old_ub || nu >= old_uc - 1 || d.Ui[ub + nu] != j) same = false;
                 d.Ui[ub + nu] = j;
                 d.Ux[ub + nu] = m;
             }
-            nu++;
-            const int64_t jl = __ldcg(d.Lbeg + j);
-            const int jc = __ldcg(d.Lcnt + j);
-            for (int q = lane; q < jc; q += 32) {
-                const int r = __ldcg(d.Li + jl + q);
-                const double l = __ldcg(d.Lx + jl + q);
-                const int s = slot_of(T, base, r);
-                if (s < 0) { if (!why) why = 65; continue; }
-                x[s] = fma(-l, m, x[s]);
-                const int p = s < T.hi - base ? __ldcg(d.pinv + r) : -1;
+#pragma unroll
+            for (int u = 0; u < RSTEP_PF; u++) {
+                if (cur.s[u] < 0) continue;
+                x[cur.s[u]] = fma(-cur.l[u], m, xv[u]);
+                if (cur.bit[u] >= 0) set_bit(sb, cur.bit[u]);
+                else if (cur.bit[u] <= -2) set_bit(rb, -2 - cur.bit[u]);
+            }
+            if (cur.why && !why) why = cur.why;
+            for (int q = 32 * RSTEP_PF + lane; q < cur.jc; q += 32) {
+                const int r = __ldcg(d.Li + cur.jl + q);
+                const double l = __ldcg(d.Lx + cur.jl + q);
+                const int s1 = slot_of(T, base, r);
+                if (s1 < 0) { if (!why) why = 65; continue; }
+                x[s1] = fma(-l, m, x[s1]);
+                const int p = s1 < T.hi - base ? __ldcg(d.pinv + r) : -1;
                 if (p >= 0 && p < c) {
                     if (p > j) set_bit(sb, p - base);
                     else if (!why) why = 66;
-                } else if (s >= ndesc) {
-                    set_bit(rb, s - ndesc);
+                } else if (s1 >= ndesc) {
+                    set_bit(rb, s1 - ndesc);
                 } else if (!why) {
                     why = 67;
                 }
             }
+            if (lane == 0 && oldu != j) same = false;
+            nu++;
             __syncwarp();
+            jb = next_step_bit(sb, nsw, w0, lane);
+            if (jb >= 0) {
+                if (jb == jbp) cur = nxt;
+                else read_step(d, T, cur, base + jb, c, s0, epoch, lane, ndesc);
+            }
         }
         why = warp_max_i(why);
-        // Algorithm 1's pivot selection among the node's unpivoted rows
+        // Algorithm 1's pivot selection among the node's unpivoted rows.  The
+        // pattern's row slots are listed in ascending order, a segment of at most
+        // RLIST at a time, and their values read eight per lane at once.
+        int *list = rlist + wib * RLIST;
         double amax = 0.0;
-        int ncand = 0;
-        for (int w = lane; w < nrw; w += 32) {
-            uint32_t bits = rb[w];
-            while (bits) {
-                const int b = __ffs(bits) - 1;
-                bits &= bits - 1;
-                const int ls = (w << 5) + b;
-                const double v = x[ndesc + ls];
-                if (!isfinite(v)) bad = true;
-                if (ls < nown) {
-                    ncand++;
-                    amax = fmax(amax, fabs(v));
+        int ncand = 0, nrows = 0;
+        for (int wcur = 0; wcur < nrw;) {
+            const int filled = build_list(rb, nrw, wcur, list, lane);
+            nrows += filled;
+            for (int i0 = 0; i0 < filled; i0 += 32 * RL_PF) {
+                int ls[RL_PF];
+                double v[RL_PF];
+#pragma unroll
+                for (int u = 0; u < RL_PF; u++) {
+                    const int i = i0 + lane + 32 * u;
+                    ls[u] = i < filled ? list[i] : -1;
+                    v[u] = ls[u] >= 0 ? x[ndesc + ls[u]] : 0.0;
+                }
+#pragma unroll
+                for (int u = 0; u < RL_PF; u++) {
+                    if (ls[u] < 0) continue;
+                    if (!isfinite(v[u])) bad = true;
+                    if (ls[u] < nown) {
+                        ncand++;
+                        amax = fmax(amax, fabs(v[u]));
+                    }
                 }
             }
+            __syncwarp();
         }
         amax = warp_max(amax);
         ncand = warp_sum(ncand);
@@ -336,19 +455,27 @@ __global__ void __launch_bounds__(128) bk_dd_kernel(bk_dev d, const int32_t *__r
                 piv = pref;
                 ok = true;
             } else if (resolve) {
+                // the lowest own row reaching the maximum
                 int best = INT_MAX;
                 const int nw_own = (nown + 31) >> 5;
-                for (int w = lane; w < nw_own; w += 32) {
-                    uint32_t bits = rb[w];
-                    while (bits) {
-                        const int b = __ffs(bits) - 1;
-                        bits &= bits - 1;
-                        const int ls = (w << 5) + b;
-                        if (ls < nown && fabs(x[ndesc + ls]) == amax) { best = ls; break; }
+                for (int wcur = 0; wcur < nw_own && best == INT_MAX;) {
+                    const int filled = build_list(rb, nw_own, wcur, list, lane);
+                    for (int i0 = 0; i0 < filled; i0 += 32 * RL_PF) {
+                        int ls[RL_PF];
+                        double v[RL_PF];
+#pragma unroll
+                        for (int u = 0; u < RL_PF; u++) {
+                            const int i = i0 + lane + 32 * u;
+                            ls[u] = i < filled ? list[i] : -1;
+                            v[u] = ls[u] >= 0 ? x[ndesc + ls[u]] : 0.0;
+                        }
+#pragma unroll
+                        for (int u = 0; u < RL_PF; u++)
+                            if (ls[u] >= 0 && ls[u] < nown && fabs(v[u]) == amax) best = min(best, ls[u]);
                     }
-                    if (best != INT_MAX) break;
+                    best = warp_min(best);
+                    __syncwarp();
                 }
-                best = warp_min(best);
                 piv = T.lo + best;
                 ok = true;
             }
@@ -363,9 +490,7 @@ __global__ void __launch_bounds__(128) bk_dd_kernel(bk_dev d, const int32_t *__r
         const double xp = pin ? x[ndesc + pls] : 0.0;
         // L(:,c) = x / pivot over the pattern's unpivoted rows; clear the state
         {
-            int cnt_all = 0;
-            for (int w = lane; w < nrw; w += 32) cnt_all += __popc(rb[w]);
-            cnt_all = warp_sum(cnt_all) - (pin ? 1 : 0);
+            const int cnt_all = nrows - (pin ? 1 : 0);
             if (!overflow && lb + cnt_all > le) {
                 const int64_t cap = max((long long)cnt_all,
                                         min((long long)(2 * (int64_t)cnt_all + 16),
@@ -384,34 +509,42 @@ __global__ void __launch_bounds__(128) bk_dd_kernel(bk_dev d, const int32_t *__r
                     }
                 }
             }
+            if (lb + cnt_all > le) overflow = true;
         }
         int64_t lpos = lb;
-        for (int wbase = 0; wbase < nrw; wbase += 32) {
-            const int w = wbase + lane;
-            uint32_t bits = w < nrw ? rb[w] : 0u;
-            if (w < nrw && bits) rb[w] = 0u;
-            if (pin && w == (pls >> 5)) bits &= ~(1u << (pls & 31));
-            const int cnt = __popc(bits);
-            const int pre = warp_exscan(cnt, lane);
-            const int tot = __shfl_sync(BK_FULL, pre + cnt, 31);
-            const bool room = !overflow && lpos + tot <= le;
-            int64_t q = lpos + pre;
-            while (bits) {
-                const int b = __ffs(bits) - 1;
-                bits &= bits - 1;
-                const int ls = (w << 5) + b;
-                if (room) {
-                    const int r = row_of_lslot(T, ls);
-                    if (lb != old_lb || q - lb >= old_lc || d.Li[q] != r) same = false;
-                    d.Li[q] = r;
-                    d.Lx[q] = x[ndesc + ls] / xp;
+        int rank0 = 0;
+        for (int wcur = 0; wcur < nrw;) {
+            const int filled = build_list(rb, nrw, wcur, list, lane);
+            for (int i0 = 0; i0 < filled; i0 += 32 * RL_PF) {
+                int ls[RL_PF], oldr[RL_PF];
+                int64_t qq[RL_PF];
+                double v[RL_PF];
+#pragma unroll
+                for (int u = 0; u < RL_PF; u++) {
+                    const int i = i0 + lane + 32 * u;
+                    ls[u] = i < filled ? list[i] : -1;
+                    if (ls[u] == pls && pin) ls[u] = -2;          // the pivot row: cleared below
+                    qq[u] = lb + rank0 + i - ((pin && ls[u] > pls) ? 1 : 0);
+                    v[u] = ls[u] >= 0 ? x[ndesc + ls[u]] : 0.0;
+                    oldr[u] = (ls[u] >= 0 && !overflow && lb == old_lb && qq[u] - lb < old_lc) ? d.Li[qq[u]] : -1;
                 }
-                x[ndesc + ls] = 0.0;
-                q++;
+#pragma unroll
+                for (int u = 0; u < RL_PF; u++) {
+                    if (ls[u] < 0) continue;
+                    if (!overflow) {
+                        const int r = row_of_lslot(T, ls[u]);
+                        if (oldr[u] != r) same = false;
+                        d.Li[qq[u]] = r;
+                        d.Lx[qq[u]] = v[u] / xp;
+                    }
+                    x[ndesc + ls[u]] = 0.0;
+                }
             }
-            if (!room) overflow = true;
-            lpos += tot;
+            rank0 += filled;
+            __syncwarp();
         }
+        lpos = lb + nrows - (pin ? 1 : 0);
+        for (int w = lane; w < nrw; w += 32) rb[w] = 0u;
         overflow = __any_sync(BK_FULL, overflow);
         same = __all_sync(BK_FULL, same) && !overflow && nu + 1 == old_uc && lpos - lb == old_lc;
         __syncwarp();
