@@ -80,12 +80,14 @@ typedef struct {
     int32_t gp_launches;          /* kernel launches of the last factor/refactor */
     int32_t static_launches;
     int64_t kernel_launches;      /* all kernel launches since basker_symbolic */
-    double kernel_ms[8];          /* with options.timing: device time per kernel kind since
+    double kernel_ms[10];         /* with options.timing: device time per kernel kind since
                                      the last basker_info call: [0] value gather,
                                      [1] stored-pattern refactor, [2] DAG levels,
                                      [3] in-node Algorithm 1, [4] separator descendant
                                      phase, [5] solve, [6] pivot reset,
-                                     [7] speculative separator refactor */
+                                     [7] refactorization rounds after the stored-pattern
+                                     pass, [8] factors transposed into rows for the
+                                     solve, [9] reserved */
     int32_t internal_site;        /* nonzero: code of the internal consistency check that
                                      failed (reported as INVALID_ARG), for diagnosis */
     int32_t internal_col;         /* column of that check */

@@ -48,12 +48,12 @@ class Info(ctypes.Structure):
                 ("last_repivot_columns", ctypes.c_int32), ("off_diagonal_pivots", ctypes.c_int32),
                 ("capacity_regrows", ctypes.c_int32), ("device_bytes", ctypes.c_int64),
                 ("gp_launches", ctypes.c_int32), ("static_launches", ctypes.c_int32),
-                ("kernel_launches", ctypes.c_int64), ("kernel_ms", ctypes.c_double * 8),
+                ("kernel_launches", ctypes.c_int64), ("kernel_ms", ctypes.c_double * 10),
                 ("internal_site", ctypes.c_int32), ("internal_col", ctypes.c_int32),
                 ("last_rounds", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 KERNEL_KINDS = ["gather", "static_refactor", "dag_levels", "gp_in_node", "gp_descendant", "solve",
-                "pivot_reset", "spec_separator"]
+                "pivot_reset", "refactor_rounds", "rows_transpose", "reserved"]
 
 
 EXPORTED = ["basker_default_options", "basker_symbolic", "basker_factor", "basker_refactor",
@@ -228,7 +228,7 @@ class Handle:
         if s != 0:
             raise BaskerError(s, "basker_info")
         out = {k: getattr(inf, k) for k, _ in Info._fields_ if k not in ("reserved", "kernel_ms")}
-        out["kernel_ms"] = {KERNEL_KINDS[i]: inf.kernel_ms[i] for i in range(8)}
+        out["kernel_ms"] = {KERNEL_KINDS[i]: inf.kernel_ms[i] for i in range(len(KERNEL_KINDS))}
         return out
 
     def export(self):

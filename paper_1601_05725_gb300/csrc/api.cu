@@ -48,7 +48,8 @@ struct basker_s {
 
 namespace {
 
-enum { KT_GATHER = 0, KT_STATIC = 1, KT_LEVELS = 2, KT_GP = 3, KT_DESC = 4, KT_SOLVE = 5, KT_RESET = 6, KT_SPEC = 7 };
+enum { KT_GATHER = 0, KT_STATIC = 1, KT_LEVELS = 2, KT_GP = 3, KT_DESC = 4, KT_SOLVE = 5, KT_RESET = 6, KT_SPEC = 7,
+       KT_ROWS = 8 };
 
 cudaEvent_t take_event(basker_t h)
 {
@@ -151,9 +152,17 @@ int alloc_factors(basker_t h)
     h->d.lpool_end = pl.lcap + pl.lpool;
     h->d.upool_end = pl.ucap + pl.upool;
     TRY(dalloc(h, &h->d.Li, (size_t)h->d.lpool_end));
-    dfree(h, (void *)h->sd.Ls);
-    h->sd.Ls = nullptr;
-    TRY(dalloc(h, (int32_t **)&h->sd.Ls, (size_t)h->d.lpool_end));
+    // the factors by rows (for the solve) have the same capacities
+    bk_rows &r = h->sd.r;
+    dfree(h, r.Lrk); dfree(h, r.Lrx); dfree(h, r.Urk); dfree(h, r.Urx); dfree(h, r.tk); dfree(h, r.tx);
+    r.Lrk = r.Urk = r.tk = nullptr;
+    r.Lrx = r.Urx = r.tx = nullptr;
+    TRY(dalloc(h, &r.Lrk, (size_t)h->d.lpool_end));
+    TRY(dalloc(h, &r.Lrx, (size_t)h->d.lpool_end));
+    TRY(dalloc(h, &r.Urk, (size_t)h->d.upool_end));
+    TRY(dalloc(h, &r.Urx, (size_t)h->d.upool_end));
+    TRY(dalloc(h, &r.tk, (size_t)std::max(h->d.lpool_end, h->d.upool_end)));
+    TRY(dalloc(h, &r.tx, (size_t)std::max(h->d.lpool_end, h->d.upool_end)));
     TRY(dalloc(h, &h->d.Lx, (size_t)h->d.lpool_end));
     TRY(dalloc(h, &h->d.Ui, (size_t)h->d.upool_end));
     TRY(dalloc(h, &h->d.Ux, (size_t)h->d.upool_end));
@@ -275,16 +284,17 @@ int setup_device(basker_t h)
     bk_solve_plan_build(pl, h->sp);
     bk_solve_dev &s = h->sd;
     s.nitems = (int32_t)h->sp.items.size();
-    TRY(upload(h, (bk_sitem **)&s.items, h->sp.items));
-    TRY(upload(h, (int32_t **)&s.deps, h->sp.deps));
-    TRY(upload(h, (int32_t **)&s.desc, h->sp.desc));
-    TRY(dalloc(h, &s.item_done, (size_t)std::max(s.nitems, 1), true));
+    TRY(upload(h, (int32_t **)&s.items, h->sp.items));
     TRY(upload(h, (int32_t **)&s.offp, h->sp.offp));
     TRY(upload(h, (int32_t **)&s.offj, h->sp.offj));
     TRY(upload(h, (int32_t **)&s.offpos, h->sp.offpos));
-    TRY(upload(h, (int64_t **)&s.acc_off, h->sp.acc_off));
-    s.acc_stride = h->sp.acc_stride;
-    s.smem_bytes = h->sp.smem_bytes;
+    TRY(dalloc(h, &s.fdone, (size_t)n, true));
+    TRY(dalloc(h, &s.bdone, (size_t)n, true));
+    TRY(dalloc(h, &s.r.Lrp, (size_t)n + 1));
+    TRY(dalloc(h, &s.r.Urp, (size_t)n + 1));
+    TRY(dalloc(h, &s.r.Ud, (size_t)n));
+    TRY(dalloc(h, &s.r.cnt, (size_t)2 * ((size_t)n + 1)));
+    TRY(dalloc(h, &s.r.part, (size_t)n / 1024 + 2));
     TRY(upload_symbolic_pattern(h));
     h->schedule_valid = true;
     return BASKER_OK;
@@ -516,8 +526,8 @@ int factor_impl(basker_t h, const double *values, cudaStream_t s, bool refactor)
             }
         }
         if (st != BASKER_OK) { h->factored = false; return st == -1 ? BASKER_ERR_OOM : st; }
-        tbeg(h, KT_SOLVE, s, 1);
-        bk_launch_lsteps(h->d, (int *)h->sd.Ls, s);
+        tbeg(h, KT_ROWS, s, 11);
+        bk_launch_rows(h->d, h->sd.r, s);
         tend(h, s);
         h->factored = true;
         return BASKER_OK;
@@ -536,8 +546,8 @@ int factor_impl(basker_t h, const double *values, cudaStream_t s, bool refactor)
         if (st != -1) break;
     }
     if (st != BASKER_OK) { h->factored = false; return st == -1 ? BASKER_ERR_OOM : st; }
-    tbeg(h, KT_SOLVE, s, 1);
-    bk_launch_lsteps(h->d, (int *)h->sd.Ls, s);
+    tbeg(h, KT_ROWS, s, 11);
+    bk_launch_rows(h->d, h->sd.r, s);
     tend(h, s);
     h->info.off_diagonal_pivots = h->h_status->offdiag;
     // with the natural pivots everywhere the pattern is the symbolic one, whose
@@ -551,10 +561,10 @@ int ensure_solve_buffers(basker_t h, int32_t nrhs)
 {
     if (nrhs <= h->nrhs_cap) return BASKER_OK;
     dfree(h, h->sd.w);
-    dfree(h, h->sd.acc);
-    h->sd.w = h->sd.acc = nullptr;
+    dfree(h, h->sd.z);
+    h->sd.w = h->sd.z = nullptr;
     TRY(dalloc(h, &h->sd.w, (size_t)h->pl.n * (size_t)nrhs));
-    TRY(dalloc(h, &h->sd.acc, (size_t)h->sd.acc_stride * (size_t)nrhs));
+    TRY(dalloc(h, &h->sd.z, (size_t)h->pl.n * (size_t)nrhs));
     h->nrhs_cap = nrhs;
     return BASKER_OK;
 }
@@ -570,7 +580,7 @@ int32_t bk_handle_n(basker_t h) { return h->pl.n; }
 
 int64_t bk_solve_scratch_doubles(basker_t h, int32_t nrhs)
 {
-    return (int64_t)nrhs * ((int64_t)h->pl.n + h->sd.acc_stride);
+    return (int64_t)nrhs * 2 * (int64_t)h->pl.n;
 }
 
 int bk_solve_on_scratch(basker_t h, int32_t nrhs, const double *b_dev, int32_t ldb, double *x_dev, int32_t ldx,
@@ -580,7 +590,7 @@ int bk_solve_on_scratch(basker_t h, int32_t nrhs, const double *b_dev, int32_t l
     if (nrhs == 0 || h->pl.n == 0) return BASKER_OK;
     bk_solve_dev sd = h->sd;
     sd.w = scratch;
-    sd.acc = scratch + (size_t)nrhs * (size_t)h->pl.n;
+    sd.z = scratch + (size_t)nrhs * (size_t)h->pl.n;
     cudaStream_t s = (cudaStream_t)stream;
     CU(cudaMemsetAsync(h->d.counter + 2, 0, sizeof(int32_t), s));
     h->solve_epoch++;

@@ -1,22 +1,24 @@
 // kernels_solve.cu -- x = A^{-1} b with the factors of the BTF diagonal blocks.
 //
-// BTF back-substitution (Sec. II and III-B: only the diagonal blocks are factored;
-// the off-diagonal blocks keep A's values and enter through a product): blocks
-// from last to first, c_d -= sum_{e>d} B_de z_e, then L_d w = P_d c_d and
-// U_d z_d = w.  The work is a list of items claimed by warps in a topological
-// order, each item waiting for the items it needs through flags (point-to-point
-// synchronisation, Sec. IV) with a bounded wait:
-//   BLOCK d        a BTF block without ND: coupling rows, forward, backward
-//   FWD t          ND node t: its rows' coupling terms and the contributions its
-//                  descendants left for it, then the forward sweep over its own
-//                  columns; contributions to ancestor rows go to the node's own
-//                  buffer (read later by the ancestors, in a fixed order)
-//   BWD t          ND node t, after its ancestors: backward sweep over its columns,
-//                  which updates its own and its descendants' rows
-// Values written by other warps are read through L2 (ld.cg).
+// BTF back-substitution (Sec. II and III-B: only the diagonal blocks are
+// factored; the off-diagonal blocks keep A's values and enter through a
+// product): blocks from last to first, c_d -= sum_{e>d} B_de z_e, then
+// L_d w = P_d c_d and U_d z_d = w.  Evaluated by rows in pivot-step space, one
+// warp per row and direction, claimed in a topological order:
+//   forward row i   w_i = c(prow i) - sum_k L(i,k) w_k, k ascending, after the
+//                   coupling terms of row prow i (later blocks' final z_j)
+//   backward row i  z_i = (w_i - sum_k U(i,k) z_k) / U(i,i), k descending
+// Each term waits for the flag of the row it reads (point-to-point
+// synchronisation, Sec. IV) with a bounded wait.  Per solution entry the fma
+// sequence is the one of the column sweeps (ascending steps for L, descending for
+// U), so the result does not depend on the schedule.
+//
+// The factors are kept by columns; after every factorization bk_launch_rows
+// transposes them into rows (count, scan, scatter, and a rank sort per row).
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 
 #include "basker_internal.h"
 #include "device_util.cuh"
@@ -26,225 +28,304 @@ using namespace bk;
 
 namespace {
 
-__device__ __forceinline__ bool wait_items(const bk_dev &d, const bk_solve_dev &s, const bk_sitem &it,
-                                           int epoch, long long budget, int lane)
+// ---------------------------------------------------------------- factors by rows
+
+__global__ void bk_rows_count(bk_dev d, bk_rows r)
 {
-    int ok = 1;
-    for (int q = it.dep_beg + lane; q < it.dep_end; q += 32) {
-        const int *flag = s.item_done + s.deps[q];
-        if (ld_acquire(flag) != epoch) {
-            const long long t0 = clock64();
-            while (ld_acquire(flag) != epoch) {
-                if (*reinterpret_cast<const volatile int *>(&d.status->timeout) || clock64() - t0 > budget) {
-                    atomicExch(&d.status->timeout, 1);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(32);
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    int32_t *lc = r.cnt, *uc = r.cnt + d.n + 1;
+    for (int c = warp; c < d.n; c += nwarps) {
+        const int64_t lb = d.Lbeg[c];
+        const int ln = d.Lcnt[c];
+        for (int t = lane; t < ln; t += 32) atomicAdd(lc + d.pinv[d.Li[lb + t]], 1);
+        const int64_t ub = d.Ubeg[c];
+        const int un = d.Ucnt[c];
+        for (int t = lane; t < un - 1; t += 32) atomicAdd(uc + d.Ui[ub + t], 1);
+        if (lane == 0) r.Ud[c] = d.Ux[ub + un - 1];
+    }
+}
+
+// Exclusive scan of m counts into m + 1 starts: per-block sums, a scan of the
+// block sums, then each block's scan plus its offset.
+__device__ __forceinline__ int64_t block_exscan(int64_t v, int64_t *warp_tot, int64_t &total)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int64_t inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(BK_FULL, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) warp_tot[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        int64_t t = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : 0;
+        int64_t ti = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(BK_FULL, ti, o);
+            if (lane >= o) ti += y;
+        }
+        warp_tot[lane] = ti - t;
+        if (lane == 31) warp_tot[32] = ti;
+    }
+    __syncthreads();
+    const int64_t ex = inc - v + warp_tot[wid];
+    total = warp_tot[32];
+    __syncthreads();
+    return ex;
+}
+
+__global__ void __launch_bounds__(1024) bk_scan_sums(const int32_t *cnt, int32_t m, int64_t *part)
+{
+    __shared__ int64_t wt[33];
+    const int i = blockIdx.x * 1024 + threadIdx.x;
+    int64_t total;
+    block_exscan(i < m ? cnt[i] : 0, wt, total);
+    if (threadIdx.x == 0) part[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(1024) bk_scan_parts(int64_t *part, int32_t nb)
+{
+    __shared__ int64_t wt[33];
+    int64_t carry = 0;
+    for (int b0 = 0; b0 < nb; b0 += 1024) {
+        const int i = b0 + threadIdx.x;
+        const int64_t v = i < nb ? part[i] : 0;
+        int64_t total;
+        const int64_t ex = block_exscan(v, wt, total);
+        if (i < nb) part[i] = carry + ex;
+        carry += total;
+    }
+    if (threadIdx.x == 0) part[nb] = carry;
+}
+
+__global__ void __launch_bounds__(1024) bk_scan_apply(const int32_t *cnt, int32_t m, const int64_t *part,
+                                                      int64_t *out)
+{
+    __shared__ int64_t wt[33];
+    const int i = blockIdx.x * 1024 + threadIdx.x;
+    int64_t total;
+    const int64_t ex = block_exscan(i < m ? cnt[i] : 0, wt, total);
+    if (i < m) out[i] = part[blockIdx.x] + ex;
+    if (i == 0) out[m] = part[gridDim.x];
+}
+
+// Entries of L (which = 0) or U (which = 1) into the unsorted row buffer.
+__global__ void bk_rows_scatter(bk_dev d, bk_rows r, int which)
+{
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    int32_t *cur = r.cnt + (which ? d.n + 1 : 0);
+    const int64_t *rp = which ? r.Urp : r.Lrp;
+    for (int c = warp; c < d.n; c += nwarps) {
+        if (which == 0) {
+            const int64_t lb = d.Lbeg[c];
+            const int ln = d.Lcnt[c];
+            for (int t = lane; t < ln; t += 32) {
+                const int i = d.pinv[d.Li[lb + t]];
+                const int64_t pos = rp[i] + atomicAdd(cur + i, 1);
+                r.tk[pos] = c;
+                r.tx[pos] = d.Lx[lb + t];
+            }
+        } else {
+            const int64_t ub = d.Ubeg[c];
+            const int un = d.Ucnt[c];
+            for (int t = lane; t < un - 1; t += 32) {
+                const int i = d.Ui[ub + t];
+                const int64_t pos = rp[i] + atomicAdd(cur + i, 1);
+                r.tk[pos] = c;
+                r.tx[pos] = d.Ux[ub + t];
             }
         }
-        if (!ok) break;
+    }
+}
+
+// Each row's entries in ascending (L) or descending (U) column order: the rank of
+// an entry is the number of entries of its row that come before it.
+__global__ void bk_rows_sort(int32_t n, const int64_t *rp, const int32_t *tk, const double *tx, int32_t *ok,
+                             double *ox, int desc)
+{
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int sentinel = desc ? INT_MIN : INT_MAX;
+    for (int i = warp; i < n; i += nwarps) {
+        const int64_t p0 = rp[i];
+        const int len = (int)(rp[i + 1] - p0);
+        for (int e0 = 0; e0 < len; e0 += 32) {
+            const bool mine = e0 + lane < len;
+            const int myk = mine ? tk[p0 + e0 + lane] : sentinel;
+            const double myx = mine ? tx[p0 + e0 + lane] : 0.0;
+            int rank = 0;
+            for (int f0 = 0; f0 < len; f0 += 32) {
+                const int other = f0 + lane < len ? tk[p0 + f0 + lane] : sentinel;
+#pragma unroll 8
+                for (int t = 0; t < 32; t++) {
+                    const int kk = __shfl_sync(BK_FULL, other, t);
+                    rank += desc ? (kk > myk) : (kk < myk);
+                }
+            }
+            if (mine) {
+                ok[p0 + rank] = myk;
+                ox[p0 + rank] = myx;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- the solve
+
+// Lane-parallel bounded wait on flags[j] == epoch for the lanes with want; false
+// if a wait ran out (the timeout status is then set).
+__device__ __forceinline__ bool wait_flags(const bk_dev &d, const int32_t *flags, int j, bool want, int epoch,
+                                           long long budget)
+{
+    int ok = 1;
+    if (want && ld_acquire(flags + j) != epoch) {
+        const long long t0 = clock64();
+        unsigned ns = 32;
+        while (ld_acquire(flags + j) != epoch) {
+            if (*reinterpret_cast<const volatile int *>(&d.status->timeout) || clock64() - t0 > budget) {
+                atomicExch(&d.status->timeout, 1);
+                ok = 0;
+                break;
+            }
+            __nanosleep(ns);
+            ns = min(ns * 2, 512u);
+        }
     }
     return !__any_sync(BK_FULL, !ok);
 }
 
-// Slot of step i among the ancestor rows of task u (its contribution buffer).
-__device__ __forceinline__ int anc_slot(const bk_task &U, int i)
+// z -= sum over up to 32 terms a_t * v_t, in lane order (every lane computes the
+// same chain).
+__device__ __forceinline__ double chain(double z, double a, double v, int cnt)
 {
-    int off = 0;
-    for (int a = 0; a < U.nanc; a++) {
-        if (i >= U.anc_lo[a] && i < U.anc_hi[a]) return off + (i - U.anc_lo[a]);
-        off += U.anc_hi[a] - U.anc_lo[a];
-    }
-    return -1;
+    for (int t = 0; t < cnt; t++) z = fma(-__shfl_sync(BK_FULL, a, t), __shfl_sync(BK_FULL, v, t), z);
+    return z;
 }
 
-// w(k) = b(P(prow k)) - sum of coupling terms of row prow(k) (columns of later blocks)
-__device__ __forceinline__ double init_row(const bk_dev &d, const bk_solve_dev &s, int k, int q,
-                                           const double *b, int ldb)
+__global__ void __launch_bounds__(128) bk_solve_kernel(bk_dev d, bk_solve_dev s, int32_t nrhs,
+                                                       const double *__restrict__ b, int32_t ldb, double *x,
+                                                       int32_t ldx, int32_t epoch, long long budget)
 {
-    const int r = d.prow[k];
-    double v = b[(int64_t)q * ldb + d.P[r]];
-    for (int e = s.offp[r]; e < s.offp[r + 1]; e++)
-        v = fma(-d.Bx[s.offpos[e]], __ldcg(s.w + (int64_t)q * d.n + s.offj[e]), v);
-    return v;
-}
-
-// Forward sweep over the node's own columns: wl holds the node's own rows (in
-// shared memory when they fit), acc its ancestors' rows.  The first 32 entries
-// of the next column are loaded while the current one is applied.
-__device__ void forward_sweep(const bk_dev &d, const bk_solve_dev &s, const bk_task &T, double *wl,
-                              double *acc, int lane)
-{
-    const int lo = T.lo, hi = T.hi;
-    int64_t nb = d.Lbeg[lo];
-    int nc = d.Lcnt[lo];
-    int ni = lane < nc ? s.Ls[nb + lane] : -1;
-    double nv = lane < nc ? d.Lx[nb + lane] : 0.0;
-    for (int k = lo; k < hi; k++) {
-        const int64_t lb = nb;
-        const int lc = nc;
-        const int ci = ni;
-        const double cv = nv;
-        if (k + 1 < hi) {
-            nb = d.Lbeg[k + 1];
-            nc = d.Lcnt[k + 1];
-            ni = lane < nc ? s.Ls[nb + lane] : -1;
-            nv = lane < nc ? d.Lx[nb + lane] : 0.0;
-        }
-        const double wk = wl[k - lo];
-        auto apply = [&](int i, double l) {
-            if (i > k && i < hi) {
-                wl[i - lo] = fma(-l, wk, wl[i - lo]);
-            } else {
-                const int a = acc ? anc_slot(T, i) : -1;
-                if (a >= 0) acc[a] = fma(l, wk, acc[a]);
-                else report_internal(d.status, k, 51);
-            }
-        };
-        if (lane < lc) apply(ci, cv);
-        for (int t = 32 + lane; t < lc; t += 32) apply(s.Ls[lb + t], d.Lx[lb + t]);
-        __syncwarp();
-    }
-}
-
-// Backward sweep: z_k = w_k / U(k,k), then w -= U(:,k) z_k; own rows in wl, the
-// descendants' rows (separators only) in global memory.
-__device__ void backward_sweep(const bk_dev &d, const bk_solve_dev &s, const bk_task &T, double *wl,
-                               double *wg, int lane)
-{
-    const int lo = T.lo, hi = T.hi;
-    int64_t nb = d.Ubeg[hi - 1];
-    int nc = d.Ucnt[hi - 1];
-    int ni = lane < nc ? d.Ui[nb + lane] : -1;
-    double nv = lane < nc ? d.Ux[nb + lane] : 0.0;
-    for (int k = hi - 1; k >= lo; k--) {
-        const int64_t ub = nb;
-        const int uc = nc;
-        const int ci = ni;
-        const double cv = nv;
-        if (k > lo) {
-            nb = d.Ubeg[k - 1];
-            nc = d.Ucnt[k - 1];
-            ni = lane < nc ? d.Ui[nb + lane] : -1;
-            nv = lane < nc ? d.Ux[nb + lane] : 0.0;
-        }
-        const double zk = wl[k - lo] / d.Ux[ub + uc - 1];
-        auto apply = [&](int i, double u) {
-            if (i >= lo) wl[i - lo] = fma(-u, zk, wl[i - lo]);
-            else wg[i] = fma(-u, zk, __ldcg(wg + i));
-        };
-        if (lane < uc - 1) apply(ci, cv);
-        for (int t = 32 + lane; t < uc - 1; t += 32) apply(d.Ui[ub + t], d.Ux[ub + t]);
-        __syncwarp();
-        if (lane == 0) wl[k - lo] = zk;
-        __syncwarp();
-    }
-}
-
-__global__ void __launch_bounds__(32) bk_solve_kernel(bk_dev d, bk_solve_dev s, int32_t nrhs,
-                                                      const double *__restrict__ b, int32_t ldb,
-                                                      double *x, int32_t ldx, int32_t epoch,
-                                                      long long budget)
-{
-    extern __shared__ __align__(16) double sw[];
-    __shared__ bk_task T;
-    __shared__ bk_task U;
-    const int lane = threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int64_t n = d.n;
     for (;;) {
         int k = 0;
         if (lane == 0) k = atomicAdd(d.counter + 2, 1);
         k = __shfl_sync(BK_FULL, k, 0);
         if (k >= s.nitems) break;
-        const bk_sitem it = s.items[k];
-        if (!wait_items(d, s, it, epoch, budget, lane)) return;
-        load_task(T, d.tasks + it.task, lane);
-        const int nown = T.hi - T.lo;
-        const int na = it.type == BK_ITEM_BLOCK ? 0 : T.lspace - nown;
-        const bool fits = (int64_t)(nown + na) * 8 <= s.smem_bytes;
-        for (int q = 0; q < nrhs; q++) {
-            double *w = s.w + (int64_t)q * d.n;
-            double *wl = fits ? sw : w + T.lo;
-            double *accg = s.acc + (int64_t)q * s.acc_stride + s.acc_off[it.task];
-            double *acc = it.type == BK_ITEM_FWD ? (fits ? sw + nown : accg) : nullptr;
-            if (it.type == BK_ITEM_BLOCK || it.type == BK_ITEM_FWD) {
-                for (int kk = T.lo + lane; kk < T.hi; kk += 32) wl[kk - T.lo] = init_row(d, s, kk, q, b, ldb);
-                if (acc)
-                    for (int a = lane; a < na; a += 32) acc[a] = 0.0;
-                __syncwarp();
-                if (it.type == BK_ITEM_FWD) {
-                    // contributions of every descendant (fixed order: postorder)
-                    for (int u = it.desc_beg; u < it.desc_end; u++) {
-                        const int ut = s.desc[u];
-                        load_task(U, d.tasks + ut, lane);
-                        const double *au = s.acc + (int64_t)q * s.acc_stride + s.acc_off[ut];
-                        for (int kk = T.lo + lane; kk < T.hi; kk += 32) {
-                            const int a = anc_slot(U, kk);
-                            if (a >= 0) wl[kk - T.lo] -= __ldcg(au + a);
-                        }
-                        __syncwarp();
-                    }
+        const int it = s.items[k];
+        if (it >= 0) {
+            // forward row i: coupling terms of row prow i, then L(i,:)
+            const int i = it;
+            const int r = d.prow[i];
+            const int e0 = s.offp[r], e1 = s.offp[r + 1];
+            const int64_t l0 = s.r.Lrp[i], l1 = s.r.Lrp[i + 1];
+            for (int q = 0; q < nrhs; q++) {
+                double z = b[(int64_t)q * ldb + d.P[r]];
+                for (int e = e0; e < e1; e += 32) {
+                    const int cnt = min(32, e1 - e);
+                    const bool have = lane < cnt;
+                    const int j = have ? s.offj[e + lane] : 0;
+                    const double a = have ? d.Bx[s.offpos[e + lane]] : 0.0;
+                    if (!wait_flags(d, s.bdone, j, have, epoch, budget)) return;
+                    const double v = have ? __ldcg(s.z + q * n + j) : 0.0;
+                    z = chain(z, a, v, cnt);
                 }
-                forward_sweep(d, s, T, wl, acc, lane);
-                if (it.type == BK_ITEM_BLOCK) backward_sweep(d, s, T, wl, w, lane);
-                if (fits && acc)
-                    for (int a = lane; a < na; a += 32) accg[a] = acc[a];
-            } else {
-                // own rows were written by other warps: read them through L2 (and
-                // rewrite them in place when they stay in global memory)
-                for (int kk = T.lo + lane; kk < T.hi; kk += 32) wl[kk - T.lo] = __ldcg(w + kk);
-                __syncwarp();
-                backward_sweep(d, s, T, wl, w, lane);
+                for (int64_t e = l0; e < l1; e += 32) {
+                    const int cnt = (int)min((int64_t)32, l1 - e);
+                    const bool have = lane < cnt;
+                    const int j = have ? s.r.Lrk[e + lane] : 0;
+                    const double a = have ? s.r.Lrx[e + lane] : 0.0;
+                    if (!wait_flags(d, s.fdone, j, have, epoch, budget)) return;
+                    const double v = have ? __ldcg(s.w + q * n + j) : 0.0;
+                    z = chain(z, a, v, cnt);
+                }
+                if (lane == 0) s.w[q * n + i] = z;
             }
+            __threadfence();
             __syncwarp();
-            if (fits)
-                for (int kk = T.lo + lane; kk < T.hi; kk += 32) w[kk] = wl[kk - T.lo];
-            if (it.type != BK_ITEM_FWD)
-                for (int kk = T.lo + lane; kk < T.hi; kk += 32) x[(int64_t)q * ldx + d.Q[kk]] = wl[kk - T.lo];
+            if (lane == 0) st_release(s.fdone + i, epoch);
+        } else {
+            // backward row i: its forward result, then U(i,:), then the diagonal
+            const int i = ~it;
+            if (!wait_flags(d, s.fdone, i, lane == 0, epoch, budget)) return;
+            const int64_t u0 = s.r.Urp[i], u1 = s.r.Urp[i + 1];
+            const double ud = s.r.Ud[i];
+            for (int q = 0; q < nrhs; q++) {
+                double z = __shfl_sync(BK_FULL, lane == 0 ? __ldcg(s.w + q * n + i) : 0.0, 0);
+                for (int64_t e = u0; e < u1; e += 32) {
+                    const int cnt = (int)min((int64_t)32, u1 - e);
+                    const bool have = lane < cnt;
+                    const int j = have ? s.r.Urk[e + lane] : 0;
+                    const double a = have ? s.r.Urx[e + lane] : 0.0;
+                    if (!wait_flags(d, s.bdone, j, have, epoch, budget)) return;
+                    const double v = have ? __ldcg(s.z + q * n + j) : 0.0;
+                    z = chain(z, a, v, cnt);
+                }
+                z = z / ud;
+                if (lane == 0) {
+                    s.z[q * n + i] = z;
+                    x[(int64_t)q * ldx + d.Q[i]] = z;
+                }
+            }
+            __threadfence();
             __syncwarp();
+            if (lane == 0) st_release(s.bdone + i, epoch);
         }
-        __threadfence();
-        __syncwarp();
-        if (lane == 0) st_release(s.item_done + k, epoch);
     }
 }
 
-// L's row indices as pivot steps (for the solve), after every factorization.
-__global__ void bk_lsteps_kernel(bk_dev d, int *Ls)
+int solve_blocks()
 {
-    const int lane = threadIdx.x & 31;
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (int c = warp; c < d.n; c += nwarps) {
-        const int64_t lb = d.Lbeg[c];
-        const int lc = d.Lcnt[c];
-        for (int t = lane; t < lc; t += 32) Ls[lb + t] = d.pinv[d.Li[lb + t]];
+    static int blocks = 0;
+    if (!blocks) {
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, bk_solve_kernel, 128, 0);
+        blocks = std::max(1, sms) * std::max(1, std::min(per, 8));
     }
+    return blocks;
+}
+
+void launch_scan(const int32_t *cnt, int32_t m, int64_t *part, int64_t *out, cudaStream_t st)
+{
+    const int nb = std::max(1, (m + 1023) / 1024);
+    bk_scan_sums<<<nb, 1024, 0, st>>>(cnt, m, part);
+    bk_scan_parts<<<1, 1024, 0, st>>>(part, nb);
+    bk_scan_apply<<<nb, 1024, 0, st>>>(cnt, m, part, out);
 }
 
 }  // namespace
+
+void bk_launch_rows(const bk_dev &d, const bk_rows &r, void *stream)
+{
+    if (d.n <= 0) return;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int n = d.n;
+    const int blocks = std::max(1, std::min((n + 7) / 8, 152 * 8));
+    cudaMemsetAsync(r.cnt, 0, sizeof(int32_t) * 2 * ((size_t)n + 1), st);
+    bk_rows_count<<<blocks, 256, 0, st>>>(d, r);
+    launch_scan(r.cnt, n, r.part, r.Lrp, st);
+    launch_scan(r.cnt + n + 1, n, r.part, r.Urp, st);
+    cudaMemsetAsync(r.cnt, 0, sizeof(int32_t) * 2 * ((size_t)n + 1), st);
+    bk_rows_scatter<<<blocks, 256, 0, st>>>(d, r, 0);
+    bk_rows_sort<<<blocks, 256, 0, st>>>(n, r.Lrp, r.tk, r.tx, r.Lrk, r.Lrx, 0);
+    bk_rows_scatter<<<blocks, 256, 0, st>>>(d, r, 1);
+    bk_rows_sort<<<blocks, 256, 0, st>>>(n, r.Urp, r.tk, r.tx, r.Urk, r.Urx, 1);
+}
 
 void bk_launch_solve(const bk_dev &d, const bk_solve_dev &s, int32_t nrhs, const double *b, int32_t ldb,
                      double *x, int32_t ldx, int32_t epoch, long long budget, void *stream)
 {
     if (s.nitems <= 0) return;
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    static int attr_set = -1;
-    if (attr_set != (int)s.smem_bytes) {
-        cudaFuncSetAttribute(bk_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.smem_bytes);
-        attr_set = (int)s.smem_bytes;
-    }
-    const int per_sm = s.smem_bytes > 0 ? std::max<int>(1, std::min<int>(16, (int)(200 * 1024 / s.smem_bytes))) : 16;
-    const int ctas = std::min<int>(s.nitems, std::max(1, sms) * per_sm);
-    bk_solve_kernel<<<ctas, 32, (size_t)s.smem_bytes, (cudaStream_t)stream>>>(d, s, nrhs, b, ldb, x, ldx, epoch,
-                                                                               budget);
-}
-
-void bk_launch_lsteps(const bk_dev &d, int *Ls, void *stream)
-{
-    if (d.n <= 0) return;
-    const int blocks = std::max(1, std::min((d.n + 7) / 8, 152 * 8));
-    bk_lsteps_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(d, Ls);
+    const int ctas = std::min<int>((s.nitems + 3) / 4, solve_blocks());
+    bk_solve_kernel<<<ctas, 128, 0, (cudaStream_t)stream>>>(d, s, nrhs, b, ldb, x, ldx, epoch, budget);
 }

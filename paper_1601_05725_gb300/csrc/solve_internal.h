@@ -1,4 +1,4 @@
-// solve_internal.h -- work items of the BTF / ND solve (kernels_solve.cu).
+// solve_internal.h -- the BTF solve by rows (kernels_solve.cu, solve_plan.cpp).
 #pragma once
 
 #include <cstdint>
@@ -6,39 +6,37 @@
 
 #include "basker_internal.h"
 
-enum { BK_ITEM_BLOCK = 0, BK_ITEM_FWD = 1, BK_ITEM_BWD = 2 };
-
-struct bk_sitem {
-    int32_t type;
-    int32_t task;
-    int32_t dep_beg, dep_end;     // items to wait for (indices into deps)
-    int32_t desc_beg, desc_end;   // FWD: descendant tasks whose buffers hold this node's terms
+// Factors by rows in pivot-step space, rebuilt after every factorization: row i
+// of L holds (k, L(i,k)) for k < i in ascending k; row i of U holds (k, U(i,k))
+// for k > i in descending k; Ud[i] = U(i,i).  Row-wise evaluation in these orders
+// performs, for every entry of the solution, the same fma sequence as the
+// column-wise sweeps of the BTF solve.
+struct bk_rows {
+    int64_t *Lrp, *Urp;          // n + 1 row starts
+    int32_t *Lrk, *Urk;          // column steps
+    double *Lrx, *Urx;           // values
+    int32_t *tk;                 // unsorted scatter (steps), capacity max(L, U) entries
+    double *tx;                  // unsorted scatter (values)
+    double *Ud;                  // n diagonal entries of U
+    int32_t *cnt;                // 2 (n + 1) row counts and cursors
+    int64_t *part;               // per-block partial sums of the row-start scan
 };
 
 struct bk_solve_dev {
-    int32_t nitems;
-    const bk_sitem *items;
-    const int32_t *deps;
-    const int32_t *desc;
-    int32_t *item_done;
-    const int32_t *offp, *offj, *offpos;   // coupling entries of B by row: columns of later blocks
-    const int64_t *acc_off;                // per task: first slot of its contribution buffer
-    int64_t acc_stride;                    // slots per right-hand side
-    double *acc;
-    double *w;                             // n x nrhs, indexed by pivot step
-    const int32_t *Ls;                     // L's row indices as pivot steps
-    int64_t smem_bytes;                    // dynamic shared memory of the solve kernel
+    int32_t nitems;               // 2 n: every step forward, then backward, block by block
+    const int32_t *items;         // k >= 0: forward row k; ~k: backward row k
+    const int32_t *offp, *offj, *offpos;  // coupling of B by row: columns of later blocks
+    int32_t *fdone, *bdone;       // per-step flags of the forward and the backward pass
+    double *w;                    // n x nrhs, forward results by step
+    double *z;                    // n x nrhs, the solution by step
+    bk_rows r;
 };
 
 struct bk_solve_plan {
-    std::vector<bk_sitem> items;
-    std::vector<int32_t> deps, desc, offp, offj, offpos;
-    std::vector<int64_t> acc_off;
-    int64_t acc_stride = 0;
-    int64_t smem_bytes = 0;                // largest item (own rows + ancestor buffer), capped
+    std::vector<int32_t> items, offp, offj, offpos;
 };
 
 void bk_solve_plan_build(const bk_plan &pl, bk_solve_plan &sp);
-void bk_launch_lsteps(const bk_dev &d, int *Ls, void *stream);
+void bk_launch_rows(const bk_dev &d, const bk_rows &r, void *stream);
 void bk_launch_solve(const bk_dev &d, const bk_solve_dev &s, int32_t nrhs, const double *b, int32_t ldb,
                      double *x, int32_t ldx, int32_t epoch, long long budget, void *stream);
