@@ -64,6 +64,8 @@ enum { BK_DD_RESOLVE = 1, BK_DD_DESC = 2 };    // refactor round flags of a task
 struct bk_dev {
     int32_t n;
     int32_t ntasks;
+    int32_t prec;                    // arithmetic of the factorization: 0 FP64, 1 FP32 (value
+                                     // arrays keep 8-byte slots; FP32 uses them as float arrays)
     const int32_t *Bp, *Bi, *dstart, *bmap, *col_task;
     double *Bx;
     bk_task *tasks;
@@ -106,6 +108,9 @@ struct bk_dev {
     const int32_t *block_ptr;
     const int32_t *P, *Q;
 };
+
+// Value arrays seen in the factorization's arithmetic type V.
+template <typename V> __host__ __device__ __forceinline__ V *vals(double *p) { return reinterpret_cast<V *>(p); }
 
 // Host-side plan built by the symbolic pass.
 struct bk_plan {

@@ -31,7 +31,8 @@ __device__ __forceinline__ bool flag_wait(const bk_dev &d, const int *flag, int 
 }
 
 // Zero x over column c's stored pattern (its rows of B are a subset).
-__device__ __forceinline__ void clear_stored(const bk_dev &d, const bk_task &T, double *x, int c, int lane)
+template <typename V>
+__device__ __forceinline__ void clear_stored(const bk_dev &d, const bk_task &T, V *x, int c, int lane)
 {
     const int base = T.sp_lo;
     const int64_t ub = d.Ubeg[c];
@@ -68,11 +69,15 @@ __device__ __forceinline__ void clear_stored(const bk_dev &d, const bk_task &T, 
 // input).
 constexpr int FIX_PF = 8;
 
-__device__ __forceinline__ bool pattern_column(const bk_dev &d, const bk_task &T, int tid, double *x, int c,
+template <typename V>
+__device__ __forceinline__ bool pattern_column(const bk_dev &d, const bk_task &T, int tid, V *x, int c,
                                                int epoch, long long budget, double tau, int lane, bool wait_all,
                                                int wait_lo, bool &ok_out, bool &bad_out, bool &broken_out,
                                                const int *pchg = nullptr, bool *aborted = nullptr)
 {
+    const V *const Bx = vals<V>(d.Bx);
+    V *const Lx = vals<V>(d.Lx);
+    V *const Ux = vals<V>(d.Ux);
     const int base = T.sp_lo;
     const int own_lo = T.lo - base, own_hi = T.hi - base;
     bool broken = false, bad = false;
@@ -80,7 +85,7 @@ __device__ __forceinline__ bool pattern_column(const bk_dev &d, const bk_task &T
     for (int e = d.dstart[c] + lane; e < e1; e += 32) {
         const int s = slot_of(T, base, d.Bi[e]);
         if (s < 0) { broken = true; continue; }
-        x[s] = d.Bx[e];
+        x[s] = Bx[e];
     }
     // rows of L(:,c) and the pivot row, for the selection at the end
     const int64_t lb = d.Lbeg[c];
@@ -123,7 +128,7 @@ __device__ __forceinline__ bool pattern_column(const bk_dev &d, const bk_task &T
         }
         // rows (and, for a finished step, values) of the chunk's first step
         int rr[FIX_PF];
-        double ll[FIX_PF];
+        V ll[FIX_PF];
         {
             const int64_t jl0 = __shfl_sync(BK_FULL, jl_l, 0);
             const int jc0 = __shfl_sync(BK_FULL, jc_l, 0);
@@ -131,7 +136,7 @@ __device__ __forceinline__ bool pattern_column(const bk_dev &d, const bk_task &T
             for (int u = 0; u < FIX_PF; u++) {
                 const int q = lane + 32 * u;
                 rr[u] = q < jc0 ? __ldcg(d.Li + jl0 + q) : -1;
-                ll[u] = (q < jc0 && !(pending & 1u)) ? __ldcg(d.Lx + jl0 + q) : 0.0;
+                ll[u] = (q < jc0 && !(pending & 1u)) ? __ldcg(Lx + jl0 + q) : 0.0;
             }
         }
         for (int t = 0; t < nin; ++t) {
@@ -141,8 +146,8 @@ __device__ __forceinline__ bool pattern_column(const bk_dev &d, const bk_task &T
             const int jc = __shfl_sync(BK_FULL, jc_l, t);
             // x(prow j) and the x values under L(:,j); all earlier steps are stored
             int ss[FIX_PF];
-            double xv[FIX_PF];
-            const double m = sp >= 0 ? x[sp] : 0.0;
+            V xv[FIX_PF];
+            const V m = sp >= 0 ? x[sp] : 0.0;
 #pragma unroll
             for (int u = 0; u < FIX_PF; u++) {
                 ss[u] = rr[u] >= 0 ? slot_of(T, base, rr[u]) : -1;
@@ -159,12 +164,12 @@ __device__ __forceinline__ bool pattern_column(const bk_dev &d, const bk_task &T
 #pragma unroll
                 for (int u = 0; u < FIX_PF; u++) {
                     const int q = lane + 32 * u;
-                    if (q < jc) ll[u] = __ldcg(d.Lx + jl + q);
+                    if (q < jc) ll[u] = __ldcg(Lx + jl + q);
                 }
             }
             // the next step's rows and, if it has finished, values
             int rn[FIX_PF];
-            double ln[FIX_PF];
+            V ln[FIX_PF];
             {
                 const int tn = t + 1 < nin ? t + 1 : t;
                 const int64_t jln = __shfl_sync(BK_FULL, jl_l, tn);
@@ -174,14 +179,14 @@ __device__ __forceinline__ bool pattern_column(const bk_dev &d, const bk_task &T
                 for (int u = 0; u < FIX_PF; u++) {
                     const int q = lane + 32 * u;
                     rn[u] = q < jcn ? __ldcg(d.Li + jln + q) : -1;
-                    ln[u] = (q < jcn && !pn) ? __ldcg(d.Lx + jln + q) : 0.0;
+                    ln[u] = (q < jcn && !pn) ? __ldcg(Lx + jln + q) : 0.0;
                 }
             }
             if (sp >= 0) {
                 __syncwarp();
                 if (lane == 0) {
                     x[sp] = 0.0;
-                    d.Ux[ub + k0 + t] = m;
+                    Ux[ub + k0 + t] = m;
                 }
                 if (!isfinite(m)) bad = true;
 #pragma unroll
@@ -190,7 +195,7 @@ __device__ __forceinline__ bool pattern_column(const bk_dev &d, const bk_task &T
                 // entries past the register window, in batches
                 for (int q0 = 32 * FIX_PF; q0 < jc; q0 += 32 * FIX_PF) {
                     int sb[FIX_PF];
-                    double lb2[FIX_PF], xb[FIX_PF];
+                    V lb2[FIX_PF], xb[FIX_PF];
 #pragma unroll
                     for (int u = 0; u < FIX_PF; u++) {
                         const int q = q0 + lane + 32 * u;
@@ -198,7 +203,7 @@ __device__ __forceinline__ bool pattern_column(const bk_dev &d, const bk_task &T
                         lb2[u] = 0.0;
                         if (q < jc) {
                             sb[u] = slot_of(T, base, __ldcg(d.Li + jl + q));
-                            lb2[u] = __ldcg(d.Lx + jl + q);
+                            lb2[u] = __ldcg(Lx + jl + q);
                             if (sb[u] < 0) broken = true;
                         }
                     }
@@ -218,10 +223,10 @@ __device__ __forceinline__ bool pattern_column(const bk_dev &d, const bk_task &T
         }
     }
     // Algorithm 1's pivot selection, validated for the stored pivot row
-    const double xp = x[sp_c];
-    double amax = fabs(xp);
+    const V xp = x[sp_c];
+    V amax = fabs(xp);
     if (!isfinite(xp)) bad = true;
-    double v[FIX_PF];
+    V v[FIX_PF];
 #pragma unroll
     for (int u = 0; u < FIX_PF; u++) v[u] = fs[u] >= 0 ? x[fs[u]] : 0.0;
 #pragma unroll
@@ -230,16 +235,16 @@ __device__ __forceinline__ bool pattern_column(const bk_dev &d, const bk_task &T
         if (!isfinite(v[u])) bad = true;
         if (fs[u] >= own_lo && fs[u] < own_hi) amax = fmax(amax, fabs(v[u]));
         x[fs[u]] = 0.0;
-        d.Lx[lb + lane + 32 * u] = v[u] / xp;
+        Lx[lb + lane + 32 * u] = v[u] / xp;
     }
     for (int t = 32 * FIX_PF + lane; t < lc; t += 32) {
         const int s = slot_of(T, base, d.Li[lb + t]);
         if (s < 0) { broken = true; continue; }
-        const double w = x[s];
+        const V w = x[s];
         x[s] = 0.0;
         if (!isfinite(w)) bad = true;
         if (s >= own_lo && s < own_hi) amax = fmax(amax, fabs(w));
-        d.Lx[lb + t] = w / xp;
+        Lx[lb + t] = w / xp;
     }
     amax = warp_max(amax);
     bad = __any_sync(BK_FULL, bad);
@@ -247,10 +252,10 @@ __device__ __forceinline__ bool pattern_column(const bk_dev &d, const bk_task &T
     __syncwarp();
     if (lane == 0) {
         x[sp_c] = 0.0;
-        d.Ux[ub + nsteps] = xp;
+        Ux[ub + nsteps] = xp;
     }
     __syncwarp();
-    ok_out = !bad && !broken && amax > 0.0 && fabs(xp) >= tau * amax;
+    ok_out = !bad && !broken && amax > V(0) && (double)fabs(xp) >= tau * (double)amax;
     bad_out = bad;
     broken_out = broken;
     return true;

@@ -41,7 +41,8 @@ __device__ __forceinline__ int row_of_lslot(const bk_task &T, int ls)
     return -1;
 }
 
-__device__ __forceinline__ double warp_max(double v)
+template <typename V>
+__device__ __forceinline__ V warp_max(V v)
 {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(BK_FULL, v, o));

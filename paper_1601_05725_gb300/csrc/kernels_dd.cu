@@ -106,15 +106,17 @@ __device__ __forceinline__ int build_list(const volatile uint32_t *rb, int nrw, 
 // read only when column j is final in this round (full); pinv of the rows is
 // final for every column after the round's resolve column.
 constexpr int RSTEP_PF = 4;
+template <typename V>
 struct RStep {
     int sp, jc, why;
     int64_t jl;
     bool full;
     int s[RSTEP_PF], bit[RSTEP_PF];
-    double l[RSTEP_PF];
+    V l[RSTEP_PF];
 };
 
-__device__ __forceinline__ void read_step(const bk_dev &d, const bk_task &T, RStep &st, int j, int c, int s0,
+template <typename V>
+__device__ __forceinline__ void read_step(const bk_dev &d, const bk_task &T, RStep<V> &st, int j, int c, int s0,
                                           int epoch, int lane, int ndesc, bool after_wait = false)
 {
     const int base = T.sp_lo;
@@ -137,7 +139,7 @@ __device__ __forceinline__ void read_step(const bk_dev &d, const bk_task &T, RSt
         st.l[u] = 0.0;
         if (!dn || q >= st.jc) continue;
         const int r = __ldcg(d.Li + st.jl + q);
-        st.l[u] = __ldcg(d.Lx + st.jl + q);
+        st.l[u] = __ldcg(vals<V>(d.Lx) + st.jl + q);
         const int s = slot_of(T, base, r);
         if (s < 0) { st.why = 65; continue; }
         st.s[u] = s;
@@ -153,10 +155,14 @@ __device__ __forceinline__ void read_step(const bk_dev &d, const bk_task &T, RSt
     }
 }
 
+template <typename V>
 __global__ void __launch_bounds__(128) bk_dd_kernel(bk_dev d, const int32_t *__restrict__ cols, int32_t ncols,
                                                     int32_t *counter, double tau, int32_t epoch, long long budget,
                                                     int32_t refno)
 {
+    const V *const Bx = vals<V>(d.Bx);
+    V *const Lx = vals<V>(d.Lx);
+    V *const Ux = vals<V>(d.Ux);
     __shared__ bk_task Ts[4];
     __shared__ int rlist[4 * RLIST];
     extern __shared__ uint32_t dd_bits[];
@@ -266,7 +272,7 @@ __global__ void __launch_bounds__(128) bk_dd_kernel(bk_dev d, const int32_t *__r
             }
             if (mode == 1) {
                 bool ok = false, bad = false, broken = false, aborted = false;
-                double *xs = reinterpret_cast<double *>(slice);
+                V *xs = reinterpret_cast<V *>(slice);
                 if (!pattern_column(d, T, tid, xs, c, epoch, budget, tau, lane, false, s0, ok, bad, broken,
                                    d.pchg_ep, &aborted))
                     return;
@@ -296,7 +302,7 @@ __global__ void __launch_bounds__(128) bk_dd_kernel(bk_dev d, const int32_t *__r
         const int lsp = T.lspace;
         const int nsw = (nsteps + 31) >> 5;
         const int nrw = (lsp + 31) >> 5;
-        double *x = reinterpret_cast<double *>(slice);
+        V *x = reinterpret_cast<V *>(slice);
         volatile uint32_t *sb = d.dd_words ? wbits : reinterpret_cast<uint32_t *>(x + T.space);
         volatile uint32_t *rb = sb + nsw;
         bool bad = false, overflow = false;
@@ -312,7 +318,7 @@ __global__ void __launch_bounds__(128) bk_dd_kernel(bk_dev d, const int32_t *__r
             const int r = d.Bi[e];
             const int s = slot_of(T, base, r);
             if (s < 0) { if (!why) why = 61; continue; }
-            x[s] = d.Bx[e];
+            x[s] = Bx[e];
             const int p = s < T.hi - base ? __ldcg(d.pinv + r) : -1;
             if (p >= 0 && p < c && p >= base) set_bit(sb, p - base);
             else if (s >= ndesc) set_bit(rb, s - ndesc);
@@ -325,7 +331,7 @@ __global__ void __launch_bounds__(128) bk_dd_kernel(bk_dev d, const int32_t *__r
         // that the current one adds below the prediction is read when it is found.
         int w0 = 0;
         int jb = next_step_bit(sb, nsw, w0, lane);
-        RStep cur, nxt;
+        RStep<V> cur, nxt;
         if (jb >= 0) read_step(d, T, cur, base + jb, c, s0, epoch, lane, ndesc);
         for (int iter = 0; jb >= 0; iter++) {
             const int j = base + jb;
@@ -342,8 +348,8 @@ __global__ void __launch_bounds__(128) bk_dd_kernel(bk_dev d, const int32_t *__r
             }
             const int sp = cur.sp;
             if (sp < 0) { if (!why) why = 64; break; }
-            const double m = x[sp];
-            double xv[RSTEP_PF];
+            const V m = x[sp];
+            V xv[RSTEP_PF];
 #pragma unroll
             for (int u = 0; u < RSTEP_PF; u++) xv[u] = cur.s[u] >= 0 ? x[cur.s[u]] : 0.0;
             const int oldu = (lane == 0 && ub == old_ub && nu < old_uc - 1) ? d.Ui[ub + nu] : -1;
@@ -360,7 +366,7 @@ __global__ void __launch_bounds__(128) bk_dd_kernel(bk_dev d, const int32_t *__r
                 } else {
                     for (int q = lane; q < nu; q += 32) {
                         d.Ui[nb + q] = d.Ui[ub + q];
-                        d.Ux[nb + q] = d.Ux[ub + q];
+                        Ux[nb + q] = Ux[ub + q];
                     }
                     __syncwarp();
                     ub = nb;
@@ -373,7 +379,7 @@ __global__ void __launch_bounds__(128) bk_dd_kernel(bk_dev d, const int32_t *__r
             }
             if (!overflow && lane == 0) {
                 d.Ui[ub + nu] = j;
-                d.Ux[ub + nu] = m;
+                Ux[ub + nu] = m;
             }
 #pragma unroll
             for (int u = 0; u < RSTEP_PF; u++) {
@@ -385,7 +391,7 @@ __global__ void __launch_bounds__(128) bk_dd_kernel(bk_dev d, const int32_t *__r
             if (cur.why && !why) why = cur.why;
             for (int q = 32 * RSTEP_PF + lane; q < cur.jc; q += 32) {
                 const int r = __ldcg(d.Li + cur.jl + q);
-                const double l = __ldcg(d.Lx + cur.jl + q);
+                const V l = __ldcg(Lx + cur.jl + q);
                 const int s1 = slot_of(T, base, r);
                 if (s1 < 0) { if (!why) why = 65; continue; }
                 x[s1] = fma(-l, m, x[s1]);
@@ -413,14 +419,14 @@ __global__ void __launch_bounds__(128) bk_dd_kernel(bk_dev d, const int32_t *__r
         // pattern's row slots are listed in ascending order, a segment of at most
         // RLIST at a time, and their values read eight per lane at once.
         int *list = rlist + wib * RLIST;
-        double amax = 0.0;
+        V amax = 0.0;
         int ncand = 0, nrows = 0;
         for (int wcur = 0; wcur < nrw;) {
             const int filled = build_list(rb, nrw, wcur, list, lane);
             nrows += filled;
             for (int i0 = 0; i0 < filled; i0 += 32 * RL_PF) {
                 int ls[RL_PF];
-                double v[RL_PF];
+                V v[RL_PF];
 #pragma unroll
                 for (int u = 0; u < RL_PF; u++) {
                     const int i = i0 + lane + 32 * u;
@@ -451,7 +457,7 @@ __global__ void __launch_bounds__(128) bk_dd_kernel(bk_dev d, const int32_t *__r
         int piv = -1;
         bool ok = false;
         if (!bad && ncand > 0 && amax > 0.0) {
-            if (in_pattern(pref) && fabs(x[ndesc + pref - T.lo]) >= tau * amax) {
+            if (in_pattern(pref) && (double)fabs(x[ndesc + pref - T.lo]) >= tau * (double)amax) {
                 piv = pref;
                 ok = true;
             } else if (resolve) {
@@ -462,7 +468,7 @@ __global__ void __launch_bounds__(128) bk_dd_kernel(bk_dev d, const int32_t *__r
                     const int filled = build_list(rb, nw_own, wcur, list, lane);
                     for (int i0 = 0; i0 < filled; i0 += 32 * RL_PF) {
                         int ls[RL_PF];
-                        double v[RL_PF];
+                        V v[RL_PF];
 #pragma unroll
                         for (int u = 0; u < RL_PF; u++) {
                             const int i = i0 + lane + 32 * u;
@@ -487,7 +493,7 @@ __global__ void __launch_bounds__(128) bk_dd_kernel(bk_dev d, const int32_t *__r
         if (piv < 0) piv = pcur;                     // keep the speculation consistent
         const int pls = piv - T.lo;
         const bool pin = in_pattern(piv);
-        const double xp = pin ? x[ndesc + pls] : 0.0;
+        const V xp = pin ? x[ndesc + pls] : 0.0;
         // L(:,c) = x / pivot over the pattern's unpivoted rows; clear the state
         {
             const int cnt_all = nrows - (pin ? 1 : 0);
@@ -518,7 +524,7 @@ __global__ void __launch_bounds__(128) bk_dd_kernel(bk_dev d, const int32_t *__r
             for (int i0 = 0; i0 < filled; i0 += 32 * RL_PF) {
                 int ls[RL_PF], oldr[RL_PF];
                 int64_t qq[RL_PF];
-                double v[RL_PF];
+                V v[RL_PF];
 #pragma unroll
                 for (int u = 0; u < RL_PF; u++) {
                     const int i = i0 + lane + 32 * u;
@@ -535,7 +541,7 @@ __global__ void __launch_bounds__(128) bk_dd_kernel(bk_dev d, const int32_t *__r
                         const int r = row_of_lslot(T, ls[u]);
                         if (oldr[u] != r) same = false;
                         d.Li[qq[u]] = r;
-                        d.Lx[qq[u]] = v[u] / xp;
+                        Lx[qq[u]] = v[u] / xp;
                     }
                     x[ndesc + ls[u]] = 0.0;
                 }
@@ -553,7 +559,7 @@ __global__ void __launch_bounds__(128) bk_dd_kernel(bk_dev d, const int32_t *__r
             if (why) report_internal(d.status, c, why);
             if (!overflow) {
                 d.Ui[ub + nu] = c;
-                d.Ux[ub + nu] = xp;
+                Ux[ub + nu] = xp;
                 d.Ucnt[c] = nu + 1;
                 d.Lcnt[c] = (int)(lpos - lb);
             } else {
@@ -594,8 +600,16 @@ void bk_launch_dd(const bk_dev &d, const int32_t *cols, int32_t ncols, int32_t *
     if (ncols <= 0) return;
     int warps = std::min<int>(ncols, d.wsd_warps);
     const size_t smem = (size_t)4 * d.dd_words * sizeof(uint32_t);
-    if (smem > 48 * 1024)
-        cudaFuncSetAttribute(bk_dd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    bk_dd_kernel<<<(warps + 3) / 4, 128, smem, (cudaStream_t)stream>>>(d, cols, ncols, counter, tau, epoch,
-                                                                        budget, refno);
+    const int grid = (warps + 3) / 4;
+    if (d.prec) {
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(bk_dd_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        bk_dd_kernel<float><<<grid, 128, smem, (cudaStream_t)stream>>>(d, cols, ncols, counter, tau, epoch, budget,
+                                                                        refno);
+    } else {
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(bk_dd_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        bk_dd_kernel<double><<<grid, 128, smem, (cudaStream_t)stream>>>(d, cols, ncols, counter, tau, epoch, budget,
+                                                                         refno);
+    }
 }

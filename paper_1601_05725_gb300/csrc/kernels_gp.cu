@@ -34,12 +34,14 @@ using namespace bk;
 
 namespace {
 
-__global__ void bk_gather_kernel(double *__restrict__ Bx, const double *__restrict__ vals,
+// B's values in the factorization's type (FP32: rounded to nearest from FP64).
+template <typename V>
+__global__ void bk_gather_kernel(V *__restrict__ Bx, const double *__restrict__ vals,
                                  const int32_t *__restrict__ bmap, int64_t nnz)
 {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz;
          e += (int64_t)gridDim.x * blockDim.x)
-        Bx[e] = __ldg(vals + bmap[e]);
+        Bx[e] = (V)__ldg(vals + bmap[e]);
 }
 
 __device__ __forceinline__ void set_bit(volatile uint32_t *bm, int i)
@@ -77,10 +79,15 @@ __device__ __forceinline__ int next_step_bit(const volatile uint32_t *bm, int nw
 // pref_mode: 0 prefer the natural row; 1 prefer pref[c]; 2 a redo from task_c0
 // that recomputes only the columns whose stored pattern meets a touched row
 // (or that rejected their preferred pivot) and keeps the others.
+template <typename V>
 __global__ void __launch_bounds__(32) bk_gp_task_kernel(bk_dev d, const int32_t *__restrict__ task_ids,
                                                         const int32_t *__restrict__ task_c0, double tau,
                                                         int pref_mode)
 {
+    const V *const Bx = vals<V>(d.Bx);
+    V *const Lx = vals<V>(d.Lx);
+    V *const Ux = vals<V>(d.Ux);
+    V *const Ahat = vals<V>(d.ahat);
     __shared__ bk_task T;
     extern __shared__ __align__(16) unsigned char dsm[];
     const int lane = threadIdx.x;
@@ -96,8 +103,8 @@ __global__ void __launch_bounds__(32) bk_gp_task_kernel(bk_dev d, const int32_t 
     // spinv / sprow / slbeg / slcnt cache pinv, prow, Lbeg, Lcnt of the node's own
     // rows and columns (written through to global memory when they change).
     unsigned char *area = T.wsoff < 0 ? dsm : d.ws + T.wsoff;
-    double *x = reinterpret_cast<double *>(area);
-    int64_t *slbeg = reinterpret_cast<int64_t *>(x + lsp);
+    V *x = reinterpret_cast<V *>(area);
+    int64_t *slbeg = reinterpret_cast<int64_t *>(area + (size_t)lsp * 8);
     uint32_t *s32 = reinterpret_cast<uint32_t *>(slbeg + nown);
     volatile uint32_t *sb = s32;
     volatile uint32_t *rb = s32 + nsw;
@@ -166,7 +173,7 @@ __global__ void __launch_bounds__(32) bk_gp_task_kernel(bk_dev d, const int32_t 
         if (sep) {
             // A-hat(:,c) = the column after all descendant steps (Algorithm 4's solves with L_ii and reductions)
             nu = d.dcnt[c];
-            const double *ah = d.ahat + T.ahoff + (int64_t)(c - T.lo) * lsp;
+            const V *ah = Ahat + T.ahoff + (int64_t)(c - T.lo) * lsp;
             const uint32_t *ab = d.abits + T.aboff + (int64_t)(c - T.lo) * nrw;
             for (int w = lane; w < nrw; w += 32) {
                 uint32_t bits = ab[w];
@@ -188,7 +195,7 @@ __global__ void __launch_bounds__(32) bk_gp_task_kernel(bk_dev d, const int32_t 
                 const int r = d.Bi[e];
                 const int s = slot_of(T, base, r);
                 if (s < 0) { report_internal(d.status, c, 11); continue; }
-                x[s] = d.Bx[e];
+                x[s] = Bx[e];
                 const int p = s < nown ? spinv[s] : -1;
                 if (p >= 0 && p < c) {
                     if (p >= base) set_bit(sb, p - base);
@@ -211,7 +218,7 @@ __global__ void __launch_bounds__(32) bk_gp_task_kernel(bk_dev d, const int32_t 
                 if (lane == 0) report_internal(d.status, c, 13);
                 return;
             }
-            const double m = x[sp];
+            const V m = x[sp];
             __syncwarp();
             if (lane == 0) {
                 atomicAnd(const_cast<uint32_t *>(sb) + (jb >> 5), ~(1u << (jb & 31)));
@@ -230,7 +237,7 @@ __global__ void __launch_bounds__(32) bk_gp_task_kernel(bk_dev d, const int32_t 
                 }
                 for (int k = lane; k < nu; k += 32) {
                     d.Ui[nb + k] = d.Ui[ub + k];
-                    d.Ux[nb + k] = d.Ux[ub + k];
+                    Ux[nb + k] = Ux[ub + k];
                 }
                 __syncwarp();
                 ub = nb;
@@ -242,14 +249,14 @@ __global__ void __launch_bounds__(32) bk_gp_task_kernel(bk_dev d, const int32_t 
             }
             if (lane == 0) {
                 d.Ui[ub + nu] = j;
-                d.Ux[ub + nu] = m;
+                Ux[ub + nu] = m;
             }
             nu++;
             const int64_t jl = slbeg[jb];
             const int jc = slcnt[jb];
             for (int k = lane; k < jc; k += 32) {
                 const int r = d.Li[jl + k];
-                const double l = d.Lx[jl + k];
+                const V l = Lx[jl + k];
                 const int s = slot_of(T, base, r);
                 if (s < 0) { report_internal(d.status, c, 14); continue; }
                 x[s] = fma(-l, m, x[s]);
@@ -265,7 +272,7 @@ __global__ void __launch_bounds__(32) bk_gp_task_kernel(bk_dev d, const int32_t 
         }
 
         // Algorithm 1's pivot selection: threshold pivot among the unpivoted own rows
-        double amax = 0.0;
+        V amax = 0.0;
         int ncand = 0;
         for (int w = lane; w < nrw; w += 32) {
             uint32_t bits = rb[w];
@@ -273,7 +280,7 @@ __global__ void __launch_bounds__(32) bk_gp_task_kernel(bk_dev d, const int32_t 
                 const int b = __ffs(bits) - 1;
                 bits &= bits - 1;
                 const int ls = (w << 5) + b;
-                const double v = x[ls];
+                const V v = x[ls];
                 if (!isfinite(v)) bad = true;
                 if (ls < nown) {
                     ncand++;
@@ -288,7 +295,7 @@ __global__ void __launch_bounds__(32) bk_gp_task_kernel(bk_dev d, const int32_t 
         if (!bad && ncand > 0 && amax > 0.0) {
             const int pref = pref_mode ? d.pref[c] : c;
             if (pref >= T.lo && pref < T.hi && (spinv[pref - base] < 0 || spinv[pref - base] >= c) &&
-                fabs(x[pref - base]) >= tau * amax) {
+                (double)fabs(x[pref - base]) >= tau * (double)amax) {
                 piv = pref;
             } else {
                 int best = INT_MAX;
@@ -312,10 +319,10 @@ __global__ void __launch_bounds__(32) bk_gp_task_kernel(bk_dev d, const int32_t 
         }
 
         // Algorithm 1's copy to L and U: U(:,c) got the steps above, the pivot closes it, L(:,c) = x / pivot
-        const double xp = x[piv - base];
+        const V xp = x[piv - base];
         if (lane == 0) {
             d.Ui[ub + nu] = c;
-            d.Ux[ub + nu] = xp;
+            Ux[ub + nu] = xp;
         }
         nu++;
         const int pl = piv - base;
@@ -361,7 +368,7 @@ __global__ void __launch_bounds__(32) bk_gp_task_kernel(bk_dev d, const int32_t 
                 bits &= bits - 1;
                 const int ls = (w << 5) + b;
                 d.Li[q] = row_of_lslot(T, ls);
-                d.Lx[q] = x[ls] / xp;
+                Lx[q] = x[ls] / xp;
                 x[ls] = 0.0;
                 q++;
             }
@@ -388,9 +395,14 @@ __global__ void __launch_bounds__(32) bk_gp_task_kernel(bk_dev d, const int32_t 
 // Descendant phase of separator columns (one warp per column, persistent).
 // Column space: subtree rows [sp_lo, hi) then ancestors (base = sp_lo); the step
 // bitmap covers descendant steps [sp_lo, lo) only.
+template <typename V>
 __global__ void __launch_bounds__(128) bk_gp_desc_kernel(bk_dev d, const int32_t *__restrict__ cols,
                                                          int32_t ncols, int32_t *counter)
 {
+    const V *const Bx = vals<V>(d.Bx);
+    V *const Lx = vals<V>(d.Lx);
+    V *const Ux = vals<V>(d.Ux);
+    V *const Ahat = vals<V>(d.ahat);
     __shared__ bk_task Ts[4];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
@@ -416,7 +428,7 @@ __global__ void __launch_bounds__(128) bk_gp_desc_kernel(bk_dev d, const int32_t
         const int lsp = T.lspace;
         const int nsw = (ndesc + 31) >> 5;
         const int nrw = (lsp + 31) >> 5;
-        double *x = reinterpret_cast<double *>(slice);
+        V *x = reinterpret_cast<V *>(slice);
         volatile uint32_t *sb = reinterpret_cast<uint32_t *>(x + T.space);
         volatile uint32_t *rb = sb + nsw;
         int64_t ub = d.Ubeg[c], ue = d.Uend[c];
@@ -428,7 +440,7 @@ __global__ void __launch_bounds__(128) bk_gp_desc_kernel(bk_dev d, const int32_t
             const int r = d.Bi[e];
             const int s = slot_of(T, base, r);
             if (s < 0) { report_internal(d.status, c, 16); continue; }
-            x[s] = d.Bx[e];
+            x[s] = Bx[e];
             if (s < ndesc) {
                 const int p = d.pinv[r];            // descendant rows are all pivoted
                 if ((unsigned)(p - base) < (unsigned)ndesc) set_bit(sb, p - base);
@@ -446,7 +458,7 @@ __global__ void __launch_bounds__(128) bk_gp_desc_kernel(bk_dev d, const int32_t
             const int j = base + jb;
             const int sp = d.prow[j] - base;       // descendant row: slot = row - sp_lo
             if (iter > ndesc || (unsigned)sp >= (unsigned)ndesc) { broken = true; break; }
-            const double m = x[sp];
+            const V m = x[sp];
             __syncwarp();
             if (lane == 0) {
                 atomicAnd(const_cast<uint32_t *>(sb) + (jb >> 5), ~(1u << (jb & 31)));
@@ -463,7 +475,7 @@ __global__ void __launch_bounds__(128) bk_gp_desc_kernel(bk_dev d, const int32_t
                 } else {
                     for (int k = lane; k < nu; k += 32) {
                         d.Ui[nb + k] = d.Ui[ub + k];
-                        d.Ux[nb + k] = d.Ux[ub + k];
+                        Ux[nb + k] = Ux[ub + k];
                     }
                     __syncwarp();
                     ub = nb;
@@ -476,14 +488,14 @@ __global__ void __launch_bounds__(128) bk_gp_desc_kernel(bk_dev d, const int32_t
             }
             if (!overflow && lane == 0) {
                 d.Ui[ub + nu] = j;
-                d.Ux[ub + nu] = m;
+                Ux[ub + nu] = m;
             }
             nu++;
             const int64_t jl = d.Lbeg[j];
             const int jc = d.Lcnt[j];
             for (int q = lane; q < jc; q += 32) {
                 const int r = d.Li[jl + q];
-                const double l = d.Lx[jl + q];
+                const V l = Lx[jl + q];
                 const int s = slot_of(T, base, r);
                 if (s < 0) { report_internal(d.status, c, 18); continue; }
                 x[s] = fma(-l, m, x[s]);
@@ -498,7 +510,7 @@ __global__ void __launch_bounds__(128) bk_gp_desc_kernel(bk_dev d, const int32_t
             __syncwarp();
         }
         // A-hat(:,c) on the separator's and ancestors' rows, and its pattern
-        double *ah = d.ahat + T.ahoff + (int64_t)(c - T.lo) * lsp;
+        V *ah = Ahat + T.ahoff + (int64_t)(c - T.lo) * lsp;
         uint32_t *ab = d.abits + T.aboff + (int64_t)(c - T.lo) * nrw;
         for (int w = lane; w < nrw; w += 32) {
             uint32_t bits = rb[w];
@@ -548,7 +560,10 @@ void bk_launch_gather(const bk_dev &d, const double *values, int64_t nnz, void *
 {
     if (nnz <= 0) return;
     int blocks = (int)std::min<int64_t>((nnz + 255) / 256, 152 * 16);
-    bk_gather_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(d.Bx, values, d.bmap, nnz);
+    if (d.prec)
+        bk_gather_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(vals<float>(d.Bx), values, d.bmap, nnz);
+    else
+        bk_gather_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(d.Bx, values, d.bmap, nnz);
 }
 
 void bk_launch_gp_tasks(const bk_dev &d, const int32_t *task_ids, const int32_t *task_c0,
@@ -557,11 +572,16 @@ void bk_launch_gp_tasks(const bk_dev &d, const int32_t *task_ids, const int32_t 
     if (ntasks <= 0) return;
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(bk_gp_task_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(bk_gp_task_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)bk_gp_smem_limit());
+        cudaFuncSetAttribute(bk_gp_task_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)bk_gp_smem_limit());
         attr = true;
     }
-    bk_gp_task_kernel<<<ntasks, 32, smem, (cudaStream_t)stream>>>(d, task_ids, task_c0, tau, pref_mode);
+    if (d.prec)
+        bk_gp_task_kernel<float><<<ntasks, 32, smem, (cudaStream_t)stream>>>(d, task_ids, task_c0, tau, pref_mode);
+    else
+        bk_gp_task_kernel<double><<<ntasks, 32, smem, (cudaStream_t)stream>>>(d, task_ids, task_c0, tau, pref_mode);
 }
 
 void bk_launch_gp_desc(const bk_dev &d, const int32_t *cols, int32_t ncols, int32_t *counter,
@@ -569,7 +589,10 @@ void bk_launch_gp_desc(const bk_dev &d, const int32_t *cols, int32_t ncols, int3
 {
     if (ncols <= 0) return;
     int warps = std::min<int>(ncols, d.wsd_warps);
-    bk_gp_desc_kernel<<<(warps + 3) / 4, 128, 0, (cudaStream_t)stream>>>(d, cols, ncols, counter);
+    if (d.prec)
+        bk_gp_desc_kernel<float><<<(warps + 3) / 4, 128, 0, (cudaStream_t)stream>>>(d, cols, ncols, counter);
+    else
+        bk_gp_desc_kernel<double><<<(warps + 3) / 4, 128, 0, (cudaStream_t)stream>>>(d, cols, ncols, counter);
 }
 
 void bk_launch_reset_pivots(const bk_dev &d, const int32_t *task_ids, const int32_t *task_c0,

@@ -30,6 +30,7 @@ namespace {
 
 // ---------------------------------------------------------------- factors by rows
 
+template <typename V>
 __global__ void bk_rows_count(bk_dev d, bk_rows r)
 {
     const int lane = threadIdx.x & 31;
@@ -43,7 +44,7 @@ __global__ void bk_rows_count(bk_dev d, bk_rows r)
         const int64_t ub = d.Ubeg[c];
         const int un = d.Ucnt[c];
         for (int t = lane; t < un - 1; t += 32) atomicAdd(uc + d.Ui[ub + t], 1);
-        if (lane == 0) r.Ud[c] = d.Ux[ub + un - 1];
+        if (lane == 0) vals<V>(r.Ud)[c] = vals<V>(d.Ux)[ub + un - 1];
     }
 }
 
@@ -114,6 +115,7 @@ __global__ void __launch_bounds__(1024) bk_scan_apply(const int32_t *cnt, int32_
 }
 
 // Entries of L (which = 0) or U (which = 1) into the unsorted row buffer.
+template <typename V>
 __global__ void bk_rows_scatter(bk_dev d, bk_rows r, int which)
 {
     const int lane = threadIdx.x & 31;
@@ -129,7 +131,7 @@ __global__ void bk_rows_scatter(bk_dev d, bk_rows r, int which)
                 const int i = d.pinv[d.Li[lb + t]];
                 const int64_t pos = rp[i] + atomicAdd(cur + i, 1);
                 r.tk[pos] = c;
-                r.tx[pos] = d.Lx[lb + t];
+                vals<V>(r.tx)[pos] = vals<V>(d.Lx)[lb + t];
             }
         } else {
             const int64_t ub = d.Ubeg[c];
@@ -138,7 +140,7 @@ __global__ void bk_rows_scatter(bk_dev d, bk_rows r, int which)
                 const int i = d.Ui[ub + t];
                 const int64_t pos = rp[i] + atomicAdd(cur + i, 1);
                 r.tk[pos] = c;
-                r.tx[pos] = d.Ux[ub + t];
+                vals<V>(r.tx)[pos] = vals<V>(d.Ux)[ub + t];
             }
         }
     }
@@ -146,8 +148,9 @@ __global__ void bk_rows_scatter(bk_dev d, bk_rows r, int which)
 
 // Each row's entries in ascending (L) or descending (U) column order: the rank of
 // an entry is the number of entries of its row that come before it.
-__global__ void bk_rows_sort(int32_t n, const int64_t *rp, const int32_t *tk, const double *tx, int32_t *ok,
-                             double *ox, int desc)
+template <typename V>
+__global__ void bk_rows_sort(int32_t n, const int64_t *rp, const int32_t *tk, const V *tx, int32_t *ok, V *ox,
+                             int desc)
 {
     const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -159,7 +162,7 @@ __global__ void bk_rows_sort(int32_t n, const int64_t *rp, const int32_t *tk, co
         for (int e0 = 0; e0 < len; e0 += 32) {
             const bool mine = e0 + lane < len;
             const int myk = mine ? tk[p0 + e0 + lane] : sentinel;
-            const double myx = mine ? tx[p0 + e0 + lane] : 0.0;
+            const V myx = mine ? tx[p0 + e0 + lane] : V(0);
             int rank = 0;
             for (int f0 = 0; f0 < len; f0 += 32) {
                 const int other = f0 + lane < len ? tk[p0 + f0 + lane] : sentinel;
@@ -179,42 +182,66 @@ __global__ void bk_rows_sort(int32_t n, const int64_t *rp, const int32_t *tk, co
 
 // ---------------------------------------------------------------- the solve
 
-// Lane-parallel bounded wait on flags[j] == epoch for the lanes with want; false
-// if a wait ran out (the timeout status is then set).
+// Bounded wait until flags[j] == epoch for every lane with want.  Each lane
+// checks its flag once; lane 0 alone then polls the flags still unset, in lane
+// order (one poller per warp, and no rereads of the other flags meanwhile), and
+// finally each of those lanes rereads its own flag with an acquiring load, which
+// orders its later reads.  False if a wait ran out (the timeout status is then
+// set).
+__device__ __forceinline__ bool lane0_poll(const bk_dev &d, const int32_t *flag, int epoch, long long budget)
+{
+    const long long t0 = clock64();
+    unsigned ns = 32;
+    while (ld_acquire(flag) != epoch) {
+        if (*reinterpret_cast<const volatile int *>(&d.status->timeout) || clock64() - t0 > budget) {
+            atomicExch(&d.status->timeout, 1);
+            return false;
+        }
+        __nanosleep(ns);
+        ns = min(ns * 2, 256u);
+    }
+    return true;
+}
+
 __device__ __forceinline__ bool wait_flags(const bk_dev &d, const int32_t *flags, int j, bool want, int epoch,
                                            long long budget)
 {
+    const int lane = threadIdx.x & 31;
+    const uint32_t pending = __ballot_sync(BK_FULL, want && ld_acquire(flags + j) != epoch);
+    if (!pending) return true;
     int ok = 1;
-    if (want && ld_acquire(flags + j) != epoch) {
-        const long long t0 = clock64();
-        unsigned ns = 32;
-        while (ld_acquire(flags + j) != epoch) {
-            if (*reinterpret_cast<const volatile int *>(&d.status->timeout) || clock64() - t0 > budget) {
-                atomicExch(&d.status->timeout, 1);
-                ok = 0;
-                break;
-            }
-            __nanosleep(ns);
-            ns = min(ns * 2, 512u);
-        }
+    for (uint32_t p = pending; p; p &= p - 1) {
+        const int jt = __shfl_sync(BK_FULL, j, __ffs(p) - 1);
+        if (lane == 0 && ok) ok = lane0_poll(d, flags + jt, epoch, budget);
     }
-    return !__any_sync(BK_FULL, !ok);
+    if (!__shfl_sync(BK_FULL, ok, 0)) return false;
+    int mine = 1;
+    if ((pending >> lane) & 1u) mine = lane0_poll(d, flags + j, epoch, budget);
+    return __all_sync(BK_FULL, mine);
 }
 
 // z -= sum over up to 32 terms a_t * v_t, in lane order (every lane computes the
 // same chain).
-__device__ __forceinline__ double chain(double z, double a, double v, int cnt)
+template <typename V>
+__device__ __forceinline__ V chain(V z, V a, V v, int cnt)
 {
     for (int t = 0; t < cnt; t++) z = fma(-__shfl_sync(BK_FULL, a, t), __shfl_sync(BK_FULL, v, t), z);
     return z;
 }
 
+template <typename V>
 __global__ void __launch_bounds__(128) bk_solve_kernel(bk_dev d, bk_solve_dev s, int32_t nrhs,
                                                        const double *__restrict__ b, int32_t ldb, double *x,
                                                        int32_t ldx, int32_t epoch, long long budget)
 {
     const int lane = threadIdx.x & 31;
     const int64_t n = d.n;
+    const V *const Bx = vals<V>(d.Bx);
+    const V *const Lrx = vals<V>(s.r.Lrx);
+    const V *const Urx = vals<V>(s.r.Urx);
+    const V *const Ud = vals<V>(s.r.Ud);
+    V *const w = vals<V>(s.w);
+    V *const zz = vals<V>(s.z);
     for (;;) {
         int k = 0;
         if (lane == 0) k = atomicAdd(d.counter + 2, 1);
@@ -228,26 +255,26 @@ __global__ void __launch_bounds__(128) bk_solve_kernel(bk_dev d, bk_solve_dev s,
             const int e0 = s.offp[r], e1 = s.offp[r + 1];
             const int64_t l0 = s.r.Lrp[i], l1 = s.r.Lrp[i + 1];
             for (int q = 0; q < nrhs; q++) {
-                double z = b[(int64_t)q * ldb + d.P[r]];
+                V z = (V)b[(int64_t)q * ldb + d.P[r]];
                 for (int e = e0; e < e1; e += 32) {
                     const int cnt = min(32, e1 - e);
                     const bool have = lane < cnt;
                     const int j = have ? s.offj[e + lane] : 0;
-                    const double a = have ? d.Bx[s.offpos[e + lane]] : 0.0;
+                    const V a = have ? Bx[s.offpos[e + lane]] : V(0);
                     if (!wait_flags(d, s.bdone, j, have, epoch, budget)) return;
-                    const double v = have ? __ldcg(s.z + q * n + j) : 0.0;
+                    const V v = have ? __ldcg(zz + q * n + j) : V(0);
                     z = chain(z, a, v, cnt);
                 }
                 for (int64_t e = l0; e < l1; e += 32) {
                     const int cnt = (int)min((int64_t)32, l1 - e);
                     const bool have = lane < cnt;
                     const int j = have ? s.r.Lrk[e + lane] : 0;
-                    const double a = have ? s.r.Lrx[e + lane] : 0.0;
+                    const V a = have ? Lrx[e + lane] : V(0);
                     if (!wait_flags(d, s.fdone, j, have, epoch, budget)) return;
-                    const double v = have ? __ldcg(s.w + q * n + j) : 0.0;
+                    const V v = have ? __ldcg(w + q * n + j) : V(0);
                     z = chain(z, a, v, cnt);
                 }
-                if (lane == 0) s.w[q * n + i] = z;
+                if (lane == 0) w[q * n + i] = z;
             }
             __threadfence();
             __syncwarp();
@@ -257,22 +284,22 @@ __global__ void __launch_bounds__(128) bk_solve_kernel(bk_dev d, bk_solve_dev s,
             const int i = ~it;
             if (!wait_flags(d, s.fdone, i, lane == 0, epoch, budget)) return;
             const int64_t u0 = s.r.Urp[i], u1 = s.r.Urp[i + 1];
-            const double ud = s.r.Ud[i];
+            const V ud = Ud[i];
             for (int q = 0; q < nrhs; q++) {
-                double z = __shfl_sync(BK_FULL, lane == 0 ? __ldcg(s.w + q * n + i) : 0.0, 0);
+                V z = __shfl_sync(BK_FULL, lane == 0 ? __ldcg(w + q * n + i) : V(0), 0);
                 for (int64_t e = u0; e < u1; e += 32) {
                     const int cnt = (int)min((int64_t)32, u1 - e);
                     const bool have = lane < cnt;
                     const int j = have ? s.r.Urk[e + lane] : 0;
-                    const double a = have ? s.r.Urx[e + lane] : 0.0;
+                    const V a = have ? Urx[e + lane] : V(0);
                     if (!wait_flags(d, s.bdone, j, have, epoch, budget)) return;
-                    const double v = have ? __ldcg(s.z + q * n + j) : 0.0;
+                    const V v = have ? __ldcg(zz + q * n + j) : V(0);
                     z = chain(z, a, v, cnt);
                 }
                 z = z / ud;
                 if (lane == 0) {
-                    s.z[q * n + i] = z;
-                    x[(int64_t)q * ldx + d.Q[i]] = z;
+                    zz[q * n + i] = z;
+                    x[(int64_t)q * ldx + d.Q[i]] = (double)z;
                 }
             }
             __threadfence();
@@ -289,7 +316,7 @@ int solve_blocks()
         int dev = 0, sms = 0, per = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, bk_solve_kernel, 128, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, bk_solve_kernel<double>, 128, 0);
         blocks = std::max(1, sms) * std::max(1, std::min(per, 8));
     }
     return blocks;
@@ -312,14 +339,24 @@ void bk_launch_rows(const bk_dev &d, const bk_rows &r, void *stream)
     const int n = d.n;
     const int blocks = std::max(1, std::min((n + 7) / 8, 152 * 8));
     cudaMemsetAsync(r.cnt, 0, sizeof(int32_t) * 2 * ((size_t)n + 1), st);
-    bk_rows_count<<<blocks, 256, 0, st>>>(d, r);
+    if (d.prec)
+        bk_rows_count<float><<<blocks, 256, 0, st>>>(d, r);
+    else
+        bk_rows_count<double><<<blocks, 256, 0, st>>>(d, r);
     launch_scan(r.cnt, n, r.part, r.Lrp, st);
     launch_scan(r.cnt + n + 1, n, r.part, r.Urp, st);
     cudaMemsetAsync(r.cnt, 0, sizeof(int32_t) * 2 * ((size_t)n + 1), st);
-    bk_rows_scatter<<<blocks, 256, 0, st>>>(d, r, 0);
-    bk_rows_sort<<<blocks, 256, 0, st>>>(n, r.Lrp, r.tk, r.tx, r.Lrk, r.Lrx, 0);
-    bk_rows_scatter<<<blocks, 256, 0, st>>>(d, r, 1);
-    bk_rows_sort<<<blocks, 256, 0, st>>>(n, r.Urp, r.tk, r.tx, r.Urk, r.Urx, 1);
+    if (d.prec) {
+        bk_rows_scatter<float><<<blocks, 256, 0, st>>>(d, r, 0);
+        bk_rows_sort<float><<<blocks, 256, 0, st>>>(n, r.Lrp, r.tk, vals<float>(r.tx), r.Lrk, vals<float>(r.Lrx), 0);
+        bk_rows_scatter<float><<<blocks, 256, 0, st>>>(d, r, 1);
+        bk_rows_sort<float><<<blocks, 256, 0, st>>>(n, r.Urp, r.tk, vals<float>(r.tx), r.Urk, vals<float>(r.Urx), 1);
+    } else {
+        bk_rows_scatter<double><<<blocks, 256, 0, st>>>(d, r, 0);
+        bk_rows_sort<double><<<blocks, 256, 0, st>>>(n, r.Lrp, r.tk, r.tx, r.Lrk, r.Lrx, 0);
+        bk_rows_scatter<double><<<blocks, 256, 0, st>>>(d, r, 1);
+        bk_rows_sort<double><<<blocks, 256, 0, st>>>(n, r.Urp, r.tk, r.tx, r.Urk, r.Urx, 1);
+    }
 }
 
 void bk_launch_solve(const bk_dev &d, const bk_solve_dev &s, int32_t nrhs, const double *b, int32_t ldb,
@@ -327,5 +364,8 @@ void bk_launch_solve(const bk_dev &d, const bk_solve_dev &s, int32_t nrhs, const
 {
     if (s.nitems <= 0) return;
     const int ctas = std::min<int>((s.nitems + 3) / 4, solve_blocks());
-    bk_solve_kernel<<<ctas, 128, 0, (cudaStream_t)stream>>>(d, s, nrhs, b, ldb, x, ldx, epoch, budget);
+    if (d.prec)
+        bk_solve_kernel<float><<<ctas, 128, 0, (cudaStream_t)stream>>>(d, s, nrhs, b, ldb, x, ldx, epoch, budget);
+    else
+        bk_solve_kernel<double><<<ctas, 128, 0, (cudaStream_t)stream>>>(d, s, nrhs, b, ldb, x, ldx, epoch, budget);
 }

@@ -28,6 +28,7 @@ using namespace bk;
 
 namespace {
 
+template <typename V>
 __global__ void __launch_bounds__(128) bk_static_kernel(bk_dev d, int32_t ncols, double tau, int32_t epoch,
                                                         long long budget)
 {
@@ -37,7 +38,7 @@ __global__ void __launch_bounds__(128) bk_static_kernel(bk_dev d, int32_t ncols,
     const int gw = blockIdx.x * 4 + wib;
     if (gw >= d.sx_warps) return;
     bk_task &T = Ts[wib];
-    double *x = d.sx + (int64_t)gw * d.sx_stride;
+    V *x = vals<V>(d.sx) + (int64_t)gw * d.sx_stride;
     int cur = -1;
     for (;;) {
         int k = 0;
@@ -155,7 +156,7 @@ int bk_static_blocks()
         int dev = 0, sms = 0, per = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, bk_static_kernel, 128, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, bk_static_kernel<double>, 128, 0);
         blocks = std::max(1, sms) * std::max(1, std::min(per, 4));
     }
     return blocks;
@@ -165,7 +166,10 @@ void bk_launch_static(const bk_dev &d, int32_t ncols, double tau, int32_t epoch,
                       int blocks, void *stream)
 {
     if (ncols <= 0) return;
-    bk_static_kernel<<<blocks, 128, 0, (cudaStream_t)stream>>>(d, ncols, tau, epoch, budget);
+    if (d.prec)
+        bk_static_kernel<float><<<blocks, 128, 0, (cudaStream_t)stream>>>(d, ncols, tau, epoch, budget);
+    else
+        bk_static_kernel<double><<<blocks, 128, 0, (cudaStream_t)stream>>>(d, ncols, tau, epoch, budget);
 }
 
 // Levels of the current pattern's column DAG and the claim order sorted by level.
