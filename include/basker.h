@@ -59,7 +59,18 @@ typedef struct {
                                      the reach of Algorithm 1 (other values: INVALID_ARG) */
     int timing;                   /* nonzero: record CUDA events around every kernel launch
                                      on the caller's stream; totals in basker_info */
-    int reserved[6];
+    int precision;                /* 0 (default): FP64 factorization and solve.
+                                     1: FP32 factorization and FP32 triangular solves,
+                                     refined in FP64 (residual b - A x, update and backward
+                                     error in FP64) until the backward error reaches ir_tol;
+                                     a factorization whose pivot growth exceeds growth_limit,
+                                     that fails in FP32, or whose refinement stalls is redone
+                                     in FP64 (BASKER_OK; basker_info counts it) */
+    int ir_max_iter;              /* precision 1: refinement steps at most; default 10 */
+    double ir_tol;                /* precision 1: backward error to reach; default 1e-13 */
+    double growth_limit;          /* precision 1: max over BTF blocks of max|U_d| / max|B_d|
+                                     above which the FP32 factors are not used; default 1e4 */
+    int reserved[4];
 } basker_options;
 
 typedef struct {
@@ -87,12 +98,17 @@ typedef struct {
                                      phase, [5] solve, [6] pivot reset,
                                      [7] refactorization rounds after the stored-pattern
                                      pass, [8] factors transposed into rows for the
-                                     solve, [9] reserved */
+                                     solve, [9] FP64 refinement (precision 1) */
     int32_t internal_site;        /* nonzero: code of the internal consistency check that
                                      failed (reported as INVALID_ARG), for diagnosis */
     int32_t internal_col;         /* column of that check */
     int32_t last_rounds;          /* redo rounds of the last refactor (0: no pivot rejected) */
-    int32_t reserved[5];
+    int32_t ir_iterations;        /* precision 1: refinement steps of the last solve */
+    int32_t ir_fallbacks;         /* precision 1: factorizations redone in FP64 so far */
+    int32_t precision_used;       /* arithmetic of the factors the last solve used: 0 FP64, 1 FP32 */
+    int32_t reserved[2];
+    double ir_eta;                /* precision 1: backward error after the last solve's refinement */
+    double growth;                /* precision 1: pivot growth of the last FP32 factorization */
 } basker_info_t;
 
 /* Defaults listed in basker_options. */
@@ -136,8 +152,11 @@ int basker_refactor(basker_t h, const double *values_dev, void *stream);
 /* Solve A X = B for nrhs right-hand sides (column-major, leading dimensions ldb,
  * ldx >= n, device pointers; b_dev and x_dev may not overlap).  BTF blocks from
  * last to first: subtract the off-diagonal blocks' products, then the L and U
- * solves of the block.  Asynchronous on the stream.  Errors: INVALID_ARG,
- * NOT_FACTORED, CUDA, OOM. */
+ * solves of the block.  Asynchronous on the stream.  With options.precision 1
+ * the solves run on the FP32 factors and are refined in FP64 (each step
+ * synchronises the stream once to test the backward error); a stalled
+ * refinement refactors in FP64 and solves with those factors.  Errors:
+ * INVALID_ARG, NOT_FACTORED, CUDA, OOM. */
 int basker_solve(basker_t h, int32_t nrhs, const double *b_dev, int32_t ldb,
                  double *x_dev, int32_t ldx, void *stream);
 
@@ -162,8 +181,9 @@ int basker_refactor_solve_host(basker_t h, const double *values_host, int32_t nr
  *   The work vectors and ND buffers of the solve live in one array of
  *   BASKER_NOALLOC_SCRATCH_DOUBLES doubles compiled into the library, so the call
  *   performs no cudaMalloc, cudaFree or other allocation.  It needs
- *   nrhs * (n + the ND buffer length) doubles; larger requests return
- *   BASKER_ERR_INVALID_ARG without launching anything.
+ *   2 * nrhs * n doubles; larger requests return BASKER_ERR_INVALID_ARG without
+ *   launching anything, and so does a handle with options.precision 1 (its
+ *   refinement needs buffers of its own).
  *   The first call on a device looks up the array's device address (with that
  *   device current) and caches it; make that first call before any stream
  *   capture begins.

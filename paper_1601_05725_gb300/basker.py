@@ -37,7 +37,8 @@ class BaskerError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_double), ("slack", ctypes.c_double),
                 ("wait_budget_cycles", ctypes.c_longlong), ("factor_mode", ctypes.c_int),
-                ("timing", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
+                ("timing", ctypes.c_int), ("precision", ctypes.c_int), ("ir_max_iter", ctypes.c_int),
+                ("ir_tol", ctypes.c_double), ("growth_limit", ctypes.c_double), ("reserved", ctypes.c_int * 4)]
 
 
 class Info(ctypes.Structure):
@@ -50,10 +51,12 @@ class Info(ctypes.Structure):
                 ("gp_launches", ctypes.c_int32), ("static_launches", ctypes.c_int32),
                 ("kernel_launches", ctypes.c_int64), ("kernel_ms", ctypes.c_double * 10),
                 ("internal_site", ctypes.c_int32), ("internal_col", ctypes.c_int32),
-                ("last_rounds", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("last_rounds", ctypes.c_int32), ("ir_iterations", ctypes.c_int32),
+                ("ir_fallbacks", ctypes.c_int32), ("precision_used", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2), ("ir_eta", ctypes.c_double), ("growth", ctypes.c_double)]
 
 KERNEL_KINDS = ["gather", "static_refactor", "dag_levels", "gp_in_node", "gp_descendant", "solve",
-                "pivot_reset", "refactor_rounds", "rows_transpose", "reserved"]
+                "pivot_reset", "refactor_rounds", "rows_transpose", "refine"]
 
 
 EXPORTED = ["basker_default_options", "basker_symbolic", "basker_factor", "basker_refactor",
@@ -132,10 +135,19 @@ class Handle:
 
     def __init__(self, n, colptr, rowind, P, Q, block_ptr, nd_block=-1, nd_leaves=0, nd_node_ptr=None,
                  tau: float = 1e-3, slack: Optional[float] = None, wait_budget_cycles: Optional[int] = None,
-                 factor_mode: int = 0, timing: bool = False):
+                 factor_mode: int = 0, timing: bool = False, precision: int = 0,
+                 ir_max_iter: Optional[int] = None, ir_tol: Optional[float] = None,
+                 growth_limit: Optional[float] = None):
         self.lib = load()
         opt = default_options()
         opt.tau = float(tau)
+        opt.precision = int(precision)
+        if ir_max_iter is not None:
+            opt.ir_max_iter = int(ir_max_iter)
+        if ir_tol is not None:
+            opt.ir_tol = float(ir_tol)
+        if growth_limit is not None:
+            opt.growth_limit = float(growth_limit)
         if slack is not None:
             opt.slack = float(slack)
         if wait_budget_cycles is not None:

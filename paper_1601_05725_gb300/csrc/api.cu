@@ -4,11 +4,14 @@
 
 #include <algorithm>
 #include <climits>
+#include <cmath>
+#include <cstdint>
 #include <cstdlib>
 #include <cstring>
 #include <new>
 
 #include "basker_internal.h"
+#include "refine_internal.h"
 #include "solve_internal.h"
 
 struct basker_s {
@@ -44,12 +47,26 @@ struct basker_s {
     std::vector<cudaEvent_t> pool;
     cudaEvent_t open_ev = nullptr;
     int open_kind = 0;
+    // precision 1: FP64 refinement state, and an FP64 twin handle for the
+    // factorizations the FP32 factors cannot serve (built on first need)
+    bk_refine_dev rf{};
+    double *d_norms = nullptr;       // [0] ||B||_inf, [1] pivot growth
+    double *h_norms = nullptr;       // pinned: 2 + 3 * ir_cap
+    double *d_vals64 = nullptr;      // the values of the last factorization (A's order)
+    double *ir_c = nullptr, *ir_r = nullptr, *ir_z = nullptr, *ir_dz = nullptr, *d_irn = nullptr;
+    int32_t ir_cap = 0;
+    double bnorm = 0.0;
+    bool use64 = false, fp32_valid = false;
+    basker_t twin = nullptr;
+    // the symbolic inputs, kept to build the twin
+    std::vector<int32_t> in_colptr, in_rowind, in_P, in_Q, in_bptr, in_ndptr;
+    int32_t in_nblocks = 0, in_ndblock = -1, in_ndleaves = 0;
 };
 
 namespace {
 
 enum { KT_GATHER = 0, KT_STATIC = 1, KT_LEVELS = 2, KT_GP = 3, KT_DESC = 4, KT_SOLVE = 5, KT_RESET = 6, KT_SPEC = 7,
-       KT_ROWS = 8 };
+       KT_ROWS = 8, KT_REFINE = 9 };
 
 cudaEvent_t take_event(basker_t h)
 {
@@ -205,6 +222,34 @@ int setup_device(basker_t h)
     const int32_t n = pl.n;
     d.n = n;
     d.ntasks = (int32_t)pl.tasks.size();
+    d.prec = h->opt.precision;
+    if (d.prec) {
+        // B by rows (entries in ascending column order) for the FP64 residual
+        std::vector<int64_t> brp((size_t)n + 1, 0);
+        for (int32_t j = 0; j < n; j++)
+            for (int32_t e = pl.Bp[(size_t)j]; e < pl.Bp[(size_t)j + 1]; e++) brp[(size_t)pl.Bi[(size_t)e] + 1]++;
+        for (int32_t i = 0; i < n; i++) brp[(size_t)i + 1] += brp[(size_t)i];
+        std::vector<int32_t> brj((size_t)pl.nnz), brpos((size_t)pl.nnz), blk((size_t)n, 0);
+        std::vector<int64_t> cur(brp.begin(), brp.end() - 1);
+        for (int32_t j = 0; j < n; j++)
+            for (int32_t e = pl.Bp[(size_t)j]; e < pl.Bp[(size_t)j + 1]; e++) {
+                const int64_t q = cur[(size_t)pl.Bi[(size_t)e]]++;
+                brj[(size_t)q] = j;
+                brpos[(size_t)q] = e;
+            }
+        for (int32_t b = 0; b < pl.nblocks; b++)
+            for (int32_t i = pl.block_ptr[(size_t)b]; i < pl.block_ptr[(size_t)b + 1]; i++) blk[(size_t)i] = b;
+        TRY(upload(h, (int64_t **)&h->rf.Brp, brp));
+        TRY(upload(h, (int32_t **)&h->rf.Brj, brj));
+        TRY(upload(h, (int32_t **)&h->rf.Brpos, brpos));
+        TRY(upload(h, (int32_t **)&h->rf.blk, blk));
+        TRY(dalloc(h, &h->rf.Bx64, (size_t)pl.nnz));
+        TRY(dalloc(h, &h->rf.bmax, (size_t)std::max(pl.nblocks, 1)));
+        TRY(dalloc(h, &h->rf.umax, (size_t)std::max(pl.nblocks, 1)));
+        TRY(dalloc(h, &h->d_norms, 2));
+        TRY(dalloc(h, &h->d_vals64, (size_t)pl.nnz));
+        CU(cudaMallocHost((void **)&h->h_norms, sizeof(double) * 2));
+    }
     TRY(upload(h, (int32_t **)&d.Bp, pl.Bp));
     TRY(upload(h, (int32_t **)&d.Bi, pl.Bi));
     TRY(upload(h, (int32_t **)&d.dstart, pl.dstart));
@@ -569,6 +614,130 @@ int ensure_solve_buffers(basker_t h, int32_t nrhs)
     return BASKER_OK;
 }
 
+// ---- precision 1: FP32 factorization, FP64 refinement
+
+int ensure_twin(basker_t h)
+{
+    if (h->twin) return BASKER_OK;
+    basker_options o = h->opt;
+    o.precision = 0;
+    return basker_symbolic(h->pl.n, h->in_colptr.data(), h->in_rowind.data(), h->in_P.data(), h->in_Q.data(),
+                           h->in_nblocks, h->in_bptr.data(), h->in_ndblock, h->in_ndleaves,
+                           h->in_ndptr.empty() ? nullptr : h->in_ndptr.data(), &o, &h->twin);
+}
+
+// FP64 factorization, by the twin, of the values of the last factorization call.
+int factor_twin(basker_t h, cudaStream_t s)
+{
+    TRY(ensure_twin(h));
+    const int st = h->twin->factored ? basker_refactor(h->twin, h->d_vals64, s)
+                                     : basker_factor(h->twin, h->d_vals64, s);
+    h->use64 = true;
+    h->info.ir_fallbacks++;
+    if (st != BASKER_OK) h->info.failed_column = h->twin->info.failed_column;
+    return st;
+}
+
+// After the FP32 kernels: B in FP64 for the residual, ||B||_inf and the pivot
+// growth; the FP64 twin takes over when the growth is too large or FP32 failed.
+int finish_fp32(basker_t h, const double *values, cudaStream_t s, int st)
+{
+    h->use64 = false;
+    h->fp32_valid = (st == BASKER_OK);
+    if (st == BASKER_OK) {
+        bk_launch_gather64(h->d, h->rf, values, h->pl.nnz, s);
+        bk_launch_norms(h->d, h->rf, h->d_norms, s);
+        CU(cudaMemcpyAsync(h->h_norms, h->d_norms, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        h->bnorm = h->h_norms[0];
+        h->info.growth = h->h_norms[1];
+        if (h->h_norms[1] <= h->opt.growth_limit) return BASKER_OK;   // false for NaN
+    } else if (st != BASKER_ERR_SINGULAR && st != BASKER_ERR_NAN) {
+        return st;
+    }
+    const int s64 = factor_twin(h, s);
+    h->factored = (s64 == BASKER_OK);
+    return s64;
+}
+
+int ensure_ir_buffers(basker_t h, int32_t nrhs)
+{
+    if (nrhs <= h->ir_cap) return BASKER_OK;
+    for (double **p : {&h->ir_c, &h->ir_r, &h->ir_z, &h->ir_dz, &h->d_irn}) {
+        dfree(h, *p);
+        *p = nullptr;
+    }
+    const size_t m = (size_t)h->pl.n * (size_t)nrhs;
+    TRY(dalloc(h, &h->ir_c, m));
+    TRY(dalloc(h, &h->ir_r, m));
+    TRY(dalloc(h, &h->ir_z, m));
+    TRY(dalloc(h, &h->ir_dz, m));
+    TRY(dalloc(h, &h->d_irn, (size_t)3 * (size_t)nrhs));
+    if (h->h_norms) cudaFreeHost(h->h_norms);
+    h->h_norms = nullptr;
+    CU(cudaMallocHost((void **)&h->h_norms, sizeof(double) * (2 + 3 * (size_t)nrhs)));
+    h->ir_cap = nrhs;
+    return BASKER_OK;
+}
+
+// x = A^{-1} b from the FP32 factors, refined in FP64 in B's space: z = 0,
+// r = c = b(P); repeat dz = solve(r), z += dz, r = c - B z until the backward
+// error reaches ir_tol.  A step that fails to halve it, or the last allowed
+// step, hands the system to the FP64 twin.
+int solve_refined(basker_t h, int32_t nrhs, const double *b, int32_t ldb, double *x, int32_t ldx, cudaStream_t s)
+{
+    if (h->use64) {
+        h->info.precision_used = 0;
+        h->info.ir_iterations = 0;
+        return basker_solve(h->twin, nrhs, b, ldb, x, ldx, s);
+    }
+    TRY(ensure_ir_buffers(h, nrhs));
+    TRY(ensure_solve_buffers(h, nrhs));
+    const int32_t n = h->pl.n;
+    double *cmax = h->d_irn, *zmax = cmax + nrhs, *rmax = zmax + nrhs;
+    CU(cudaMemsetAsync(cmax, 0, sizeof(double) * (size_t)nrhs, s));
+    tbeg(h, KT_REFINE, s, 1);
+    bk_launch_ir_start(h->d, nrhs, b, ldb, h->ir_c, h->ir_r, h->ir_z, cmax, s);
+    tend(h, s);
+    double prev = INFINITY;
+    for (int it = 1;; it++) {
+        CU(cudaMemsetAsync(zmax, 0, sizeof(double) * 2 * (size_t)nrhs, s));
+        CU(cudaMemsetAsync(h->d.counter + 2, 0, sizeof(int32_t), s));
+        h->solve_epoch++;
+        tbeg(h, KT_SOLVE, s, 1);
+        bk_launch_solve(h->d, h->sd, nrhs, h->ir_r, n, h->ir_dz, n, h->solve_epoch, h->opt.wait_budget_cycles, s,
+                        false);
+        tend(h, s);
+        tbeg(h, KT_REFINE, s, 2);
+        bk_launch_ir_step(h->d, h->rf, nrhs, h->ir_c, h->ir_z, h->ir_dz, h->ir_r, zmax, rmax, s);
+        tend(h, s);
+        h->info.kernel_launches += 3;
+        CU(cudaGetLastError());
+        CU(cudaMemcpyAsync(h->h_norms + 2, cmax, sizeof(double) * 3 * (size_t)nrhs, cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        double eta = 0.0;
+        for (int32_t q = 0; q < nrhs; q++) {
+            const double c = h->h_norms[2 + q], z = h->h_norms[2 + nrhs + q], r = h->h_norms[2 + 2 * nrhs + q];
+            const double den = h->bnorm * z + c;
+            const double e = den > 0.0 ? r / den : (r > 0.0 ? INFINITY : 0.0);
+            eta = (e > eta || e != e) ? e : eta;
+        }
+        h->info.ir_iterations = it;
+        h->info.ir_eta = eta;
+        if (eta <= h->opt.ir_tol) break;
+        if (it >= h->opt.ir_max_iter || !(eta <= 0.5 * prev)) {
+            TRY(factor_twin(h, s));
+            h->info.precision_used = 0;
+            return basker_solve(h->twin, nrhs, b, ldb, x, ldx, s);
+        }
+        prev = eta;
+    }
+    bk_launch_ir_finish(h->d, nrhs, h->ir_z, x, ldx, s);
+    h->info.precision_used = 1;
+    CU(cudaGetLastError());
+    return BASKER_OK;
+}
+
 }  // namespace
 
 // Helpers of the allocation-free solve (noalloc.cu).  They launch the same solve
@@ -580,6 +749,7 @@ int32_t bk_handle_n(basker_t h) { return h->pl.n; }
 
 int64_t bk_solve_scratch_doubles(basker_t h, int32_t nrhs)
 {
+    if (h->opt.precision) return INT64_MAX;    // the refinement needs buffers of its own
     return (int64_t)nrhs * 2 * (int64_t)h->pl.n;
 }
 
@@ -610,6 +780,10 @@ void basker_default_options(basker_options *opt)
     opt->slack = 1.0;
     opt->wait_budget_cycles = 20000000000LL;
     opt->factor_mode = 0;
+    opt->precision = 0;
+    opt->ir_max_iter = 10;
+    opt->ir_tol = 1e-13;
+    opt->growth_limit = 1e4;
 }
 
 const char *basker_strerror(int status)
@@ -641,11 +815,24 @@ int basker_symbolic(int32_t n, const int32_t *colptr, const int32_t *rowind, con
     basker_default_options(&h->opt);
     if (opt) h->opt = *opt;
     if (!(h->opt.tau > 0.0 && h->opt.tau <= 1.0) || h->opt.slack < 0.0 || h->opt.wait_budget_cycles <= 0 ||
-        h->opt.factor_mode != 0) {
+        h->opt.factor_mode != 0 || (h->opt.precision != 0 && h->opt.precision != 1) ||
+        (h->opt.precision == 1 && (h->opt.ir_max_iter < 1 || !(h->opt.ir_tol > 0.0) || !(h->opt.growth_limit > 0.0)))) {
         delete h;
         return BASKER_ERR_INVALID_ARG;
     }
     cudaGetDevice(&h->device);
+    if (h->opt.precision == 1 && n > 0 && colptr && rowind && P && Q && block_ptr && nblocks >= 0) {
+        // kept to build the FP64 twin on first need
+        h->in_colptr.assign(colptr, colptr + n + 1);
+        h->in_rowind.assign(rowind, rowind + colptr[n]);
+        h->in_P.assign(P, P + n);
+        h->in_Q.assign(Q, Q + n);
+        h->in_bptr.assign(block_ptr, block_ptr + nblocks + 1);
+        if (nd_block >= 0 && nd_node_ptr) h->in_ndptr.assign(nd_node_ptr, nd_node_ptr + 2 * nd_leaves);
+        h->in_nblocks = nblocks;
+        h->in_ndblock = nd_block;
+        h->in_ndleaves = nd_leaves;
+    }
     int32_t bad = -1;
     int st = bk_plan_build(n, colptr, rowind, P, Q, nblocks, block_ptr, nd_block, nd_leaves, nd_node_ptr,
                            h->opt.slack, h->pl, &bad);
@@ -672,8 +859,12 @@ int basker_factor(basker_t h, const double *values_dev, void *stream)
     if (!h || (!values_dev && h->pl.nnz > 0)) return BASKER_ERR_INVALID_ARG;
     cudaSetDevice(h->device);
     h->factored = false;
-    int st = factor_impl(h, values_dev, (cudaStream_t)stream, false);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (h->opt.precision && h->pl.nnz > 0)
+        CU(cudaMemcpyAsync(h->d_vals64, values_dev, sizeof(double) * (size_t)h->pl.nnz, cudaMemcpyDeviceToDevice, s));
+    int st = factor_impl(h, values_dev, s, false);
     h->info.gp_launches = h->launches;
+    if (h->opt.precision) st = finish_fp32(h, values_dev, s, st);
     return st;
 }
 
@@ -682,8 +873,15 @@ int basker_refactor(basker_t h, const double *values_dev, void *stream)
     if (!h || (!values_dev && h->pl.nnz > 0)) return BASKER_ERR_INVALID_ARG;
     if (!h->factored) return BASKER_ERR_NOT_FACTORED;
     cudaSetDevice(h->device);
-    int st = factor_impl(h, values_dev, (cudaStream_t)stream, true);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (h->opt.precision && h->pl.nnz > 0)
+        CU(cudaMemcpyAsync(h->d_vals64, values_dev, sizeof(double) * (size_t)h->pl.nnz, cudaMemcpyDeviceToDevice, s));
+    // FP32 factors that failed last time are not a base to refactor from
+    const bool re = !h->opt.precision || h->fp32_valid;
+    if (!re) h->factored = false;
+    int st = factor_impl(h, values_dev, s, re);
     h->info.static_launches = h->launches;
+    if (h->opt.precision) st = finish_fp32(h, values_dev, s, st);
     return st;
 }
 
@@ -695,10 +893,12 @@ int basker_solve(basker_t h, int32_t nrhs, const double *b_dev, int32_t ldb, dou
     if (!h->factored) return BASKER_ERR_NOT_FACTORED;
     if (nrhs == 0 || h->pl.n == 0) return BASKER_OK;
     cudaSetDevice(h->device);
+    if (h->opt.precision) return solve_refined(h, nrhs, b_dev, ldb, x_dev, ldx, (cudaStream_t)stream);
     TRY(ensure_solve_buffers(h, nrhs));
     cudaStream_t s = (cudaStream_t)stream;
     CU(cudaMemsetAsync(h->d.counter + 2, 0, sizeof(int32_t), s));
     h->solve_epoch++;
+    h->info.precision_used = 0;
     tbeg(h, KT_SOLVE, s, 1);
     bk_launch_solve(h->d, h->sd, nrhs, b_dev, ldb, x_dev, ldx, h->solve_epoch, h->opt.wait_budget_cycles, s);
     tend(h, s);
@@ -796,9 +996,18 @@ int basker_export(basker_t h, int32_t *prow, int64_t *Lp, int32_t *Li, double *L
     std::vector<int32_t> li((size_t)h->d.lpool_end), ui((size_t)h->d.upool_end);
     std::vector<double> lx((size_t)h->d.lpool_end), ux((size_t)h->d.upool_end);
     CU(cudaMemcpy(li.data(), h->d.Li, li.size() * 4, cudaMemcpyDeviceToHost));
-    CU(cudaMemcpy(lx.data(), h->d.Lx, lx.size() * 8, cudaMemcpyDeviceToHost));
     CU(cudaMemcpy(ui.data(), h->d.Ui, ui.size() * 4, cudaMemcpyDeviceToHost));
-    CU(cudaMemcpy(ux.data(), h->d.Ux, ux.size() * 8, cudaMemcpyDeviceToHost));
+    if (h->d.prec) {
+        // FP32 factors, widened
+        std::vector<float> f(std::max(lx.size(), ux.size()));
+        CU(cudaMemcpy(f.data(), h->d.Lx, lx.size() * 4, cudaMemcpyDeviceToHost));
+        for (size_t i = 0; i < lx.size(); i++) lx[i] = f[i];
+        CU(cudaMemcpy(f.data(), h->d.Ux, ux.size() * 4, cudaMemcpyDeviceToHost));
+        for (size_t i = 0; i < ux.size(); i++) ux[i] = f[i];
+    } else {
+        CU(cudaMemcpy(lx.data(), h->d.Lx, lx.size() * 8, cudaMemcpyDeviceToHost));
+        CU(cudaMemcpy(ux.data(), h->d.Ux, ux.size() * 8, cudaMemcpyDeviceToHost));
+    }
     std::memcpy(prow, pr.data(), n * 4);
     Lp[0] = Up[0] = 0;
     std::vector<std::pair<int32_t, double>> col;
@@ -837,6 +1046,8 @@ void basker_free(basker_t h)
     for (auto &t : h->pending) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
     for (auto e : h->pool) cudaEventDestroy(e);
     if (h->open_ev) cudaEventDestroy(h->open_ev);
+    if (h->h_norms) cudaFreeHost(h->h_norms);
+    if (h->twin) basker_free(h->twin);
     delete h;
 }
 

@@ -232,7 +232,9 @@ __device__ __forceinline__ V chain(V z, V a, V v, int cnt)
 template <typename V>
 __global__ void __launch_bounds__(128) bk_solve_kernel(bk_dev d, bk_solve_dev s, int32_t nrhs,
                                                        const double *__restrict__ b, int32_t ldb, double *x,
-                                                       int32_t ldx, int32_t epoch, long long budget)
+                                                       int32_t ldx, int32_t epoch, long long budget,
+                                                       const int32_t *__restrict__ Pin,
+                                                       const int32_t *__restrict__ Qout)
 {
     const int lane = threadIdx.x & 31;
     const int64_t n = d.n;
@@ -255,7 +257,7 @@ __global__ void __launch_bounds__(128) bk_solve_kernel(bk_dev d, bk_solve_dev s,
             const int e0 = s.offp[r], e1 = s.offp[r + 1];
             const int64_t l0 = s.r.Lrp[i], l1 = s.r.Lrp[i + 1];
             for (int q = 0; q < nrhs; q++) {
-                V z = (V)b[(int64_t)q * ldb + d.P[r]];
+                V z = (V)b[(int64_t)q * ldb + (Pin ? Pin[r] : r)];
                 for (int e = e0; e < e1; e += 32) {
                     const int cnt = min(32, e1 - e);
                     const bool have = lane < cnt;
@@ -299,7 +301,7 @@ __global__ void __launch_bounds__(128) bk_solve_kernel(bk_dev d, bk_solve_dev s,
                 z = z / ud;
                 if (lane == 0) {
                     zz[q * n + i] = z;
-                    x[(int64_t)q * ldx + d.Q[i]] = (double)z;
+                    x[(int64_t)q * ldx + (Qout ? Qout[i] : i)] = (double)z;
                 }
             }
             __threadfence();
@@ -360,12 +362,15 @@ void bk_launch_rows(const bk_dev &d, const bk_rows &r, void *stream)
 }
 
 void bk_launch_solve(const bk_dev &d, const bk_solve_dev &s, int32_t nrhs, const double *b, int32_t ldb,
-                     double *x, int32_t ldx, int32_t epoch, long long budget, void *stream)
+                     double *x, int32_t ldx, int32_t epoch, long long budget, void *stream, bool permute)
 {
+    const int32_t *Pin = permute ? d.P : nullptr, *Qout = permute ? d.Q : nullptr;
     if (s.nitems <= 0) return;
     const int ctas = std::min<int>((s.nitems + 3) / 4, solve_blocks());
     if (d.prec)
-        bk_solve_kernel<float><<<ctas, 128, 0, (cudaStream_t)stream>>>(d, s, nrhs, b, ldb, x, ldx, epoch, budget);
+        bk_solve_kernel<float><<<ctas, 128, 0, (cudaStream_t)stream>>>(d, s, nrhs, b, ldb, x, ldx, epoch, budget, Pin,
+                                                                        Qout);
     else
-        bk_solve_kernel<double><<<ctas, 128, 0, (cudaStream_t)stream>>>(d, s, nrhs, b, ldb, x, ldx, epoch, budget);
+        bk_solve_kernel<double><<<ctas, 128, 0, (cudaStream_t)stream>>>(d, s, nrhs, b, ldb, x, ldx, epoch, budget, Pin,
+                                                                         Qout);
 }

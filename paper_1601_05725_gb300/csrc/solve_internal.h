@@ -38,5 +38,7 @@ struct bk_solve_plan {
 
 void bk_solve_plan_build(const bk_plan &pl, bk_solve_plan &sp);
 void bk_launch_rows(const bk_dev &d, const bk_rows &r, void *stream);
+// permute: b is indexed by A's rows and x by A's columns (b(P), x(Q)); otherwise
+// both are in B's row / column space (the refinement's corrections).
 void bk_launch_solve(const bk_dev &d, const bk_solve_dev &s, int32_t nrhs, const double *b, int32_t ldb,
-                     double *x, int32_t ldx, int32_t epoch, long long budget, void *stream);
+                     double *x, int32_t ldx, int32_t epoch, long long budget, void *stream, bool permute = true);
