@@ -172,13 +172,15 @@ int alloc_factors(basker_t h)
     // the factors by rows (for the solve) have the same capacities
     bk_rows &r = h->sd.r;
     dfree(h, r.Lrk); dfree(h, r.Lrx); dfree(h, r.Urk); dfree(h, r.Urx); dfree(h, r.tk); dfree(h, r.tx);
-    r.Lrk = r.Urk = r.tk = nullptr;
+    dfree(h, r.Ls);
+    r.Lrk = r.Urk = r.tk = r.Ls = nullptr;
     r.Lrx = r.Urx = r.tx = nullptr;
     TRY(dalloc(h, &r.Lrk, (size_t)h->d.lpool_end));
     TRY(dalloc(h, &r.Lrx, (size_t)h->d.lpool_end));
     TRY(dalloc(h, &r.Urk, (size_t)h->d.upool_end));
     TRY(dalloc(h, &r.Urx, (size_t)h->d.upool_end));
     TRY(dalloc(h, &r.tk, (size_t)std::max(h->d.lpool_end, h->d.upool_end)));
+    TRY(dalloc(h, &r.Ls, (size_t)h->d.lpool_end));
     TRY(dalloc(h, &r.tx, (size_t)std::max(h->d.lpool_end, h->d.upool_end)));
     TRY(dalloc(h, &h->d.Lx, (size_t)h->d.lpool_end));
     TRY(dalloc(h, &h->d.Ui, (size_t)h->d.upool_end));
@@ -212,6 +214,7 @@ int upload_symbolic_pattern(basker_t h)
     CU(cudaMemcpy(h->d.prow, prow.data(), (size_t)pl.n * 4, cudaMemcpyHostToDevice));
     CU(cudaMemcpy(h->d.pinv, pinv.data(), (size_t)pl.n * 4, cudaMemcpyHostToDevice));
     CU(cudaMemcpy(h->d.order, pl.sorder.data(), (size_t)pl.n * 4, cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(h->d.level, pl.slevel.data(), (size_t)pl.n * 4, cudaMemcpyHostToDevice));
     return BASKER_OK;
 }
 
@@ -329,10 +332,20 @@ int setup_device(basker_t h)
     bk_solve_plan_build(pl, h->sp);
     bk_solve_dev &s = h->sd;
     s.nitems = (int32_t)h->sp.items.size();
-    TRY(upload(h, (int32_t **)&s.items, h->sp.items));
+    TRY(upload(h, &s.items, h->sp.items));
     TRY(upload(h, (int32_t **)&s.offp, h->sp.offp));
     TRY(upload(h, (int32_t **)&s.offj, h->sp.offj));
     TRY(upload(h, (int32_t **)&s.offpos, h->sp.offpos));
+    TRY(upload(h, (int32_t **)&s.cutlo, h->sp.cutlo));
+    TRY(upload(h, (int32_t **)&s.cuthi, h->sp.cuthi));
+    s.nleaves = (int32_t)h->sp.leaf_tasks.size();
+    s.leaf_rows = h->sp.leaf_rows;
+    s.leaf_f0 = h->sp.leaf_f0;
+    s.leaf_b0 = h->sp.leaf_b0;
+    s.leaf_maxrows = h->sp.leaf_maxrows;
+    TRY(upload(h, (int32_t **)&s.leaf_tasks, h->sp.leaf_tasks));
+    TRY(dalloc(h, &s.leaf_bad, std::max<size_t>(h->sp.leaf_tasks.size(), 1)));
+    TRY(dalloc(h, &s.lcnt, (size_t)2 * ((size_t)h->sp.leaf_maxrows + 1)));
     TRY(dalloc(h, &s.fdone, (size_t)n, true));
     TRY(dalloc(h, &s.bdone, (size_t)n, true));
     TRY(dalloc(h, &s.r.Lrp, (size_t)n + 1));
@@ -536,6 +549,20 @@ int static_pass(basker_t h, cudaStream_t s)
     return BASKER_OK;
 }
 
+// After a factorization: the column levels of the new pattern (the next
+// refactorization's claim order, and the backward order of the ND leaves in the
+// solve), the factors by rows, and the solve's order of the leaf rows.
+int finish_factorization(basker_t h, cudaStream_t s)
+{
+    if (!h->schedule_valid) TRY(compute_schedule(h, s));
+    tbeg(h, KT_ROWS, s, 14);
+    bk_launch_rows(h->d, h->sd.r, s);
+    bk_launch_leaf_order(h->d, h->sd, s);
+    tend(h, s);
+    CU(cudaGetLastError());
+    return BASKER_OK;
+}
+
 int factor_impl(basker_t h, const double *values, cudaStream_t s, bool refactor)
 {
     h->launches = 0;
@@ -571,9 +598,7 @@ int factor_impl(basker_t h, const double *values, cudaStream_t s, bool refactor)
             }
         }
         if (st != BASKER_OK) { h->factored = false; return st == -1 ? BASKER_ERR_OOM : st; }
-        tbeg(h, KT_ROWS, s, 11);
-        bk_launch_rows(h->d, h->sd.r, s);
-        tend(h, s);
+        TRY(finish_factorization(h, s));
         h->factored = true;
         return BASKER_OK;
     }
@@ -591,13 +616,11 @@ int factor_impl(basker_t h, const double *values, cudaStream_t s, bool refactor)
         if (st != -1) break;
     }
     if (st != BASKER_OK) { h->factored = false; return st == -1 ? BASKER_ERR_OOM : st; }
-    tbeg(h, KT_ROWS, s, 11);
-    bk_launch_rows(h->d, h->sd.r, s);
-    tend(h, s);
     h->info.off_diagonal_pivots = h->h_status->offdiag;
     // with the natural pivots everywhere the pattern is the symbolic one, whose
     // static schedule is already on the device
     h->schedule_valid = (h->h_status->offdiag == 0 && h->order_is_symbolic);
+    TRY(finish_factorization(h, s));
     h->factored = true;
     return BASKER_OK;
 }

@@ -40,7 +40,11 @@ __global__ void bk_rows_count(bk_dev d, bk_rows r)
     for (int c = warp; c < d.n; c += nwarps) {
         const int64_t lb = d.Lbeg[c];
         const int ln = d.Lcnt[c];
-        for (int t = lane; t < ln; t += 32) atomicAdd(lc + d.pinv[d.Li[lb + t]], 1);
+        for (int t = lane; t < ln; t += 32) {
+            const int i = d.pinv[d.Li[lb + t]];
+            r.Ls[lb + t] = i;
+            atomicAdd(lc + i, 1);
+        }
         const int64_t ub = d.Ubeg[c];
         const int un = d.Ucnt[c];
         for (int t = lane; t < un - 1; t += 32) atomicAdd(uc + d.Ui[ub + t], 1);
@@ -180,6 +184,84 @@ __global__ void bk_rows_sort(int32_t n, const int64_t *rp, const int32_t *tk, co
     }
 }
 
+// ---------------------------------------------------------------- leaf order
+
+// Orders of an ND leaf's rows.  Backward: U(i,k) != 0 makes column k depend on
+// step i in the factorization, so the factorization's column levels (d.level,
+// longest chain from a source, counting only the leaf's steps for a leaf
+// column) taken in decreasing order are a valid order, and one with the most
+// rows at each level.  Forward: the same levels in increasing order are valid
+// when every L(i,k) != 0 of the leaf has level(k) < level(i) (true for
+// symmetric patterns); a leaf where that fails keeps its step order.  One
+// block a leaf checks it.
+__global__ void bk_leaf_check(bk_dev d, bk_solve_dev s)
+{
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const bk_task &T = d.tasks[s.leaf_tasks[blockIdx.x]];
+    int bad = 0;
+    for (int i = T.lo + wid; i < T.hi; i += nw) {
+        const int li = d.level[i];
+        for (int64_t e = s.r.Lrp[i] + lane; e < s.r.Lrp[i + 1]; e += 32)
+            if (d.level[s.r.Lrk[e]] >= li) bad = 1;
+    }
+    if (__any_sync(BK_FULL, bad) && lane == 0) s.leaf_bad[blockIdx.x] = 1;
+}
+
+// Sort key of leaf row i (both below the leaf's size).
+__device__ __forceinline__ int leaf_key(const bk_dev &d, const bk_solve_dev &s, int leaf, int lo, int hi, int i,
+                                        int dir)
+{
+    if (dir == 0) return s.leaf_bad[leaf] ? i - lo : d.level[i];
+    return s.leaf_maxrows - d.level[i];
+}
+
+// Counting sort of all leaf rows by level into their places of the claim order.
+__global__ void bk_leaf_count(bk_dev d, bk_solve_dev s)
+{
+    const int warp = blockIdx.x;
+    const int lane = threadIdx.x;
+    if (warp >= s.nleaves) return;
+    const bk_task &T = d.tasks[s.leaf_tasks[warp]];
+    for (int i = T.lo + lane; i < T.hi; i += 32) {
+        atomicAdd(s.lcnt + leaf_key(d, s, warp, T.lo, T.hi, i, 0), 1);
+        atomicAdd(s.lcnt + (s.leaf_maxrows + 1) + leaf_key(d, s, warp, T.lo, T.hi, i, 1), 1);
+    }
+}
+
+__global__ void __launch_bounds__(1024) bk_leaf_scan(bk_solve_dev s)
+{
+    // exclusive scan of both count arrays (one block; counts of at most leaf_maxrows levels)
+    __shared__ int64_t wt[33];
+    const int m = s.leaf_maxrows + 1;
+    for (int dir = 0; dir < 2; dir++) {
+        int32_t *c = s.lcnt + dir * m;
+        int64_t carry = 0;
+        for (int b0 = 0; b0 < m; b0 += 1024) {
+            const int i = b0 + threadIdx.x;
+            const int64_t v = i < m ? c[i] : 0;
+            int64_t total;
+            const int64_t ex = block_exscan(v, wt, total);
+            if (i < m) c[i] = (int32_t)(carry + ex);
+            carry += total;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void bk_leaf_scatter(bk_dev d, bk_solve_dev s)
+{
+    const int warp = blockIdx.x;
+    const int lane = threadIdx.x;
+    if (warp >= s.nleaves) return;
+    const bk_task &T = d.tasks[s.leaf_tasks[warp]];
+    const int m = s.leaf_maxrows + 1;
+    for (int i = T.lo + lane; i < T.hi; i += 32) {
+        s.items[s.leaf_f0 + atomicAdd(s.lcnt + leaf_key(d, s, warp, T.lo, T.hi, i, 0), 1)] = i;
+        s.items[s.leaf_b0 + atomicAdd(s.lcnt + m + leaf_key(d, s, warp, T.lo, T.hi, i, 1), 1)] = ~i;
+    }
+}
+
 // ---------------------------------------------------------------- the solve
 
 // Bounded wait until flags[j] == epoch for every lane with want.  Each lane
@@ -229,6 +311,116 @@ __device__ __forceinline__ V chain(V z, V a, V v, int cnt)
     return z;
 }
 
+// One warp solves a separator's own triangle, its rows' outside terms already
+// applied (the rows' values are in zs, in shared memory or in place in global
+// memory).  Forward: for k ascending, w_k = zs[k] is final and L(i,k) w_k is
+// subtracted from the node's rows i > k; backward: for k descending, z_k =
+// zs[k] / U(k,k) is final and U(j,k) z_k is subtracted from the node's rows
+// j < k.  Per row the terms come in the order of the row sweeps (ascending k
+// forward, descending backward), after the outside terms.
+// The node's own entries of a column, read ahead: up to SW_PF * 32 entries of
+// L(:,k) from its start (own rows come before ancestor rows) or of U(:,k) from
+// just above its diagonal downwards (own steps come after descendant steps).
+constexpr int SW_PF = 8;
+
+template <typename V>
+struct SweepCol {
+    int row[SW_PF];   // node-local row (-1: none)
+    V val[SW_PF];
+    int cnt;          // entries of the column (L) or strictly above the diagonal (U)
+    int64_t beg;
+    V diag;           // U(k,k) (backward only)
+};
+
+template <typename V>
+__device__ __forceinline__ void sweep_meta(const bk_dev &d, int k, bool lower, int64_t &beg, int &cnt, int lane)
+{
+    int64_t b = 0;
+    int c = 0;
+    if (lane == 0) {
+        b = lower ? d.Lbeg[k] : d.Ubeg[k];
+        c = lower ? d.Lcnt[k] : d.Ucnt[k];
+    }
+    beg = __shfl_sync(BK_FULL, b, 0);
+    cnt = __shfl_sync(BK_FULL, c, 0);
+}
+
+template <typename V>
+__device__ __forceinline__ void sweep_read(const bk_dev &d, const bk_solve_dev &s, SweepCol<V> &col, int64_t beg,
+                                           int cnt, bool lower, int lo, int hi, int lane)
+{
+    const V *const Lx = vals<V>(d.Lx);
+    const V *const Ux = vals<V>(d.Ux);
+    col.beg = beg;
+    col.cnt = lower ? cnt : cnt - 1;
+    if (!lower) col.diag = Ux[beg + cnt - 1];
+#pragma unroll
+    for (int u = 0; u < SW_PF; u++) {
+        const int t = lane + 32 * u;
+        col.row[u] = -1;
+        col.val[u] = V(0);
+        if (t >= col.cnt) continue;
+        const int64_t e = lower ? beg + t : beg + col.cnt - 1 - t;
+        const int i = lower ? s.r.Ls[e] : d.Ui[e];
+        if (lower ? i < hi : i >= lo) {
+            col.row[u] = i - lo;
+            col.val[u] = lower ? Lx[e] : Ux[e];
+        }
+    }
+}
+
+// One warp solves a separator's own triangle, its rows' outside terms already
+// applied (the rows' values are in zs, in shared memory or in place in global
+// memory).  Forward: for k ascending, w_k = zs[k] is final and L(i,k) w_k is
+// subtracted from the node's rows i > k; backward: for k descending, z_k =
+// zs[k] / U(k,k) is final and U(j,k) z_k is subtracted from the node's rows
+// j < k.  Per row the terms come in the order of the row sweeps (ascending k
+// forward, descending backward), after the outside terms.  The next column's
+// entries and the one after's extent are read while a column is applied.
+template <typename V>
+__device__ __forceinline__ void sweep(const bk_dev &d, const bk_solve_dev &s, int lo, int hi, V *zs, bool fwd,
+                                      int lane)
+{
+    const V *const Lx = vals<V>(d.Lx);
+    const V *const Ux = vals<V>(d.Ux);
+    const int nown = hi - lo;
+    SweepCol<V> cur, nxt;
+    int64_t nbeg = 0;
+    int ncnt = 0;
+    {
+        int64_t b0;
+        int c0;
+        sweep_meta<V>(d, fwd ? lo : hi - 1, fwd, b0, c0, lane);
+        sweep_read(d, s, cur, b0, c0, fwd, lo, hi, lane);
+        if (nown > 1) sweep_meta<V>(d, fwd ? lo + 1 : hi - 2, fwd, nbeg, ncnt, lane);
+    }
+    for (int step = 0; step < nown; step++) {
+        const int kl = fwd ? step : nown - 1 - step;      // node-local column
+        if (step + 1 < nown) sweep_read(d, s, nxt, nbeg, ncnt, fwd, lo, hi, lane);
+        if (step + 2 < nown) sweep_meta<V>(d, lo + (fwd ? step + 2 : nown - 3 - step), fwd, nbeg, ncnt, lane);
+        V vk = zs[kl];
+        if (!fwd) {
+            vk = vk / cur.diag;
+            __syncwarp();
+            if (lane == 0) zs[kl] = vk;
+        }
+#pragma unroll
+        for (int u = 0; u < SW_PF; u++)
+            if (cur.row[u] >= 0) zs[cur.row[u]] = fma(-cur.val[u], vk, zs[cur.row[u]]);
+        // entries past the read-ahead window, up to the first outside the node
+        for (int t = 32 * SW_PF + lane; t < cur.cnt; t += 32) {
+            const int64_t e = fwd ? cur.beg + t : cur.beg + cur.cnt - 1 - t;
+            const int i = fwd ? s.r.Ls[e] : d.Ui[e];
+            if (fwd ? i >= hi : i < lo) break;
+            zs[i - lo] = fma(-(fwd ? Lx[e] : Ux[e]), vk, zs[i - lo]);
+        }
+        __syncwarp();
+        cur = nxt;
+    }
+}
+
+constexpr int SEP_SMEM_ROWS = 1024;   // separator rows a warp sweeps in shared memory
+
 template <typename V>
 __global__ void __launch_bounds__(128) bk_solve_kernel(bk_dev d, bk_solve_dev s, int32_t nrhs,
                                                        const double *__restrict__ b, int32_t ldb, double *x,
@@ -236,7 +428,9 @@ __global__ void __launch_bounds__(128) bk_solve_kernel(bk_dev d, bk_solve_dev s,
                                                        const int32_t *__restrict__ Pin,
                                                        const int32_t *__restrict__ Qout)
 {
+    extern __shared__ __align__(16) double solve_smem[];
     const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
     const int64_t n = d.n;
     const V *const Bx = vals<V>(d.Bx);
     const V *const Lrx = vals<V>(s.r.Lrx);
@@ -244,15 +438,46 @@ __global__ void __launch_bounds__(128) bk_solve_kernel(bk_dev d, bk_solve_dev s,
     const V *const Ud = vals<V>(s.r.Ud);
     V *const w = vals<V>(s.w);
     V *const zz = vals<V>(s.z);
+    V *const zsm = reinterpret_cast<V *>(solve_smem) + (int64_t)wib * SEP_SMEM_ROWS;
     for (;;) {
         int k = 0;
         if (lane == 0) k = atomicAdd(d.counter + 2, 1);
         k = __shfl_sync(BK_FULL, k, 0);
         if (k >= s.nitems) break;
         const int it = s.items[k];
-        if (it >= 0) {
-            // forward row i: coupling terms of row prow i, then L(i,:)
-            const int i = it;
+        const bool fwd = it >= 0;
+        const int i = fwd ? it : ~it;
+        if (i >= n) {
+            // a separator's own triangle (forward or backward sweep)
+            const bk_task &T = d.tasks[i - n];
+            const int lo = T.lo, hi = T.hi, nown = hi - lo;
+            int32_t *flags = fwd ? s.fdone : s.bdone;
+            for (int r0 = lo; r0 < hi; r0 += 32)
+                if (!wait_flags(d, flags, r0 + lane, r0 + lane < hi, -epoch, budget)) return;
+            for (int q = 0; q < nrhs; q++) {
+                V *vq = (fwd ? w : zz) + q * n;
+                V *zs = nown <= SEP_SMEM_ROWS ? zsm : vq + lo;
+                if (zs == zsm)
+                    for (int r = lane; r < nown; r += 32) zs[r] = __ldcg(vq + lo + r);
+                __syncwarp();
+                sweep(d, s, lo, hi, zs, fwd, lane);
+                for (int r = lane; r < nown; r += 32) {
+                    const V v = zs[r];
+                    vq[lo + r] = v;
+                    if (!fwd) x[(int64_t)q * ldx + (Qout ? Qout[lo + r] : lo + r)] = (double)v;
+                }
+                __syncwarp();
+            }
+            __threadfence();
+            __syncwarp();
+            for (int r = lo + lane; r < hi; r += 32) st_release(flags + r, epoch);
+            continue;
+        }
+        // a separator's row takes only the terms from outside its node
+        const int clo = s.cutlo[i], chi = s.cuthi[i];
+        const bool part = clo >= 0;
+        if (fwd) {
+            // forward row i: coupling terms of row prow i, then L(i,k) for k < clo (or all)
             const int r = d.prow[i];
             const int e0 = s.offp[r], e1 = s.offp[r + 1];
             const int64_t l0 = s.r.Lrp[i], l1 = s.r.Lrp[i + 1];
@@ -268,45 +493,50 @@ __global__ void __launch_bounds__(128) bk_solve_kernel(bk_dev d, bk_solve_dev s,
                     z = chain(z, a, v, cnt);
                 }
                 for (int64_t e = l0; e < l1; e += 32) {
-                    const int cnt = (int)min((int64_t)32, l1 - e);
+                    int cnt = (int)min((int64_t)32, l1 - e);
+                    const int j0 = lane < cnt ? s.r.Lrk[e + lane] : 0;
+                    if (part) cnt = __popc(__ballot_sync(BK_FULL, lane < cnt && j0 < clo));
                     const bool have = lane < cnt;
-                    const int j = have ? s.r.Lrk[e + lane] : 0;
+                    const int j = have ? j0 : 0;
                     const V a = have ? Lrx[e + lane] : V(0);
                     if (!wait_flags(d, s.fdone, j, have, epoch, budget)) return;
                     const V v = have ? __ldcg(w + q * n + j) : V(0);
                     z = chain(z, a, v, cnt);
+                    if (cnt < 32) break;
                 }
                 if (lane == 0) w[q * n + i] = z;
             }
             __threadfence();
             __syncwarp();
-            if (lane == 0) st_release(s.fdone + i, epoch);
+            if (lane == 0) st_release(s.fdone + i, part ? -epoch : epoch);
         } else {
-            // backward row i: its forward result, then U(i,:), then the diagonal
-            const int i = ~it;
+            // backward row i: its forward result, then U(i,k) for k >= chi (or all), then the diagonal
             if (!wait_flags(d, s.fdone, i, lane == 0, epoch, budget)) return;
             const int64_t u0 = s.r.Urp[i], u1 = s.r.Urp[i + 1];
             const V ud = Ud[i];
             for (int q = 0; q < nrhs; q++) {
                 V z = __shfl_sync(BK_FULL, lane == 0 ? __ldcg(w + q * n + i) : V(0), 0);
                 for (int64_t e = u0; e < u1; e += 32) {
-                    const int cnt = (int)min((int64_t)32, u1 - e);
+                    int cnt = (int)min((int64_t)32, u1 - e);
+                    const int j0 = lane < cnt ? s.r.Urk[e + lane] : 0;
+                    if (part) cnt = __popc(__ballot_sync(BK_FULL, lane < cnt && j0 >= chi));
                     const bool have = lane < cnt;
-                    const int j = have ? s.r.Urk[e + lane] : 0;
+                    const int j = have ? j0 : 0;
                     const V a = have ? Urx[e + lane] : V(0);
                     if (!wait_flags(d, s.bdone, j, have, epoch, budget)) return;
                     const V v = have ? __ldcg(zz + q * n + j) : V(0);
                     z = chain(z, a, v, cnt);
+                    if (cnt < 32) break;
                 }
-                z = z / ud;
+                if (!part) z = z / ud;
                 if (lane == 0) {
                     zz[q * n + i] = z;
-                    x[(int64_t)q * ldx + (Qout ? Qout[i] : i)] = (double)z;
+                    if (!part) x[(int64_t)q * ldx + (Qout ? Qout[i] : i)] = (double)z;
                 }
             }
             __threadfence();
             __syncwarp();
-            if (lane == 0) st_release(s.bdone + i, epoch);
+            if (lane == 0) st_release(s.bdone + i, part ? -epoch : epoch);
         }
     }
 }
@@ -318,7 +548,8 @@ int solve_blocks()
         int dev = 0, sms = 0, per = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, bk_solve_kernel<double>, 128, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, bk_solve_kernel<double>, 128,
+                                                      4 * SEP_SMEM_ROWS * sizeof(double));
         blocks = std::max(1, sms) * std::max(1, std::min(per, 8));
     }
     return blocks;
@@ -361,16 +592,29 @@ void bk_launch_rows(const bk_dev &d, const bk_rows &r, void *stream)
     }
 }
 
+void bk_launch_leaf_order(const bk_dev &d, const bk_solve_dev &s, void *stream)
+{
+    if (s.nleaves <= 0) return;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaMemsetAsync(s.leaf_bad, 0, sizeof(int32_t) * (size_t)s.nleaves, st);
+    bk_leaf_check<<<s.nleaves, 256, 0, st>>>(d, s);
+    cudaMemsetAsync(s.lcnt, 0, sizeof(int32_t) * 2 * ((size_t)s.leaf_maxrows + 1), st);
+    bk_leaf_count<<<s.nleaves, 32, 0, st>>>(d, s);
+    bk_leaf_scan<<<1, 1024, 0, st>>>(s);
+    bk_leaf_scatter<<<s.nleaves, 32, 0, st>>>(d, s);
+}
+
 void bk_launch_solve(const bk_dev &d, const bk_solve_dev &s, int32_t nrhs, const double *b, int32_t ldb,
                      double *x, int32_t ldx, int32_t epoch, long long budget, void *stream, bool permute)
 {
     const int32_t *Pin = permute ? d.P : nullptr, *Qout = permute ? d.Q : nullptr;
     if (s.nitems <= 0) return;
     const int ctas = std::min<int>((s.nitems + 3) / 4, solve_blocks());
+    const size_t smem = (size_t)4 * SEP_SMEM_ROWS * sizeof(double);
     if (d.prec)
-        bk_solve_kernel<float><<<ctas, 128, 0, (cudaStream_t)stream>>>(d, s, nrhs, b, ldb, x, ldx, epoch, budget, Pin,
+        bk_solve_kernel<float><<<ctas, 128, smem, (cudaStream_t)stream>>>(d, s, nrhs, b, ldb, x, ldx, epoch, budget, Pin,
                                                                         Qout);
     else
-        bk_solve_kernel<double><<<ctas, 128, 0, (cudaStream_t)stream>>>(d, s, nrhs, b, ldb, x, ldx, epoch, budget, Pin,
+        bk_solve_kernel<double><<<ctas, 128, smem, (cudaStream_t)stream>>>(d, s, nrhs, b, ldb, x, ldx, epoch, budget, Pin,
                                                                          Qout);
 }

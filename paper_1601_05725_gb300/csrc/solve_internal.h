@@ -15,6 +15,7 @@ struct bk_rows {
     int64_t *Lrp, *Urp;          // n + 1 row starts
     int32_t *Lrk, *Urk;          // column steps
     double *Lrx, *Urx;           // values
+    int32_t *Ls;                 // L's row indices as steps, in L's column order
     int32_t *tk;                 // unsorted scatter (steps), capacity max(L, U) entries
     double *tx;                  // unsorted scatter (values)
     double *Ud;                  // n diagonal entries of U
@@ -23,8 +24,18 @@ struct bk_rows {
 };
 
 struct bk_solve_dev {
-    int32_t nitems;               // 2 n: every step forward, then backward, block by block
-    const int32_t *items;         // k >= 0: forward row k; ~k: backward row k
+    int32_t nitems;               // every step forward and backward, and every ND separator twice
+    int32_t *items;               // k < n: forward row k; n + t: forward sweep of separator task t;
+                                  // ~k, ~(n + t): the same backward
+    // ND leaves: their rows' places in items are filled after every factorization,
+    // all leaves together, in order of the factorization's column levels
+    // (increasing forward, decreasing backward; see kernels_solve.cu)
+    int32_t nleaves;
+    const int32_t *leaf_tasks;
+    int32_t leaf_rows, leaf_f0, leaf_b0, leaf_maxrows;
+    int32_t *leaf_bad;            // per leaf: the levels do not order its forward rows
+    int32_t *lcnt;                // 2 (leaf_maxrows + 1): per-key counts, then starts
+    const int32_t *cutlo, *cuthi; // per step: its separator's own rows [lo, hi), or lo = hi = -1
     const int32_t *offp, *offj, *offpos;  // coupling of B by row: columns of later blocks
     int32_t *fdone, *bdone;       // per-step flags of the forward and the backward pass
     double *w;                    // n x nrhs, forward results by step
@@ -33,11 +44,13 @@ struct bk_solve_dev {
 };
 
 struct bk_solve_plan {
-    std::vector<int32_t> items, offp, offj, offpos;
+    std::vector<int32_t> items, offp, offj, offpos, cutlo, cuthi, leaf_tasks;
+    int32_t leaf_rows = 0, leaf_f0 = -1, leaf_b0 = -1, leaf_maxrows = 0;
 };
 
 void bk_solve_plan_build(const bk_plan &pl, bk_solve_plan &sp);
 void bk_launch_rows(const bk_dev &d, const bk_rows &r, void *stream);
+void bk_launch_leaf_order(const bk_dev &d, const bk_solve_dev &s, void *stream);
 // permute: b is indexed by A's rows and x by A's columns (b(P), x(Q)); otherwise
 // both are in B's row / column space (the refinement's corrections).
 void bk_launch_solve(const bk_dev &d, const bk_solve_dev &s, int32_t nrhs, const double *b, int32_t ldb,

@@ -31,19 +31,29 @@ void bk_solve_plan_build(const bk_plan &pl, bk_solve_plan &sp)
                 }
     }
     // Claim order: blocks from last to first; in each, the forward rows, then the
-    // backward rows.  Every row waits only for rows claimed before it.  In a block
-    // without ND the forward rows go in ascending step order and the backward rows
-    // in descending order.  In the ND block the rows of independent nodes are
-    // interleaved so that the warps in flight cover the whole tree level: forward,
-    // tree levels from the leaves up, the nodes of a level taking turns row by
-    // row (ascending in each node); backward, levels from the root down (rows
-    // descending in each node).  A node's rows depend only on its own earlier
-    // (forward) or later (backward) rows and on its descendants (forward) or
-    // ancestors (backward), so both orders are topological.
+    // backward rows.  Every item waits only for items claimed before it.  In a
+    // block without ND the forward rows go in ascending step order and the
+    // backward rows in descending order.  In the ND block, forward, tree levels
+    // from the leaves up; backward, levels from the root down.  The rows of the
+    // nodes of a level take turns row by row (ascending in each node forward,
+    // descending backward), so that the warps in flight cover the whole level.
+    // A leaf's rows are complete row items.  A separator (a node above others)
+    // is dense: its row items take only the terms from outside the node
+    // (coupling and descendants forward, ancestors backward), and one sweep item
+    // per separator, after its rows, solves the node's own triangle in one warp.
     sp.items.clear();
-    sp.items.reserve((size_t)2 * (size_t)n);
+    sp.items.reserve((size_t)2 * (size_t)n + 2 * pl.tasks.size());
+    sp.cutlo.assign((size_t)n, -1);
+    sp.cuthi.assign((size_t)n, -1);
     int32_t maxh = 0;
     for (const auto &T : pl.tasks) maxh = std::max(maxh, T.level);
+    auto is_sep = [&](const bk_task &T) { return T.node >= 0 && T.sp_lo < T.lo; };
+    for (const auto &T : pl.tasks)
+        if (is_sep(T))
+            for (int32_t i = T.lo; i < T.hi; i++) {
+                sp.cutlo[(size_t)i] = T.lo;
+                sp.cuthi[(size_t)i] = T.hi;
+            }
     auto interleave = [&](const std::vector<int32_t> &tasks, bool fwd) {
         int32_t longest = 0;
         for (int32_t t : tasks) longest = std::max(longest, pl.tasks[(size_t)t].hi - pl.tasks[(size_t)t].lo);
@@ -53,6 +63,8 @@ void bk_solve_plan_build(const bk_plan &pl, bk_solve_plan &sp)
                 if (q >= T.hi - T.lo) continue;
                 sp.items.push_back(fwd ? T.lo + q : ~(T.hi - 1 - q));
             }
+        for (int32_t t : tasks)
+            if (is_sep(pl.tasks[(size_t)t])) sp.items.push_back(fwd ? n + t : ~(n + t));
     };
     for (int32_t d = pl.nblocks - 1; d >= 0; d--) {
         const int32_t k0 = pl.block_ptr[(size_t)d], k1 = pl.block_ptr[(size_t)d + 1];
@@ -64,7 +76,18 @@ void bk_solve_plan_build(const bk_plan &pl, bk_solve_plan &sp)
         std::vector<std::vector<int32_t>> by_height((size_t)maxh + 1);
         for (size_t t = 0; t < pl.tasks.size(); t++)
             if (pl.tasks[t].block == d) by_height[(size_t)pl.tasks[t].level].push_back((int32_t)t);
+        // the leaves (height 0) get their order after each factorization; their
+        // places here hold a valid order until then
+        sp.leaf_tasks = by_height[0];
+        sp.leaf_rows = 0;
+        for (int32_t t : sp.leaf_tasks) {
+            sp.leaf_rows += pl.tasks[(size_t)t].hi - pl.tasks[(size_t)t].lo;
+            sp.leaf_maxrows = std::max(sp.leaf_maxrows, pl.tasks[(size_t)t].hi - pl.tasks[(size_t)t].lo);
+        }
+        sp.leaf_f0 = (int32_t)sp.items.size();
         for (int32_t h = 0; h <= maxh; h++) interleave(by_height[(size_t)h], true);
-        for (int32_t h = maxh; h >= 0; h--) interleave(by_height[(size_t)h], false);
+        for (int32_t h = maxh; h >= 1; h--) interleave(by_height[(size_t)h], false);
+        sp.leaf_b0 = (int32_t)sp.items.size();
+        interleave(by_height[0], false);
     }
 }
