@@ -65,9 +65,12 @@ typedef struct {
                                      error in FP64) until the backward error reaches ir_tol;
                                      a factorization whose pivot growth exceeds growth_limit,
                                      that fails in FP32, or whose refinement stalls is redone
-                                     in FP64 (BASKER_OK; basker_info counts it) */
-    int ir_max_iter;              /* precision 1: refinement steps at most; default 10 */
-    double ir_tol;                /* precision 1: backward error to reach; default 1e-13 */
+                                     in FP64 (BASKER_OK; basker_info counts it).
+                                     2: FP64 factorization; every solve refined in FP64
+                                     the same way until its backward error reaches ir_tol
+                                     (at most ir_max_iter solves; no FP64 redo needed) */
+    int ir_max_iter;              /* precision 1, 2: refinement steps at most; default 10 */
+    double ir_tol;                /* precision 1, 2: backward error to reach; default 1e-13 */
     double growth_limit;          /* precision 1: max over BTF blocks of max|U_d| / max|B_d|
                                      above which the FP32 factors are not used; default 1e4 */
     int reserved[4];
@@ -109,6 +112,11 @@ typedef struct {
     int32_t reserved[2];
     double ir_eta;                /* precision 1: backward error after the last solve's refinement */
     double growth;                /* precision 1: pivot growth of the last FP32 factorization */
+    int32_t kernel_calls[10];     /* launches per kernel kind (as kernel_ms) since the last
+                                     basker_info call, counted with or without timing */
+    int32_t reserved2[2];
+    int64_t rounds_columns;       /* columns processed by refactorization rounds since the
+                                     last basker_info call */
 } basker_info_t;
 
 /* Defaults listed in basker_options. */

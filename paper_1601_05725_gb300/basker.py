@@ -53,7 +53,9 @@ class Info(ctypes.Structure):
                 ("internal_site", ctypes.c_int32), ("internal_col", ctypes.c_int32),
                 ("last_rounds", ctypes.c_int32), ("ir_iterations", ctypes.c_int32),
                 ("ir_fallbacks", ctypes.c_int32), ("precision_used", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2), ("ir_eta", ctypes.c_double), ("growth", ctypes.c_double)]
+                ("reserved", ctypes.c_int32 * 2), ("ir_eta", ctypes.c_double), ("growth", ctypes.c_double),
+                ("kernel_calls", ctypes.c_int32 * 10), ("reserved2", ctypes.c_int32 * 2),
+                ("rounds_columns", ctypes.c_int64)]
 
 KERNEL_KINDS = ["gather", "static_refactor", "dag_levels", "gp_in_node", "gp_descendant", "solve",
                 "pivot_reset", "refactor_rounds", "rows_transpose", "refine"]
@@ -239,7 +241,9 @@ class Handle:
         s = self.lib.basker_info(self.h, ctypes.byref(inf))
         if s != 0:
             raise BaskerError(s, "basker_info")
-        out = {k: getattr(inf, k) for k, _ in Info._fields_ if k not in ("reserved", "kernel_ms")}
+        out = {k: getattr(inf, k) for k, _ in Info._fields_ if k not in ("reserved", "reserved2", "kernel_ms",
+                                                                          "kernel_calls")}
+        out["kernel_calls"] = {KERNEL_KINDS[i]: inf.kernel_calls[i] for i in range(len(KERNEL_KINDS))}
         out["kernel_ms"] = {KERNEL_KINDS[i]: inf.kernel_ms[i] for i in range(len(KERNEL_KINDS))}
         return out
 

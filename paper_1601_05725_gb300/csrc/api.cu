@@ -84,6 +84,7 @@ cudaEvent_t take_event(basker_t h)
 void tbeg(basker_t h, int kind, cudaStream_t s, int nkernels)
 {
     h->info.kernel_launches += nkernels;
+    h->info.kernel_calls[kind]++;
     if (!h->opt.timing) return;
     h->open_ev = take_event(h);
     h->open_kind = kind;
@@ -225,8 +226,8 @@ int setup_device(basker_t h)
     const int32_t n = pl.n;
     d.n = n;
     d.ntasks = (int32_t)pl.tasks.size();
-    d.prec = h->opt.precision;
-    if (d.prec) {
+    d.prec = h->opt.precision == 1 ? 1 : 0;     // precision 2: FP64 factors, refined solves
+    if (h->opt.precision >= 1) {
         // B by rows (entries in ascending column order) for the FP64 residual
         std::vector<int64_t> brp((size_t)n + 1, 0);
         for (int32_t j = 0; j < n; j++)
@@ -502,6 +503,7 @@ int launch_redo(basker_t h, cudaStream_t s)
             h->launches++;
             h->info.last_rounds++;
             redone += (int32_t)cols.size();
+            h->info.rounds_columns += (int64_t)cols.size();
             CU(cudaMemcpyAsync(h->h_task_fail, h->d.task_fail, sizeof(int32_t) * nt, cudaMemcpyDeviceToHost, s));
             const int st = read_status(h, s);
             if (st != BASKER_OK) return st;
@@ -683,6 +685,17 @@ int finish_fp32(basker_t h, const double *values, cudaStream_t s, int st)
     return s64;
 }
 
+// precision 2: FP64 factors; B in FP64 and ||B||_inf for the refined solves.
+int finish_fp64(basker_t h, const double *values, cudaStream_t s)
+{
+    bk_launch_gather64(h->d, h->rf, values, h->pl.nnz, s);
+    bk_launch_norms(h->d, h->rf, h->d_norms, s);
+    CU(cudaMemcpyAsync(h->h_norms, h->d_norms, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    h->bnorm = h->h_norms[0];
+    return BASKER_OK;
+}
+
 int ensure_ir_buffers(basker_t h, int32_t nrhs)
 {
     if (nrhs <= h->ir_cap) return BASKER_OK;
@@ -748,6 +761,7 @@ int solve_refined(basker_t h, int32_t nrhs, const double *b, int32_t ldb, double
         h->info.ir_iterations = it;
         h->info.ir_eta = eta;
         if (eta <= h->opt.ir_tol) break;
+        if (h->opt.precision == 2 && (it >= h->opt.ir_max_iter || !(eta <= 0.5 * prev))) break;   // FP64 already
         if (it >= h->opt.ir_max_iter || !(eta <= 0.5 * prev)) {
             TRY(factor_twin(h, s));
             h->info.precision_used = 0;
@@ -756,7 +770,7 @@ int solve_refined(basker_t h, int32_t nrhs, const double *b, int32_t ldb, double
         prev = eta;
     }
     bk_launch_ir_finish(h->d, nrhs, h->ir_z, x, ldx, s);
-    h->info.precision_used = 1;
+    h->info.precision_used = h->d.prec;
     CU(cudaGetLastError());
     return BASKER_OK;
 }
@@ -838,8 +852,8 @@ int basker_symbolic(int32_t n, const int32_t *colptr, const int32_t *rowind, con
     basker_default_options(&h->opt);
     if (opt) h->opt = *opt;
     if (!(h->opt.tau > 0.0 && h->opt.tau <= 1.0) || h->opt.slack < 0.0 || h->opt.wait_budget_cycles <= 0 ||
-        h->opt.factor_mode != 0 || (h->opt.precision != 0 && h->opt.precision != 1) ||
-        (h->opt.precision == 1 && (h->opt.ir_max_iter < 1 || !(h->opt.ir_tol > 0.0) || !(h->opt.growth_limit > 0.0)))) {
+        h->opt.factor_mode != 0 || h->opt.precision < 0 || h->opt.precision > 2 ||
+        (h->opt.precision >= 1 && (h->opt.ir_max_iter < 1 || !(h->opt.ir_tol > 0.0) || !(h->opt.growth_limit > 0.0)))) {
         delete h;
         return BASKER_ERR_INVALID_ARG;
     }
@@ -887,7 +901,8 @@ int basker_factor(basker_t h, const double *values_dev, void *stream)
         CU(cudaMemcpyAsync(h->d_vals64, values_dev, sizeof(double) * (size_t)h->pl.nnz, cudaMemcpyDeviceToDevice, s));
     int st = factor_impl(h, values_dev, s, false);
     h->info.gp_launches = h->launches;
-    if (h->opt.precision) st = finish_fp32(h, values_dev, s, st);
+    if (h->opt.precision == 1) st = finish_fp32(h, values_dev, s, st);
+    if (h->opt.precision == 2 && st == BASKER_OK) st = finish_fp64(h, values_dev, s);
     return st;
 }
 
@@ -900,11 +915,12 @@ int basker_refactor(basker_t h, const double *values_dev, void *stream)
     if (h->opt.precision && h->pl.nnz > 0)
         CU(cudaMemcpyAsync(h->d_vals64, values_dev, sizeof(double) * (size_t)h->pl.nnz, cudaMemcpyDeviceToDevice, s));
     // FP32 factors that failed last time are not a base to refactor from
-    const bool re = !h->opt.precision || h->fp32_valid;
+    const bool re = h->opt.precision != 1 || h->fp32_valid;
     if (!re) h->factored = false;
     int st = factor_impl(h, values_dev, s, re);
     h->info.static_launches = h->launches;
-    if (h->opt.precision) st = finish_fp32(h, values_dev, s, st);
+    if (h->opt.precision == 1) st = finish_fp32(h, values_dev, s, st);
+    if (h->opt.precision == 2 && st == BASKER_OK) st = finish_fp64(h, values_dev, s);
     return st;
 }
 
@@ -965,6 +981,8 @@ int basker_info(basker_t h, basker_info_t *out)
     tflush(h);
     *out = h->info;
     for (double &v : h->info.kernel_ms) v = 0.0;
+    for (int32_t &v : h->info.kernel_calls) v = 0;
+    h->info.rounds_columns = 0;
     if (!h->factored) return BASKER_OK;
     {
         const size_t n = (size_t)h->pl.n;

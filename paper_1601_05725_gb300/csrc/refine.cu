@@ -1,8 +1,9 @@
-// refine.cu -- FP64 iterative refinement around the FP32 factorization.
+// refine.cu -- FP64 iterative refinement of the solves.
 //
-// The factorization and the triangular solves run in FP32; FP64 holds the
-// residual r = c - B z, the update z += dz and the norms of the backward error,
-// all in B's row/column space (c = b(P), x(Q) = z):
+// With FP32 factors (options.precision 1) the triangular solves run in FP32;
+// with FP64 factors (precision 2) in FP64.  FP64 holds the residual
+// r = c - B z, the update z += dz and the norms of the backward error, all in
+// B's row/column space (c = b(P), x(Q) = z):
 //   eta = ||c - B z||_inf / (||B||_inf ||z||_inf + ||c||_inf)
 // The pivot growth max|U_d| / max|B_d| of every BTF block decides, after each
 // factorization, whether the FP32 factors are used at all.
@@ -53,9 +54,11 @@ __global__ void bk_norms_kernel(bk_dev d, bk_refine_dev rf, double *norms)
         }
         // column i of U (its block is the block of row i: diagonal blocks are square)
         float um = 0.0f;
-        const int64_t ub = d.Ubeg[i];
-        const int uc = d.Ucnt[i];
-        for (int t = lane; t < uc; t += 32) um = fmaxf(um, fabsf(Ux[ub + t]));
+        if (d.prec) {
+            const int64_t ub = d.Ubeg[i];
+            const int uc = d.Ucnt[i];
+            for (int t = lane; t < uc; t += 32) um = fmaxf(um, fabsf(Ux[ub + t]));
+        }
         um = warp_max(um);
         if (lane == 0) {
             max_nonneg(norms, s);

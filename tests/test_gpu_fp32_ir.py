@@ -122,8 +122,29 @@ def test_stalled_refinement_falls_back_to_fp64():
 
 def test_precision_option_is_validated():
     prob = I.small_problem(33, "grid", k=10, depth=1)
-    for kw in (dict(precision=2), dict(precision=1, ir_max_iter=0), dict(precision=1, ir_tol=0.0),
+    for kw in (dict(precision=3), dict(precision=1, ir_max_iter=0), dict(precision=1, ir_tol=0.0),
                dict(precision=1, growth_limit=-1.0)):
         with pytest.raises(basker.BaskerError) as e:
             basker.Handle.from_problem(prob, **kw)
         assert e.value.name == "INVALID_ARG"
+
+
+def test_fp64_refined_solve_meets_the_bar_and_equals_plain_fp64_when_one_step_suffices():
+    prob = I.small_problem(41, "netlist", n_small=60, m_netlist=400, depth=2)
+    A = H.a_matrix(prob)
+    h2 = basker.Handle.from_problem(prob, precision=2, ir_tol=1e-12)
+    h0 = basker.Handle.from_problem(prob)
+    for h in (h2, h0):
+        h.factor(_dev(prob.values))
+    b = np.random.default_rng(41).standard_normal(prob.n)
+    x2, x0 = _solve(h2, b), _solve(h0, b)
+    inf = h2.info()
+    assert inf["precision_used"] == 0 and inf["ir_iterations"] >= 1 and inf["ir_fallbacks"] == 0
+    assert H.solve_backward_error(A, x2, b) <= ETA
+    if inf["ir_iterations"] == 1:
+        np.testing.assert_array_equal(x2, x0)
+    # a stricter target takes further steps and still converges
+    h3 = basker.Handle.from_problem(prob, precision=2, ir_tol=1e-16)
+    h3.factor(_dev(prob.values))
+    x3 = _solve(h3, b)
+    assert H.solve_backward_error(A, x3, b) <= ETA
