@@ -215,6 +215,7 @@ int upload_symbolic_pattern(basker_t h)
     CU(cudaMemcpy(h->d.prow, prow.data(), (size_t)pl.n * 4, cudaMemcpyHostToDevice));
     CU(cudaMemcpy(h->d.pinv, pinv.data(), (size_t)pl.n * 4, cudaMemcpyHostToDevice));
     CU(cudaMemcpy(h->d.order, pl.sorder.data(), (size_t)pl.n * 4, cudaMemcpyHostToDevice));
+    if (!h->d.iorder) TRY(upload(h, (int32_t **)&h->d.iorder, pl.iorder));
     CU(cudaMemcpy(h->d.level, pl.slevel.data(), (size_t)pl.n * 4, cudaMemcpyHostToDevice));
     return BASKER_OK;
 }

@@ -91,6 +91,7 @@ struct bk_dev {
     unsigned char *ws;               // global workspace (zero between uses)
     int32_t *done;                   // per column: epoch of its last completion (static kernel)
     int32_t *order;                  // static kernel claim order (topological)
+    const int32_t *iorder;           // levels kernel claim order: tasks by level, interleaved
     int32_t *counter;                // claim counters
     int32_t *level;                  // per column level in the static DAG
     double *ahat;                    // separator columns after the descendant phase (dense, L-space)
@@ -125,6 +126,7 @@ struct bk_plan {
     std::vector<int64_t> sLbeg, sUbeg, lcapc, ucapc;  // region starts; per-column capacities
     std::vector<int32_t> sLcnt, sUcnt, sLi, sUi, sprow;
     std::vector<int32_t> slevel, sorder;              // static DAG levels and claim order
+    std::vector<int32_t> iorder;                      // tasks by level, each level's tasks taking turns
     int64_t lcap = 0, ucap = 0, nnz_l_sym = 0, nnz_u_sym = 0;
     int64_t lpool = 0, upool = 0;                     // spill pools after the layout's regions
     int64_t ws_bytes = 0;                             // GP global workspace

@@ -76,6 +76,7 @@ __global__ void __launch_bounds__(128) bk_levels_kernel(bk_dev d, int32_t epoch,
         if (lane == 0) c = atomicAdd(d.counter + 1, 1);
         c = __shfl_sync(BK_FULL, c, 0);
         if (c >= d.n) break;
+        c = d.iorder[c];
         const int64_t ub = d.Ubeg[c];
         const int uc = d.Ucnt[c];
         int lv = 0;

@@ -66,6 +66,28 @@ void bk_solve_plan_build(const bk_plan &pl, bk_solve_plan &sp)
         for (int32_t t : tasks)
             if (is_sep(pl.tasks[(size_t)t])) sp.items.push_back(fwd ? n + t : ~(n + t));
     };
+    // Height-0 tasks (ND leaves, and BTF blocks when no coupling entry ties
+    // the blocks together) get their order after each factorization (leaf_*).
+    auto note_leaves = [&](const std::vector<int32_t> &tasks) {
+        sp.leaf_tasks = tasks;
+        sp.leaf_rows = 0;
+        for (int32_t t : tasks) {
+            sp.leaf_rows += pl.tasks[(size_t)t].hi - pl.tasks[(size_t)t].lo;
+            sp.leaf_maxrows = std::max(sp.leaf_maxrows, pl.tasks[(size_t)t].hi - pl.tasks[(size_t)t].lo);
+        }
+    };
+    if (sp.offp[(size_t)n] == 0) {
+        // no coupling: every block is independent; all tasks by height together
+        std::vector<std::vector<int32_t>> by_height((size_t)maxh + 1);
+        for (size_t t = 0; t < pl.tasks.size(); t++) by_height[(size_t)pl.tasks[t].level].push_back((int32_t)t);
+        note_leaves(by_height[0]);
+        sp.leaf_f0 = (int32_t)sp.items.size();
+        for (int32_t h = 0; h <= maxh; h++) interleave(by_height[(size_t)h], true);
+        for (int32_t h = maxh; h >= 1; h--) interleave(by_height[(size_t)h], false);
+        sp.leaf_b0 = (int32_t)sp.items.size();
+        interleave(by_height[0], false);
+        return;
+    }
     for (int32_t d = pl.nblocks - 1; d >= 0; d--) {
         const int32_t k0 = pl.block_ptr[(size_t)d], k1 = pl.block_ptr[(size_t)d + 1];
         if (d != pl.nd_block) {
@@ -78,12 +100,7 @@ void bk_solve_plan_build(const bk_plan &pl, bk_solve_plan &sp)
             if (pl.tasks[t].block == d) by_height[(size_t)pl.tasks[t].level].push_back((int32_t)t);
         // the leaves (height 0) get their order after each factorization; their
         // places here hold a valid order until then
-        sp.leaf_tasks = by_height[0];
-        sp.leaf_rows = 0;
-        for (int32_t t : sp.leaf_tasks) {
-            sp.leaf_rows += pl.tasks[(size_t)t].hi - pl.tasks[(size_t)t].lo;
-            sp.leaf_maxrows = std::max(sp.leaf_maxrows, pl.tasks[(size_t)t].hi - pl.tasks[(size_t)t].lo);
-        }
+        note_leaves(by_height[0]);
         sp.leaf_f0 = (int32_t)sp.items.size();
         for (int32_t h = 0; h <= maxh; h++) interleave(by_height[(size_t)h], true);
         for (int32_t h = maxh; h >= 1; h--) interleave(by_height[(size_t)h], false);

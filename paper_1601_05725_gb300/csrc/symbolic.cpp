@@ -199,6 +199,20 @@ int bk_plan_build(int32_t n, const int32_t *colptr, const int32_t *rowind, const
     }
     pl.level_tasks.assign((size_t)maxlevel + 1, {});
     for (size_t i = 0; i < pl.tasks.size(); i++) pl.level_tasks[(size_t)pl.tasks[i].level].push_back((int32_t)i);
+    // a topological order of the columns with breadth: the tasks of a level take
+    // turns column by column (a column depends on earlier columns of its task and
+    // on the tasks below it)
+    pl.iorder.clear();
+    pl.iorder.reserve((size_t)n);
+    for (const auto &lt : pl.level_tasks) {
+        int32_t longest = 0;
+        for (int32_t t : lt) longest = std::max(longest, pl.tasks[(size_t)t].c1 - pl.tasks[(size_t)t].c0);
+        for (int32_t q = 0; q < longest; q++)
+            for (int32_t t : lt) {
+                const bk_task &T = pl.tasks[(size_t)t];
+                if (q < T.c1 - T.c0) pl.iorder.push_back(T.c0 + q);
+            }
+    }
     pl.max_space = 0;
     for (auto &T : pl.tasks) pl.max_space = std::max(pl.max_space, T.space);
 
