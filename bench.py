@@ -43,7 +43,7 @@ def _args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-sample", type=int, default=4, help="oracle steps in the cpu_baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["powergrid", "batched"], default="powergrid",
+    ap.add_argument("--workload", choices=["powergrid", "batched", "serving"], default="powergrid",
                     help="powergrid: the metric's refactor+solve sequence; batched: factor+solve of "
                          "8,192 independent blocks (a secondary measurement)")
     return ap.parse_args()
@@ -343,10 +343,76 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_serving(args):
+    """Serving stream (a reduced config 5): netlist patterns of log-uniform size,
+    requests of a random pattern with values base x (1 + N(0, 0.05)) and b = A 1;
+    first all at once (saturated throughput), then Poisson arrivals at 0.5, 0.8 and
+    0.95 of it; p50/p99 latency from arrival to result on the host."""
+    import torch
+    from paper_1601_05725_gb300 import build, inputs
+    from paper_1601_05725_gb300.serve import Request, Server, latency_summary, poisson_arrivals
+    world, rank, local = _dist()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    build.build()
+    rng = np.random.default_rng(1005)
+    npat, nreq = 12, max(48, args.steps * 4)
+    sizes = np.round(np.exp(rng.uniform(np.log(5000), np.log(100000), npat))).astype(int)
+    pats = {}
+    for k, m in enumerate(sizes):
+        depth = int(np.clip(round(np.log2(m / 2000.0)), 2, 5))
+        pats[f"p{k}"] = inputs.netlist_problem(2000 + k, n_small=0, m_netlist=int(m), depth=depth,
+                                               name=f"serve_{k}")
+    names = sorted(pats)
+
+    def stream(count, arrivals, seed):
+        r = np.random.default_rng(seed)
+        out = []
+        for i in range(count):
+            name = names[int(r.integers(0, len(names)))]
+            v = inputs.refactor_values(pats[name], 1 + i % 10)
+            out.append(Request(i, name, v, inputs.rhs_ones(pats[name], v), float(arrivals[i])))
+        return out
+
+    clocks = Clocks(local)
+    t_a = time.time()
+    forms = {}
+    for name, prec in (("fp64_ir", 2), ("fp32_ir", 1)):
+        srv = Server(pats, slots=4, mem_cap=100e9, precision=prec)
+        srv.run(stream(len(names), np.zeros(len(names)), 1))          # factor every pattern once
+        sat = latency_summary(srv.run(stream(nreq, np.zeros(nreq), 2)))
+        loads = {}
+        for frac in (0.5, 0.8, 0.95):
+            rate = frac * sat["throughput"]
+            res = srv.run(stream(nreq, poisson_arrivals(np.random.default_rng(3), nreq, rate), 3))
+            loads[str(frac)] = dict(latency_summary(res), offered_rate=rate)
+        srv.close()
+        forms[name] = {"saturated": sat, "poisson": loads}
+    clk = clocks.stop(t_a, time.time())
+    head = max(forms, key=lambda n: forms[n]["saturated"]["throughput"])
+    hf = forms[head]
+    out = {"metric": "serving refactor+solve/s (saturated) with p50/p99 latency at 0.5/0.8/0.95 load",
+           "value": hf["saturated"]["throughput"], "unit": "requests/s", "n_gpus": 1, "steps": nreq,
+           "warmup": len(names), "ms_per_step": 1e3 / hf["saturated"]["throughput"], "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": {"fp64_ir": "f64 (refined in f64)", "fp32_ir": "f32 factor + f64 refinement"}[head],
+           "data": "synthetic", "form": head,
+           "config": {"workload": "serving_netlist_patterns", "patterns": npat,
+                      "n_range": [int(sizes.min()), int(sizes.max())], "requests_per_run": nreq, "slots": 4,
+                      "mem_cap_gb": 100, "latency": "host clock, arrival to result"},
+           "p50_ms": hf["saturated"]["p50_ms"], "p99_ms": hf["saturated"]["p99_ms"],
+           "forms": forms, "clocks": clk}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     global WORKLOAD, METRIC, UNIT
     args = _args()
     WORKLOAD = args.workload
+    if WORKLOAD == "serving":
+        run_serving(args)
+        return
     if WORKLOAD == "batched":
         METRIC = "factor+solve/s of 8,192 independent blocks at backward err<=1e-12, FP32+IR vs FP64"
         UNIT = "factor+solve/s"

@@ -114,7 +114,9 @@ typedef struct {
     double growth;                /* precision 1: pivot growth of the last FP32 factorization */
     int32_t kernel_calls[10];     /* launches per kernel kind (as kernel_ms) since the last
                                      basker_info call, counted with or without timing */
-    int32_t reserved2[2];
+    int32_t cuda_error;           /* after a CUDA status: the runtime's error code of the last
+                                     failing call made by this thread, and */
+    int32_t cuda_line;            /* the library source line of that call (diagnosis) */
     int64_t rounds_columns;       /* columns processed by refactorization rounds since the
                                      last basker_info call */
 } basker_info_t;

@@ -54,7 +54,8 @@ class Info(ctypes.Structure):
                 ("last_rounds", ctypes.c_int32), ("ir_iterations", ctypes.c_int32),
                 ("ir_fallbacks", ctypes.c_int32), ("precision_used", ctypes.c_int32),
                 ("reserved", ctypes.c_int32 * 2), ("ir_eta", ctypes.c_double), ("growth", ctypes.c_double),
-                ("kernel_calls", ctypes.c_int32 * 10), ("reserved2", ctypes.c_int32 * 2),
+                ("kernel_calls", ctypes.c_int32 * 10), ("cuda_error", ctypes.c_int32),
+                ("cuda_line", ctypes.c_int32),
                 ("rounds_columns", ctypes.c_int64)]
 
 KERNEL_KINDS = ["gather", "static_refactor", "dag_levels", "gp_in_node", "gp_descendant", "solve",
@@ -181,6 +182,8 @@ class Handle:
             err = BaskerError(s, where, col)
             if inf["internal_site"]:
                 err.args = (err.args[0] + f" [internal check {inf['internal_site']} at column {inf['internal_col']}]",)
+            if s == 8 and inf["cuda_error"]:
+                err.args = (err.args[0] + f" [cuda error {inf['cuda_error']} at api.cu:{inf['cuda_line']}]",)
             raise err
 
     def factor(self, values, stream=None) -> None:
@@ -241,7 +244,7 @@ class Handle:
         s = self.lib.basker_info(self.h, ctypes.byref(inf))
         if s != 0:
             raise BaskerError(s, "basker_info")
-        out = {k: getattr(inf, k) for k, _ in Info._fields_ if k not in ("reserved", "reserved2", "kernel_ms",
+        out = {k: getattr(inf, k) for k, _ in Info._fields_ if k not in ("reserved", "kernel_ms",
                                                                           "kernel_calls")}
         out["kernel_calls"] = {KERNEL_KINDS[i]: inf.kernel_calls[i] for i in range(len(KERNEL_KINDS))}
         out["kernel_ms"] = {KERNEL_KINDS[i]: inf.kernel_ms[i] for i in range(len(KERNEL_KINDS))}

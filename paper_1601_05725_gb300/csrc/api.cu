@@ -150,10 +150,15 @@ int upload(basker_t h, T **p, const std::vector<T> &v)
         int s_ = (x);               \
         if (s_ != BASKER_OK) return s_; \
     } while (0)
+// the last failing runtime call of this thread: its error code and source line
+thread_local int g_cuda_err = 0, g_cuda_line = 0;
 #define CU(x)                                  \
     do {                                       \
-        if ((x) != cudaSuccess) {              \
+        const cudaError_t e_ = (x);            \
+        if (e_ != cudaSuccess) {               \
             cudaGetLastError();                \
+            g_cuda_err = (int)e_;              \
+            g_cuda_line = __LINE__;            \
             return BASKER_ERR_CUDA;            \
         }                                      \
     } while (0)
@@ -425,12 +430,14 @@ int launch_full_gp(basker_t h, cudaStream_t s, int pref_mode)
             CU(cudaMemsetAsync(h->d.counter + 3, 0, sizeof(int32_t), s));
             tbeg(h, KT_DESC, s, 1);
             bk_launch_gp_desc(h->d, h->lv_cols[l], h->lv_ncols[l], h->d.counter + 3, s);
+            CU(cudaGetLastError());
             tend(h, s);
             h->launches++;
         }
         if (h->lv_ntasks[l] > 0) {
             tbeg(h, KT_GP, s, 1);
             bk_launch_gp_tasks(h->d, h->lv_tasks[l], nullptr, h->lv_ntasks[l], h->lv_smem[l], tau, pref_mode, s);
+            CU(cudaGetLastError());
             tend(h, s);
             h->launches++;
         }
@@ -500,6 +507,7 @@ int launch_redo(basker_t h, cudaStream_t s)
             tbeg(h, KT_SPEC, s, 1);
             bk_launch_dd(h->d, h->rd_cols, (int32_t)cols.size(), h->d.counter + 3, tau, h->epoch,
                          h->opt.wait_budget_cycles, h->refno, s);
+            CU(cudaGetLastError());
             tend(h, s);
             h->launches++;
             h->info.last_rounds++;
@@ -531,6 +539,7 @@ int compute_schedule(basker_t h, cudaStream_t s)
     h->epoch++;
     tbeg(h, KT_LEVELS, s, 4);
     bk_launch_levels(h->d, h->epoch, h->opt.wait_budget_cycles, bk_static_blocks(), s);
+    CU(cudaGetLastError());
     tend(h, s);
     h->launches += 4;
     CU(cudaGetLastError());
@@ -546,6 +555,7 @@ int static_pass(basker_t h, cudaStream_t s)
     h->epoch++;
     tbeg(h, KT_STATIC, s, 1);
     bk_launch_static(h->d, h->pl.n, h->opt.tau, h->epoch, h->opt.wait_budget_cycles, bk_static_blocks(), s);
+    CU(cudaGetLastError());
     tend(h, s);
     h->launches++;
     CU(cudaGetLastError());
@@ -560,7 +570,9 @@ int finish_factorization(basker_t h, cudaStream_t s)
     if (!h->schedule_valid) TRY(compute_schedule(h, s));
     tbeg(h, KT_ROWS, s, 14);
     bk_launch_rows(h->d, h->sd.r, s);
+    CU(cudaGetLastError());
     bk_launch_leaf_order(h->d, h->sd, s);
+    CU(cudaGetLastError());
     tend(h, s);
     CU(cudaGetLastError());
     return BASKER_OK;
@@ -572,6 +584,7 @@ int factor_impl(basker_t h, const double *values, cudaStream_t s, bool refactor)
     TRY(reset_status(h, s));
     tbeg(h, KT_GATHER, s, 1);
     bk_launch_gather(h->d, values, h->pl.nnz, s);
+    CU(cudaGetLastError());
     tend(h, s);
     h->launches++;
     if (refactor) {
@@ -612,6 +625,7 @@ int factor_impl(basker_t h, const double *values, cudaStream_t s, bool refactor)
             TRY(reset_status(h, s));
             tbeg(h, KT_GATHER, s, 1);
             bk_launch_gather(h->d, values, h->pl.nnz, s);
+            CU(cudaGetLastError());
             tend(h, s);
         }
         TRY(launch_full_gp(h, s, 0));
@@ -979,6 +993,8 @@ int basker_info(basker_t h, basker_info_t *out)
     if (!h || !out) return BASKER_ERR_INVALID_ARG;
     cudaSetDevice(h->device);
     h->info.device_bytes = h->device_bytes;
+    h->info.cuda_error = g_cuda_err;
+    h->info.cuda_line = g_cuda_line;
     tflush(h);
     *out = h->info;
     for (double &v : h->info.kernel_ms) v = 0.0;

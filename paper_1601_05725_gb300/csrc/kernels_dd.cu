@@ -602,12 +602,12 @@ void bk_launch_dd(const bk_dev &d, const int32_t *cols, int32_t ncols, int32_t *
     const size_t smem = (size_t)4 * d.dd_words * sizeof(uint32_t);
     const int grid = (warps + 3) / 4;
     if (d.prec) {
-        if (smem > 48 * 1024)
+        if (smem > 0)      // static shared memory counts too: always raise the limit
             cudaFuncSetAttribute(bk_dd_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         bk_dd_kernel<float><<<grid, 128, smem, (cudaStream_t)stream>>>(d, cols, ncols, counter, tau, epoch, budget,
                                                                         refno);
     } else {
-        if (smem > 48 * 1024)
+        if (smem > 0)
             cudaFuncSetAttribute(bk_dd_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         bk_dd_kernel<double><<<grid, 128, smem, (cudaStream_t)stream>>>(d, cols, ncols, counter, tau, epoch, budget,
                                                                          refno);

@@ -222,7 +222,9 @@ def poisson_arrivals(rng: np.random.Generator, count: int, rate: float) -> np.nd
 def latency_summary(results: List[Result]) -> dict:
     lat = np.array([r.latency for r in results if r.error is None])
     span = max(r.finish for r in results) - min(r.arrival for r in results)
+    errs = sorted({r.error for r in results if r.error is not None})
     return {"requests": len(results), "errors": sum(r.error is not None for r in results),
+            "error_kinds": errs[:3],
             "p50_ms": float(np.percentile(lat, 50) * 1e3) if len(lat) else None,
             "p99_ms": float(np.percentile(lat, 99) * 1e3) if len(lat) else None,
             "throughput": len(lat) / span if span > 0 else None}

@@ -66,3 +66,23 @@ def test_config3_fp32_refined(c3):
     x = h.solve(_dev(b)).cpu().numpy()
     assert H.solve_backward_error(A, x, b) <= 1e-12
     assert h.info()["precision_used"] == 1
+
+
+def test_large_netlist_refactor_sequence_bitwise():
+    """An 81,219-row netlist block in 32 ND leaves: every refactorization that
+    repivots runs the rounds kernel with its largest shared-memory footprint."""
+    prob = I.netlist_problem(2001, n_small=0, m_netlist=81219, depth=5, name="netlist_81k")
+    o = oracle.OracleLU(prob)
+    assert o.factor() == "OK"
+    f = o.factors()
+    h = basker.Handle.from_problem(prob)
+    h.factor(_dev(prob.values))
+    _same(h, f)
+    for k in (1, 2, 4):
+        v = I.refactor_values(prob, k)
+        assert o.factor(v, pref=f.prow) == "OK"
+        f = o.factors()
+        h.refactor(_dev(v))
+        _same(h, f)
+        b = I.rhs_ones(prob, v)
+        np.testing.assert_array_equal(h.solve(_dev(b)).cpu().numpy(), o.solve(b))
