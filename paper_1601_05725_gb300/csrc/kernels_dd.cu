@@ -25,6 +25,7 @@
 
 #include <algorithm>
 #include <climits>
+#include <mutex>
 
 #include "basker_internal.h"
 #include "column_static.cuh"
@@ -601,15 +602,17 @@ void bk_launch_dd(const bk_dev &d, const int32_t *cols, int32_t ncols, int32_t *
     int warps = std::min<int>(ncols, d.wsd_warps);
     const size_t smem = (size_t)4 * d.dd_words * sizeof(uint32_t);
     const int grid = (warps + 3) / 4;
-    if (d.prec) {
-        if (smem > 0)      // static shared memory counts too: always raise the limit
-            cudaFuncSetAttribute(bk_dd_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // the limit is a property of the kernel shared by every handle and thread:
+    // raise it once to the largest footprint the plan allows (160 KB)
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaFuncSetAttribute(bk_dd_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+        cudaFuncSetAttribute(bk_dd_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    });
+    if (d.prec)
         bk_dd_kernel<float><<<grid, 128, smem, (cudaStream_t)stream>>>(d, cols, ncols, counter, tau, epoch, budget,
                                                                         refno);
-    } else {
-        if (smem > 0)
-            cudaFuncSetAttribute(bk_dd_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    else
         bk_dd_kernel<double><<<grid, 128, smem, (cudaStream_t)stream>>>(d, cols, ncols, counter, tau, epoch, budget,
                                                                          refno);
-    }
 }

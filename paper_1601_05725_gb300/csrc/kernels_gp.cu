@@ -25,6 +25,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 #include <climits>
 
 #include "basker_internal.h"
@@ -570,14 +571,13 @@ void bk_launch_gp_tasks(const bk_dev &d, const int32_t *task_ids, const int32_t 
                         int32_t ntasks, size_t smem, double tau, int pref_mode, void *stream)
 {
     if (ntasks <= 0) return;
-    static bool attr = false;
-    if (!attr) {
+    static std::once_flag once;
+    std::call_once(once, [] {
         cudaFuncSetAttribute(bk_gp_task_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)bk_gp_smem_limit());
         cudaFuncSetAttribute(bk_gp_task_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)bk_gp_smem_limit());
-        attr = true;
-    }
+    });
     if (d.prec)
         bk_gp_task_kernel<float><<<ntasks, 32, smem, (cudaStream_t)stream>>>(d, task_ids, task_c0, tau, pref_mode);
     else

@@ -543,15 +543,15 @@ __global__ void __launch_bounds__(128) bk_solve_kernel(bk_dev d, bk_solve_dev s,
 
 int solve_blocks()
 {
-    static int blocks = 0;
-    if (!blocks) {
+    // computed once, thread-safely (a function-local static)
+    static const int blocks = [] {
         int dev = 0, sms = 0, per = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, bk_solve_kernel<double>, 128,
                                                       4 * SEP_SMEM_ROWS * sizeof(double));
-        blocks = std::max(1, sms) * std::max(1, std::min(per, 8));
-    }
+        return std::max(1, sms) * std::max(1, std::min(per, 8));
+    }();
     return blocks;
 }
 

@@ -152,14 +152,14 @@ __global__ void bk_level_scatter(const int32_t *__restrict__ level, int32_t n, i
 
 int bk_static_blocks()
 {
-    static int blocks = 0;
-    if (!blocks) {
+    // computed once, thread-safely (a function-local static)
+    static const int blocks = [] {
         int dev = 0, sms = 0, per = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, bk_static_kernel<double>, 128, 0);
-        blocks = std::max(1, sms) * std::max(1, std::min(per, 4));
-    }
+        return std::max(1, sms) * std::max(1, std::min(per, 4));
+    }();
     return blocks;
 }
 
