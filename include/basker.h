@@ -109,7 +109,8 @@ typedef struct {
     int32_t ir_iterations;        /* precision 1: refinement steps of the last solve */
     int32_t ir_fallbacks;         /* precision 1: factorizations redone in FP64 so far */
     int32_t precision_used;       /* arithmetic of the factors the last solve used: 0 FP64, 1 FP32 */
-    int32_t reserved[2];
+    int32_t tuned_static_blocks;  /* basker_autotune's choices (0: defaults): persistent blocks */
+    int32_t tuned_solve_blocks;   /* of the stored-pattern pass and of the solve */
     double ir_eta;                /* precision 1: backward error after the last solve's refinement */
     double growth;                /* precision 1: pivot growth of the last FP32 factorization */
     int32_t kernel_calls[10];     /* launches per kernel kind (as kernel_ms) since the last
@@ -176,6 +177,17 @@ int basker_solve(basker_t h, int32_t nrhs, const double *b_dev, int32_t ldb,
  * A's CSC order; b_host/x_host: n x nrhs column-major (ld = n). */
 int basker_refactor_solve_host(basker_t h, const double *values_host, int32_t nrhs,
                                const double *b_host, double *x_host, void *stream);
+
+/* Launch-size tuning (no counterpart in the paper).  The stored-pattern pass,
+ * the refactorization rounds and the solve are persistent kernels whose warps
+ * claim work; how many blocks they launch changes their speed, not their
+ * results.  This runs refactor(values_dev) + solve(b_dev) (one right-hand side,
+ * device pointers, n doubles) a few times for each candidate launch size, one
+ * kernel at a time, and keeps the fastest on the handle; basker_info reports the
+ * choices.  The handle's factors and pivots are those of values_dev afterwards.
+ * Blocks the stream.  Errors: those of basker_refactor / basker_solve
+ * (the handle then keeps the default sizes). */
+int basker_autotune(basker_t h, const double *values_dev, const double *b_dev, void *stream);
 
 /* Size, in doubles, of the fixed device array basker_solve_noalloc works in
  * (8 MiB on every GPU that loads the library, held until the process exits). */

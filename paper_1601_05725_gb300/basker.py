@@ -53,7 +53,8 @@ class Info(ctypes.Structure):
                 ("internal_site", ctypes.c_int32), ("internal_col", ctypes.c_int32),
                 ("last_rounds", ctypes.c_int32), ("ir_iterations", ctypes.c_int32),
                 ("ir_fallbacks", ctypes.c_int32), ("precision_used", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2), ("ir_eta", ctypes.c_double), ("growth", ctypes.c_double),
+                ("tuned_static_blocks", ctypes.c_int32), ("tuned_solve_blocks", ctypes.c_int32),
+                ("ir_eta", ctypes.c_double), ("growth", ctypes.c_double),
                 ("kernel_calls", ctypes.c_int32 * 10), ("cuda_error", ctypes.c_int32),
                 ("cuda_line", ctypes.c_int32),
                 ("rounds_columns", ctypes.c_int64)]
@@ -64,7 +65,7 @@ KERNEL_KINDS = ["gather", "static_refactor", "dag_levels", "gp_in_node", "gp_des
 
 EXPORTED = ["basker_default_options", "basker_symbolic", "basker_factor", "basker_refactor",
             "basker_solve", "basker_refactor_solve_host", "basker_info", "basker_export",
-            "basker_free", "basker_strerror", "basker_solve_noalloc"]
+            "basker_free", "basker_strerror", "basker_solve_noalloc", "basker_autotune"]
 
 
 def library_path() -> str:
@@ -92,6 +93,8 @@ def load(path: Optional[str] = None):
             getattr(L, f).restype = ctypes.c_int
         L.basker_solve.argtypes = [vp, i32, vp, i32, vp, i32, vp]
         L.basker_solve.restype = ctypes.c_int
+        L.basker_autotune.argtypes = [vp, vp, vp, vp]
+        L.basker_autotune.restype = ctypes.c_int
         L.basker_solve_noalloc.argtypes = [vp, i32, vp, i32, vp, i32, vp]
         L.basker_solve_noalloc.restype = ctypes.c_int
         L.basker_refactor_solve_host.argtypes = [vp, vp, i32, vp, vp, vp]
@@ -228,6 +231,14 @@ class Handle:
         s = self.lib.basker_solve_noalloc(self.h, nrhs, _dev_ptr(b), ldb, _dev_ptr(x), ldx, _stream_ptr(None))
         self._check(s, "basker_solve_noalloc")
         return x
+
+    def autotune(self, values, b, stream=None) -> dict:
+        """basker_autotune: values and b CUDA float64 tensors (nnz(A), n).  Returns the
+        chosen launch sizes."""
+        self._check(self.lib.basker_autotune(self.h, _dev_ptr(values), _dev_ptr(b), _stream_ptr(stream)),
+                    "basker_autotune")
+        inf = self.info()
+        return {"static_blocks": inf["tuned_static_blocks"], "solve_blocks": inf["tuned_solve_blocks"]}
 
     def refactor_solve_host(self, values: np.ndarray, b: np.ndarray, stream=None) -> np.ndarray:
         """Host arrays in, host solution out (copies inside the call)."""

@@ -57,6 +57,8 @@ struct basker_s {
     int32_t ir_cap = 0;
     double bnorm = 0.0;
     bool use64 = false, fp32_valid = false;
+    // launch sizes chosen by basker_autotune (0: the occupancy defaults)
+    int tune_static = 0, tune_solve = 0, tune_dd = 0;
     basker_t twin = nullptr;
     // the symbolic inputs, kept to build the twin
     std::vector<int32_t> in_colptr, in_rowind, in_P, in_Q, in_bptr, in_ndptr;
@@ -162,6 +164,9 @@ thread_local int g_cuda_err = 0, g_cuda_line = 0;
             return BASKER_ERR_CUDA;            \
         }                                      \
     } while (0)
+
+// Persistent blocks of the stored-pattern and column-levels kernels.
+int static_blocks(basker_t h) { return h->tune_static > 0 ? h->tune_static : bk_static_blocks(); }
 
 // L/U arrays sized by the current layout (symbolic pattern, slack, growth), each
 // followed by its spill pool; per-column region starts and ends.
@@ -506,7 +511,7 @@ int launch_redo(basker_t h, cudaStream_t s)
             h->epoch++;
             tbeg(h, KT_SPEC, s, 1);
             bk_launch_dd(h->d, h->rd_cols, (int32_t)cols.size(), h->d.counter + 3, tau, h->epoch,
-                         h->opt.wait_budget_cycles, h->refno, s);
+                         h->opt.wait_budget_cycles, h->refno, s, h->tune_dd);
             CU(cudaGetLastError());
             tend(h, s);
             h->launches++;
@@ -538,7 +543,7 @@ int compute_schedule(basker_t h, cudaStream_t s)
 {
     h->epoch++;
     tbeg(h, KT_LEVELS, s, 4);
-    bk_launch_levels(h->d, h->epoch, h->opt.wait_budget_cycles, bk_static_blocks(), s);
+    bk_launch_levels(h->d, h->epoch, h->opt.wait_budget_cycles, static_blocks(h), s);
     CU(cudaGetLastError());
     tend(h, s);
     h->launches += 4;
@@ -554,7 +559,7 @@ int static_pass(basker_t h, cudaStream_t s)
     CU(cudaMemsetAsync(h->d.counter, 0, sizeof(int32_t), s));
     h->epoch++;
     tbeg(h, KT_STATIC, s, 1);
-    bk_launch_static(h->d, h->pl.n, h->opt.tau, h->epoch, h->opt.wait_budget_cycles, bk_static_blocks(), s);
+    bk_launch_static(h->d, h->pl.n, h->opt.tau, h->epoch, h->opt.wait_budget_cycles, static_blocks(h), s);
     CU(cudaGetLastError());
     tend(h, s);
     h->launches++;
@@ -757,7 +762,7 @@ int solve_refined(basker_t h, int32_t nrhs, const double *b, int32_t ldb, double
         h->solve_epoch++;
         tbeg(h, KT_SOLVE, s, 1);
         bk_launch_solve(h->d, h->sd, nrhs, h->ir_r, n, h->ir_dz, n, h->solve_epoch, h->opt.wait_budget_cycles, s,
-                        false);
+                        false, h->tune_solve);
         tend(h, s);
         tbeg(h, KT_REFINE, s, 2);
         bk_launch_ir_step(h->d, h->rf, nrhs, h->ir_c, h->ir_z, h->ir_dz, h->ir_r, zmax, rmax, s);
@@ -817,7 +822,8 @@ int bk_solve_on_scratch(basker_t h, int32_t nrhs, const double *b_dev, int32_t l
     CU(cudaMemsetAsync(h->d.counter + 2, 0, sizeof(int32_t), s));
     h->solve_epoch++;
     h->info.kernel_launches++;
-    bk_launch_solve(h->d, sd, nrhs, b_dev, ldb, x_dev, ldx, h->solve_epoch, h->opt.wait_budget_cycles, s);
+    bk_launch_solve(h->d, sd, nrhs, b_dev, ldb, x_dev, ldx, h->solve_epoch, h->opt.wait_budget_cycles, s, true,
+                    h->tune_solve);
     CU(cudaGetLastError());
     return BASKER_OK;
 }
@@ -954,7 +960,8 @@ int basker_solve(basker_t h, int32_t nrhs, const double *b_dev, int32_t ldb, dou
     h->solve_epoch++;
     h->info.precision_used = 0;
     tbeg(h, KT_SOLVE, s, 1);
-    bk_launch_solve(h->d, h->sd, nrhs, b_dev, ldb, x_dev, ldx, h->solve_epoch, h->opt.wait_budget_cycles, s);
+    bk_launch_solve(h->d, h->sd, nrhs, b_dev, ldb, x_dev, ldx, h->solve_epoch, h->opt.wait_budget_cycles, s, true,
+                    h->tune_solve);
     tend(h, s);
     CU(cudaGetLastError());
     return BASKER_OK;
@@ -1090,6 +1097,66 @@ int basker_export(basker_t h, int32_t *prow, int64_t *Lp, int32_t *Li, double *L
         Up[c + 1] = q;
     }
     return BASKER_OK;
+}
+
+int basker_autotune(basker_t h, const double *values_dev, const double *b_dev, void *stream)
+{
+    if (!h || (!values_dev && h->pl.nnz > 0) || (!b_dev && h->pl.n > 0)) return BASKER_ERR_INVALID_ARG;
+    if (!h->factored) return BASKER_ERR_NOT_FACTORED;
+    if (h->pl.n == 0) return BASKER_OK;
+    cudaSetDevice(h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int32_t n = h->pl.n;
+    double *x = nullptr;
+    TRY(dalloc(h, &x, (size_t)n));
+    int sms = 0;
+    CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+    sms = std::max(sms, 1);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    int st = BASKER_OK;
+    // one trial: the best of two refactor + solve runs
+    auto trial = [&]() -> float {
+        float best = 1e30f;
+        for (int rep = 0; rep < 2 && st == BASKER_OK; rep++) {
+            cudaEventRecord(e0, s);
+            st = basker_refactor(h, values_dev, s);
+            if (st == BASKER_OK) st = basker_solve(h, 1, b_dev, n, x, n, s);
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) st = BASKER_ERR_CUDA;
+            float ms = 0.f;
+            if (st == BASKER_OK && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) best = std::min(best, ms);
+        }
+        return best;
+    };
+    // coordinate search: the stored-pattern pass's persistent blocks per SM (up to
+    // the allocated per-warp slices), then the solve's, then the rounds' warps
+    auto search = [&](int &knob, const std::vector<int> &cands) {
+        float bt = 1e30f;
+        int bk = 0;
+        for (int v : cands) {
+            knob = v;
+            const float t = trial();
+            if (st != BASKER_OK) return;
+            if (t < bt) { bt = t; bk = v; }
+        }
+        knob = bk;
+    };
+    std::vector<int> cs, cv, cd;
+    for (int per = 1; per * sms <= bk_static_blocks(); per++) cs.push_back(per * sms);
+    for (int per = 2; per * sms <= bk_solve_blocks(); per += 2) cv.push_back(per * sms);
+    for (int w = h->pl.wsd_warps; w >= 152 && cd.size() < 3; w /= 2) cd.push_back(w);
+    search(h->tune_static, cs);
+    if (st == BASKER_OK) search(h->tune_solve, cv);
+    if (st == BASKER_OK) search(h->tune_dd, cd);
+    if (st != BASKER_OK) h->tune_static = h->tune_solve = h->tune_dd = 0;
+    h->info.tuned_static_blocks = h->tune_static;
+    h->info.tuned_solve_blocks = h->tune_solve;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    dfree(h, x);
+    return st;
 }
 
 void basker_free(basker_t h)

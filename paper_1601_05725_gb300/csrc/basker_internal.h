@@ -156,7 +156,7 @@ void bk_launch_gp_tasks(const bk_dev &d, const int32_t *task_ids, const int32_t 
 void bk_launch_gp_desc(const bk_dev &d, const int32_t *cols, int32_t ncols, int32_t *counter,
                        void *stream);
 void bk_launch_dd(const bk_dev &d, const int32_t *cols, int32_t ncols, int32_t *counter, double tau,
-                  int32_t epoch, long long budget, int32_t refno, void *stream);
+                  int32_t epoch, long long budget, int32_t refno, void *stream, int max_warps = 0);
 void bk_launch_reset_pivots(const bk_dev &d, const int32_t *task_ids, const int32_t *task_c0,
                             int32_t ntasks, void *stream);
 void bk_launch_static(const bk_dev &d, int32_t ncols, double tau, int32_t epoch,

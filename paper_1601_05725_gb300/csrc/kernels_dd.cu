@@ -596,10 +596,10 @@ __global__ void __launch_bounds__(128) bk_dd_kernel(bk_dev d, const int32_t *__r
 }  // namespace
 
 void bk_launch_dd(const bk_dev &d, const int32_t *cols, int32_t ncols, int32_t *counter, double tau,
-                  int32_t epoch, long long budget, int32_t refno, void *stream)
+                  int32_t epoch, long long budget, int32_t refno, void *stream, int max_warps)
 {
     if (ncols <= 0) return;
-    int warps = std::min<int>(ncols, d.wsd_warps);
+    int warps = std::min<int>(ncols, max_warps > 0 ? std::min<int>(max_warps, d.wsd_warps) : d.wsd_warps);
     const size_t smem = (size_t)4 * d.dd_words * sizeof(uint32_t);
     const int grid = (warps + 3) / 4;
     // the limit is a property of the kernel shared by every handle and thread:

@@ -541,7 +541,9 @@ __global__ void __launch_bounds__(128) bk_solve_kernel(bk_dev d, bk_solve_dev s,
     }
 }
 
-int solve_blocks()
+}  // namespace
+
+int bk_solve_blocks()
 {
     // computed once, thread-safely (a function-local static)
     static const int blocks = [] {
@@ -554,6 +556,8 @@ int solve_blocks()
     }();
     return blocks;
 }
+
+namespace {
 
 void launch_scan(const int32_t *cnt, int32_t m, int64_t *part, int64_t *out, cudaStream_t st)
 {
@@ -605,11 +609,12 @@ void bk_launch_leaf_order(const bk_dev &d, const bk_solve_dev &s, void *stream)
 }
 
 void bk_launch_solve(const bk_dev &d, const bk_solve_dev &s, int32_t nrhs, const double *b, int32_t ldb,
-                     double *x, int32_t ldx, int32_t epoch, long long budget, void *stream, bool permute)
+                     double *x, int32_t ldx, int32_t epoch, long long budget, void *stream, bool permute,
+                     int max_ctas)
 {
     const int32_t *Pin = permute ? d.P : nullptr, *Qout = permute ? d.Q : nullptr;
     if (s.nitems <= 0) return;
-    const int ctas = std::min<int>((s.nitems + 3) / 4, solve_blocks());
+    const int ctas = std::min<int>((s.nitems + 3) / 4, max_ctas > 0 ? max_ctas : bk_solve_blocks());
     const size_t smem = (size_t)4 * SEP_SMEM_ROWS * sizeof(double);
     if (d.prec)
         bk_solve_kernel<float><<<ctas, 128, smem, (cudaStream_t)stream>>>(d, s, nrhs, b, ldb, x, ldx, epoch, budget, Pin,

@@ -54,4 +54,6 @@ void bk_launch_leaf_order(const bk_dev &d, const bk_solve_dev &s, void *stream);
 // permute: b is indexed by A's rows and x by A's columns (b(P), x(Q)); otherwise
 // both are in B's row / column space (the refinement's corrections).
 void bk_launch_solve(const bk_dev &d, const bk_solve_dev &s, int32_t nrhs, const double *b, int32_t ldb,
-                     double *x, int32_t ldx, int32_t epoch, long long budget, void *stream, bool permute = true);
+                     double *x, int32_t ldx, int32_t epoch, long long budget, void *stream, bool permute = true,
+                     int max_ctas = 0);
+int bk_solve_blocks();   // persistent blocks of the solve kernel at full occupancy (4 warps each)
