@@ -43,6 +43,8 @@ def _args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-sample", type=int, default=4, help="oracle steps in the cpu_baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="keep the default launch sizes instead of basker_autotune's (untimed, before the warm-up)")
     ap.add_argument("--workload", choices=["powergrid", "batched", "serving"], default="powergrid",
                     help="powergrid: the metric's refactor+solve sequence; batched: factor+solve of "
                          "8,192 independent blocks (a secondary measurement)")
@@ -272,6 +274,7 @@ def run_ours(args):
         # refined forms aim below the 1e-12 bar (the host recomputes eta from A, x, b)
         h = basker.Handle.from_problem(prob, timing=True, precision=prec, ir_tol=2.5e-13)
         h.factor(torch.as_tensor(prob.values, device=dev))
+        tuned = h.autotune(dvals[0], drhs[0]) if args.autotune else None
         step_ms, X, info0, info1, span = _measure(h, dvals, drhs, K, W, dev, flush, dist, world)
         total_s = sum(step_ms) / 1e3
         if world > 1:
@@ -288,6 +291,7 @@ def run_ours(args):
             "kernel_ms_per_step": {k: v / K for k, v in info1["kernel_ms"].items() if v > 0},
             "roofline": _roofline(prob, info1, K, nnz_lu, 4.0 if prec == 1 else 8.0, hbm),
             "nnz_lu": int(nnz_lu), "flops_per_refactor": info1["flops"], "span": span,
+            "autotuned": tuned,
         }
         if prec >= 1:
             forms[name]["ir_fallbacks"] = info1["ir_fallbacks"]
