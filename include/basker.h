@@ -73,7 +73,14 @@ typedef struct {
     double ir_tol;                /* precision 1, 2: backward error to reach; default 1e-13 */
     double growth_limit;          /* precision 1: max over BTF blocks of max|U_d| / max|B_d|
                                      above which the FP32 factors are not used; default 1e4 */
-    int reserved[4];
+    int refactor_switch;          /* a refactorization whose stored-pattern pass rejected
+                                     pivots continues with rounds of column recomputation;
+                                     0 (default): when the rounds have taken as long as the
+                                     handle's last complete factorization, the rest is one
+                                     complete Algorithm 1 pass with the previous pivots
+                                     preferred; 1: rounds only; 2: the complete pass at once.
+                                     The factors are the same in every mode. */
+    int reserved[3];
 } basker_options;
 
 typedef struct {
@@ -120,6 +127,9 @@ typedef struct {
     int32_t cuda_line;            /* the library source line of that call (diagnosis) */
     int64_t rounds_columns;       /* columns processed by refactorization rounds since the
                                      last basker_info call */
+    int32_t full_refactors;       /* refactorizations finished by a complete Algorithm 1
+                                     pass instead of rounds (options.refactor_switch) */
+    int32_t pad0;
 } basker_info_t;
 
 /* Defaults listed in basker_options. */

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <climits>
 #include <cmath>
 #include <cstdint>
@@ -35,6 +36,7 @@ struct basker_s {
     int32_t *h_task_fail = nullptr;  // pinned
     int32_t epoch = 0, solve_epoch = 0, refno = 0;
     bool factored = false, ws_dirty = false, schedule_valid = true, order_is_symbolic = true;
+    double gp_wall_ms = 0.0;     // wall time of the last complete Algorithm 1 pass (host clock)
     int32_t nrhs_cap = 0;
     double *d_vals = nullptr, *d_b = nullptr, *d_x = nullptr;
     int32_t stage_nrhs = 0;
@@ -365,10 +367,17 @@ int setup_device(basker_t h)
     TRY(dalloc(h, &s.r.Ud, (size_t)n));
     TRY(dalloc(h, &s.r.cnt, (size_t)2 * ((size_t)n + 1)));
     TRY(dalloc(h, &s.r.part, (size_t)n / 1024 + 2));
+    s.r.swords = (int64_t)n / 32 + 2;
+    TRY(dalloc(h, &s.r.longs, (size_t)n + 1));
+    TRY(dalloc(h, &s.r.sbits, (size_t)(s.r.swords * BK_LONG_CTAS)));
+    TRY(dalloc(h, &s.r.spre, (size_t)(s.r.swords * BK_LONG_CTAS)));
     TRY(upload_symbolic_pattern(h));
     h->schedule_valid = true;
     return BASKER_OK;
 }
+
+// launch_redo's answer when the rest of a refactorization is cheaper as one complete pass
+constexpr int BK_SWITCH_TO_FULL = -2;
 
 int reset_status(basker_t h, cudaStream_t s)
 {
@@ -476,6 +485,7 @@ int launch_redo(basker_t h, cudaStream_t s)
     std::vector<int32_t> start(nt, 0), flags(nt, 0);
     int32_t redone = 0;
     h->info.last_rounds = 0;
+    const auto t0 = std::chrono::steady_clock::now();
     auto mark_ancestors = [&](size_t t) {
         const bk_task &T = pl.tasks[t];
         for (int32_t a = 0; a < T.nanc; a++) desc_changed[(size_t)pl.col_task[(size_t)T.anc_lo[a]]] = 1;
@@ -532,6 +542,13 @@ int launch_redo(basker_t h, cudaStream_t s)
                 }
             }
             active.swap(next);
+            // the rounds have cost as much as a complete pass would: finish with one
+            if (!active.empty() && h->opt.refactor_switch == 0 && h->gp_wall_ms > 0.0 &&
+                std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count() >
+                    h->gp_wall_ms) {
+                h->info.last_repivot_columns = redone;
+                return BK_SWITCH_TO_FULL;
+            }
         }
     }
     h->info.last_repivot_columns = redone;
@@ -605,9 +622,21 @@ int factor_impl(basker_t h, const double *values, cudaStream_t s, bool refactor)
         h->info.last_repivot_columns = 0;
         h->info.last_rounds = 0;
         if (h->h_status->static_fail) {
-            st = launch_redo(h, s);
+            st = h->opt.refactor_switch == 2 ? BK_SWITCH_TO_FULL : launch_redo(h, s);
             if (st == BASKER_OK) st = read_status(h, s);
             h->schedule_valid = false;
+            if (st == BK_SWITCH_TO_FULL) {
+                // Algorithm 1 on every column with the previous pivots preferred: the
+                // refactorization's definition, computed directly
+                h->info.full_refactors++;
+                h->ws_dirty = true;
+                TRY(reset_status(h, s));
+                const auto t0 = std::chrono::steady_clock::now();
+                TRY(launch_full_gp(h, s, 1));
+                st = read_status(h, s);
+                if (st == BASKER_OK)
+                    h->gp_wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+            }
             if (st == -1) {
                 // the new pivots need more room: grow and run Algorithm 1 everywhere
                 for (int tries = 0; st == -1 && tries < 16; tries++) {
@@ -633,8 +662,11 @@ int factor_impl(basker_t h, const double *values, cudaStream_t s, bool refactor)
             CU(cudaGetLastError());
             tend(h, s);
         }
+        const auto t0 = std::chrono::steady_clock::now();
         TRY(launch_full_gp(h, s, 0));
         st = read_status(h, s);
+        if (st == BASKER_OK)
+            h->gp_wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
         if (st != -1) break;
     }
     if (st != BASKER_OK) { h->factored = false; return st == -1 ? BASKER_ERR_OOM : st; }
@@ -874,6 +906,7 @@ int basker_symbolic(int32_t n, const int32_t *colptr, const int32_t *rowind, con
     if (opt) h->opt = *opt;
     if (!(h->opt.tau > 0.0 && h->opt.tau <= 1.0) || h->opt.slack < 0.0 || h->opt.wait_budget_cycles <= 0 ||
         h->opt.factor_mode != 0 || h->opt.precision < 0 || h->opt.precision > 2 ||
+        h->opt.refactor_switch < 0 || h->opt.refactor_switch > 2 ||
         (h->opt.precision >= 1 && (h->opt.ir_max_iter < 1 || !(h->opt.ir_tol > 0.0) || !(h->opt.growth_limit > 0.0)))) {
         delete h;
         return BASKER_ERR_INVALID_ARG;

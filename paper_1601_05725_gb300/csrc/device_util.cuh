@@ -137,6 +137,14 @@ __device__ __forceinline__ int64_t pool_alloc(unsigned long long *next, int64_t 
     return (int64_t)(b + cnt) <= end ? (int64_t)b : -1;
 }
 
+// Room for a U column that outgrew its region after nu entries: twice what it
+// holds so far (a column may move again; the copies add up to at most twice its
+// final size), never more than its largest possible size.
+__device__ __forceinline__ int64_t grown_ucap(int nu, int64_t bound)
+{
+    return min((long long)bound, (long long)(2 * ((int64_t)nu + 2) + 16));
+}
+
 // Column c of task T ran out of room (what: 1 = L, 2 = U): flag it for the
 // host, and stop the task and every ND ancestor (their input is incomplete).
 __device__ __forceinline__ void report_overflow(const bk_dev &d, const bk_task &T, int tid, int c, int what)

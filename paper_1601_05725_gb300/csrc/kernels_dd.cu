@@ -358,7 +358,7 @@ __global__ void __launch_bounds__(128) bk_dd_kernel(bk_dev d, const int32_t *__r
             if (lane == 0) x[sp] = 0.0;
             if (!isfinite(m)) bad = true;
             if (!overflow && ub + nu + 2 > ue) {
-                const int64_t cap = (int64_t)(c - T.sp_lo) + 1;
+                const int64_t cap = grown_ucap(nu, (int64_t)(c - T.sp_lo) + 1);
                 int64_t nb = 0;
                 if (lane == 0) nb = pool_alloc(d.pool + 1, d.upool_end, cap);
                 nb = __shfl_sync(BK_FULL, nb, 0);

@@ -227,8 +227,8 @@ __global__ void __launch_bounds__(32) bk_gp_task_kernel(bk_dev d, const int32_t 
             }
             if (!isfinite(m)) bad = true;
             if (ub + nu + 2 > ue) {
-                // move the column to a pool region of its largest possible size
-                const int64_t cap = (int64_t)(c - T.sp_lo) + 1;
+                // move the column to a larger pool region (twice its entries so far)
+                const int64_t cap = grown_ucap(nu, (int64_t)(c - T.sp_lo) + 1);
                 int64_t nb = 0;
                 if (lane == 0) nb = pool_alloc(d.pool + 1, d.upool_end, cap);
                 nb = __shfl_sync(BK_FULL, nb, 0);
@@ -467,7 +467,7 @@ __global__ void __launch_bounds__(128) bk_gp_desc_kernel(bk_dev d, const int32_t
             }
             if (!isfinite(m)) bad = true;
             if (!overflow && ub + nu + 2 > ue) {
-                const int64_t cap = (int64_t)(c - T.sp_lo) + 1;
+                const int64_t cap = grown_ucap(nu, (int64_t)(c - T.sp_lo) + 1);
                 int64_t nb = 0;
                 if (lane == 0) nb = pool_alloc(d.pool + 1, d.upool_end, cap);
                 nb = __shfl_sync(BK_FULL, nb, 0);

@@ -163,6 +163,7 @@ __global__ void bk_rows_sort(int32_t n, const int64_t *rp, const int32_t *tk, co
     for (int i = warp; i < n; i += nwarps) {
         const int64_t p0 = rp[i];
         const int len = (int)(rp[i + 1] - p0);
+        if (len > BK_LONG_ROW) continue;          // bk_rows_sort_long
         for (int e0 = 0; e0 < len; e0 += 32) {
             const bool mine = e0 + lane < len;
             const int myk = mine ? tk[p0 + e0 + lane] : sentinel;
@@ -181,6 +182,80 @@ __global__ void bk_rows_sort(int32_t n, const int64_t *rp, const int32_t *tk, co
                 ox[p0 + rank] = myx;
             }
         }
+    }
+}
+
+__global__ void bk_rows_long_list(int32_t n, const int64_t *rp, int32_t *longs)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        if (rp[i + 1] - rp[i] > BK_LONG_ROW) longs[1 + atomicAdd(longs, 1)] = i;
+}
+
+// Long rows, one block a row: the row's columns (distinct) set bits of a bitmap
+// over [cmin, cmax]; an entry's rank is the number of set bits before its own,
+// a prefix sum of the words' popcounts plus the popcount within its word.
+// Linear in the row's length and its column range.
+template <typename V>
+__global__ void __launch_bounds__(1024) bk_rows_sort_long(const int64_t *rp, const int32_t *tk, const V *tx,
+                                                          int32_t *ok, V *ox, int desc, const int32_t *longs,
+                                                          uint32_t *sbits, int32_t *spre, int64_t swords)
+{
+    __shared__ int64_t wt[33];
+    __shared__ int red[2][32];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    uint32_t *bm = sbits + (int64_t)blockIdx.x * swords;
+    int32_t *pre = spre + (int64_t)blockIdx.x * swords;
+    const int nlong = longs[0];
+    for (int q = blockIdx.x; q < nlong; q += gridDim.x) {
+        const int i = longs[1 + q];
+        const int64_t p0 = rp[i];
+        const int len = (int)(rp[i + 1] - p0);
+        int lo = INT_MAX, hi = -1;
+        for (int e = tid; e < len; e += blockDim.x) {
+            const int c = tk[p0 + e];
+            lo = min(lo, c);
+            hi = max(hi, c);
+        }
+        lo = warp_min(lo);
+        hi = warp_max_i(hi);
+        if (lane == 0) { red[0][wid] = lo; red[1][wid] = hi; }
+        __syncthreads();
+        if (wid == 0) {
+            lo = lane < (int)(blockDim.x >> 5) ? red[0][lane] : INT_MAX;
+            hi = lane < (int)(blockDim.x >> 5) ? red[1][lane] : -1;
+            lo = warp_min(lo);
+            hi = warp_max_i(hi);
+            if (lane == 0) { red[0][0] = lo; red[1][0] = hi; }
+        }
+        __syncthreads();
+        const int cmin = red[0][0];
+        const int W = ((red[1][0] - cmin) >> 5) + 1;
+        for (int w = tid; w < W; w += blockDim.x) bm[w] = 0u;
+        __syncthreads();
+        for (int e = tid; e < len; e += blockDim.x) {
+            const int off = tk[p0 + e] - cmin;
+            atomicOr(bm + (off >> 5), 1u << (off & 31));
+        }
+        __syncthreads();
+        int64_t carry = 0;
+        for (int w0 = 0; w0 < W; w0 += blockDim.x) {
+            const int w = w0 + tid;
+            const int64_t v = w < W ? __popc(bm[w]) : 0;
+            int64_t total;
+            const int64_t ex = block_exscan(v, wt, total);
+            if (w < W) pre[w] = (int32_t)(carry + ex);
+            carry += total;
+        }
+        __syncthreads();
+        for (int e = tid; e < len; e += blockDim.x) {
+            const int c = tk[p0 + e];
+            const int off = c - cmin;
+            const int r = pre[off >> 5] + __popc(bm[off >> 5] & ((1u << (off & 31)) - 1u));
+            const int rank = desc ? len - 1 - r : r;
+            ok[p0 + rank] = c;
+            ox[p0 + rank] = tx[p0 + e];
+        }
+        __syncthreads();
     }
 }
 
@@ -583,16 +658,24 @@ void bk_launch_rows(const bk_dev &d, const bk_rows &r, void *stream)
     launch_scan(r.cnt, n, r.part, r.Lrp, st);
     launch_scan(r.cnt + n + 1, n, r.part, r.Urp, st);
     cudaMemsetAsync(r.cnt, 0, sizeof(int32_t) * 2 * ((size_t)n + 1), st);
-    if (d.prec) {
-        bk_rows_scatter<float><<<blocks, 256, 0, st>>>(d, r, 0);
-        bk_rows_sort<float><<<blocks, 256, 0, st>>>(n, r.Lrp, r.tk, vals<float>(r.tx), r.Lrk, vals<float>(r.Lrx), 0);
-        bk_rows_scatter<float><<<blocks, 256, 0, st>>>(d, r, 1);
-        bk_rows_sort<float><<<blocks, 256, 0, st>>>(n, r.Urp, r.tk, vals<float>(r.tx), r.Urk, vals<float>(r.Urx), 1);
-    } else {
-        bk_rows_scatter<double><<<blocks, 256, 0, st>>>(d, r, 0);
-        bk_rows_sort<double><<<blocks, 256, 0, st>>>(n, r.Lrp, r.tk, r.tx, r.Lrk, r.Lrx, 0);
-        bk_rows_scatter<double><<<blocks, 256, 0, st>>>(d, r, 1);
-        bk_rows_sort<double><<<blocks, 256, 0, st>>>(n, r.Urp, r.tk, r.tx, r.Urk, r.Urx, 1);
+    const int lblocks = std::max(1, std::min((n + 255) / 256, 152 * 8));
+    for (int which = 0; which < 2; which++) {
+        const int64_t *rp = which ? r.Urp : r.Lrp;
+        int32_t *ok = which ? r.Urk : r.Lrk;
+        double *ox = which ? r.Urx : r.Lrx;
+        cudaMemsetAsync(r.longs, 0, sizeof(int32_t), st);
+        bk_rows_long_list<<<lblocks, 256, 0, st>>>(n, rp, r.longs);
+        if (d.prec) {
+            bk_rows_scatter<float><<<blocks, 256, 0, st>>>(d, r, which);
+            bk_rows_sort<float><<<blocks, 256, 0, st>>>(n, rp, r.tk, vals<float>(r.tx), ok, vals<float>(ox), which);
+            bk_rows_sort_long<float><<<BK_LONG_CTAS, 1024, 0, st>>>(rp, r.tk, vals<float>(r.tx), ok, vals<float>(ox),
+                                                                     which, r.longs, r.sbits, r.spre, r.swords);
+        } else {
+            bk_rows_scatter<double><<<blocks, 256, 0, st>>>(d, r, which);
+            bk_rows_sort<double><<<blocks, 256, 0, st>>>(n, rp, r.tk, r.tx, ok, ox, which);
+            bk_rows_sort_long<double><<<BK_LONG_CTAS, 1024, 0, st>>>(rp, r.tk, r.tx, ok, ox, which, r.longs, r.sbits,
+                                                                      r.spre, r.swords);
+        }
     }
 }
 

@@ -21,7 +21,15 @@ struct bk_rows {
     double *Ud;                  // n diagonal entries of U
     int32_t *cnt;                // 2 (n + 1) row counts and cursors
     int64_t *part;               // per-block partial sums of the row-start scan
+    // rows longer than BK_LONG_ROW are ordered by a column bitmap, one block a row
+    int32_t *longs;              // [0] count, then the long rows
+    uint32_t *sbits;             // per block: the row's column bitmap
+    int32_t *spre;               // per block: popcount prefix of the bitmap words
+    int64_t swords;              // words of each block's bitmap (n / 32 + 2)
 };
+
+#define BK_LONG_ROW 512
+#define BK_LONG_CTAS 64
 
 struct bk_solve_dev {
     int32_t nitems;               // every step forward and backward, and every ND separator twice

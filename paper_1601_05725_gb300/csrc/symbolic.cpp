@@ -352,17 +352,20 @@ static void prefix_layout(bk_plan &pl)
     pl.upool = pl.ucap / 2 + (1 << 20);
 }
 
-// After an overflow: a column that overflowed gets its exact upper bound, the
-// later columns of the same task twice their room (pivoting moved fill there).
+// After an overflow (a spill pool ran out): a column that overflowed gets four
+// times its room, the later columns of the same task twice theirs (pivoting moved
+// fill there), each at most its upper bound; the pools grow with the regions.
+// Growing geometrically rather than to the bounds keeps the arena proportional to
+// the fill: the bounds of a large ND block sum to many times |L + U|.
 void bk_plan_regrow(bk_plan &pl, const int32_t *over)
 {
     for (const bk_task &T : pl.tasks) {
         bool al = false, au = false;
         for (int32_t c = T.lo; c < T.hi; c++) {
             const size_t k = (size_t)c;
-            if (over[k] & 1) { pl.lcapc[k] = l_bound(T, c); al = true; }
+            if (over[k] & 1) { pl.lcapc[k] = std::min<int64_t>(4 * pl.lcapc[k] + 64, l_bound(T, c)); al = true; }
             else if (al) pl.lcapc[k] = std::min<int64_t>(2 * pl.lcapc[k] + 8, l_bound(T, c));
-            if (over[k] & 2) { pl.ucapc[k] = u_bound(T, c); au = true; }
+            if (over[k] & 2) { pl.ucapc[k] = std::min<int64_t>(4 * pl.ucapc[k] + 64, u_bound(T, c)); au = true; }
             else if (au) pl.ucapc[k] = std::min<int64_t>(2 * pl.ucapc[k] + 8, u_bound(T, c));
         }
     }

@@ -37,7 +37,8 @@ import numpy as np
 
 __all__ = [
     "Problem", "config1", "config2", "config3", "small_problem", "grid_problem",
-    "netlist_problem", "block_diagonal_problem", "refactor_values", "rhs_ones",
+    "netlist_problem", "block_diagonal_problem", "refactor_values", "rhs_ones", "config4",
+    "rhs_normal", "rail_links",
     "CONFIG_SEEDS",
 ]
 
@@ -320,22 +321,63 @@ def _small_blocks(rng: np.random.Generator, total: int, sizes: Tuple[int, int]) 
     return out
 
 
-def _nd_netlist(rng, m, depth, extra=(0, 1), nonlocal_links=False):
-    rows, cols = netlist_pattern(rng, m, extra=extra, nonlocal_links=nonlocal_links)
-    perm, sizes = bisection_order(m, rows, cols, np.arange(m), depth)
+def rail_links(rng: np.random.Generator, m_ring: int, n_rails: int, deg: Tuple[int, int],
+               drop: float = 0.05) -> Tuple[np.ndarray, np.ndarray]:
+    """Directed entries (rows, cols) joining ``n_rails`` rail nodes (ids m_ring ..
+    m_ring + n_rails - 1) to ring nodes: rail k is tied to round(log-uniform(deg))
+    distinct random ring nodes, each tie stored in both directions except that
+    ``drop`` of them keep only one (as the netlist's non-ring links)."""
+    src, dst = [], []
+    for k in range(n_rails):
+        cnt = int(min(m_ring, round(float(_log_uniform(rng, deg[0], deg[1], 1)[0]))))
+        t = np.unique(rng.integers(0, m_ring, 2 * cnt))
+        t = rng.permutation(t)[:cnt]
+        src.append(np.full(t.size, m_ring + k, np.int64))
+        dst.append(t.astype(np.int64))
+    if not src:
+        return np.zeros(0, np.int64), np.zeros(0, np.int64)
+    r = np.concatenate(src)
+    t = np.concatenate(dst)
+    dropped = rng.random(r.size) < drop
+    which = rng.random(r.size) < 0.5
+    keep_fwd = ~(dropped & which)          # rail row, ring column
+    keep_bwd = ~(dropped & ~which)         # ring row, rail column
+    rows = np.concatenate([r[keep_fwd], t[keep_bwd]])
+    cols = np.concatenate([t[keep_fwd], r[keep_bwd]])
+    return rows, cols
+
+
+def _nd_netlist(rng, m, depth, extra=(0, 1), nonlocal_links=False, n_rails=0, rail_deg=(1000, 50000)):
+    m_ring = m - n_rails
+    rows, cols = netlist_pattern(rng, m_ring, extra=extra, nonlocal_links=nonlocal_links)
+    perm, sizes = bisection_order(m_ring, rows, cols, np.arange(m_ring), depth)
+    if n_rails > 0:
+        # rails join nodes on both sides of every cut: they belong to the root separator
+        rr, rc = rail_links(rng, m_ring, n_rails, rail_deg)
+        rows, cols = np.concatenate([rows, rr]), np.concatenate([cols, rc])
+        perm = np.concatenate([perm, np.arange(m_ring, m, dtype=np.int64)])
+        sizes = list(sizes)
+        sizes[-1] += n_rails
     return rows, cols, perm, sizes
 
 
 def netlist_problem(seed: int, n_small: int = 800, small_sizes=(1, 2), m_netlist: int = 1200,
                     depth: int = 2, extra=(0, 1), nonlocal_links: bool = False,
-                    name: str = "netlist", scramble: bool = True) -> Problem:
+                    name: str = "netlist", scramble: bool = True, n_rails: int = 0,
+                    rail_deg=(1000, 50000), coupling_to: str = "next") -> Problem:
     """Circuit-like matrix in the shape of Fig. 2a: small BTF blocks (D1), one
     strongly connected netlist block in ND order (D2), small BTF blocks (D3).
 
     Small blocks have U{small_sizes} rows (full, so irreducible); each small block has
-    one coupling entry into the next block's columns (strictly above the diagonal).
+    one coupling entry (strictly above the diagonal) into the columns of the next
+    block (``coupling_to="next"``: the blocks form one chain) or of a uniformly random
+    later block (``"random"``: a shallow DAG of blocks).
     The netlist block is ND-ordered into ``2**depth`` leaves (``depth=0``: no ND).
+    ``n_rails`` of the netlist's nodes are supply rails tied to many random nodes
+    (``rail_links``); they are ordered last, in the root separator (ND required).
     """
+    if n_rails and depth <= 0:
+        raise ValueError("rails need an ND ordering")
     rng = np.random.default_rng(seed)
     sizes = _small_blocks(rng, n_small, small_sizes) if n_small > 0 else []
     nb_above = len(sizes) // 2
@@ -345,14 +387,15 @@ def netlist_problem(seed: int, n_small: int = 800, small_sizes=(1, 2), m_netlist
     b = _Builder()
     nd_block = -1
     nd_ptr = np.zeros(0, np.int32)
-    # coupling entries: one per small block into the next block
+    # coupling entries: one per small block into a later block
     coupling = []
     block_sizes = [m_netlist if s < 0 else s for s in layout]
     offsets = np.concatenate([[0], np.cumsum(block_sizes)]).astype(np.int64)
     for k, s in enumerate(layout):
         if s > 0 and k + 1 < len(layout):
+            e = k + 1 if coupling_to == "next" else int(rng.integers(k + 1, len(layout)))
             row = offsets[k] + rng.integers(0, s)
-            col = offsets[k + 1] + rng.integers(0, block_sizes[k + 1])
+            col = offsets[e] + rng.integers(0, block_sizes[e])
             coupling.append((row, col, float(_log_uniform(rng, 1e-3, 1e3, 1)[0] * _random_sign(rng, 1)[0])))
     cabs = np.zeros(int(offsets[-1]))
     for row, col, val in coupling:
@@ -361,7 +404,8 @@ def netlist_problem(seed: int, n_small: int = 800, small_sizes=(1, 2), m_netlist
         o = int(offsets[k])
         if s < 0:
             if depth > 0:
-                rows, cols, perm, nsz = _nd_netlist(rng, m_netlist, depth, extra, nonlocal_links)
+                rows, cols, perm, nsz = _nd_netlist(rng, m_netlist, depth, extra, nonlocal_links,
+                                                    n_rails, rail_deg)
             else:
                 rows, cols = netlist_pattern(rng, m_netlist, extra=extra, nonlocal_links=nonlocal_links)
                 perm = continued_bisection(m_netlist, rows, cols, np.arange(m_netlist))
@@ -384,7 +428,7 @@ def netlist_problem(seed: int, n_small: int = 800, small_sizes=(1, 2), m_netlist
     leaves = 2 ** depth if nd_block >= 0 else 0
     prob = b.finish(rng, name, scramble=scramble, nd_block=nd_block, nd_leaves=leaves,
                     nd_node_ptr=nd_ptr)
-    prob.meta.update(seed=seed, n_small_blocks=len(sizes), m_netlist=m_netlist, depth=depth,
+    prob.meta.update(seed=seed, n_small_blocks=len(sizes), m_netlist=m_netlist, depth=depth, n_rails=n_rails,
                      nd_node_sizes=np.diff(nd_ptr).tolist() if nd_block >= 0 else [])
     return prob
 
@@ -499,6 +543,25 @@ def config2(seed: int = CONFIG_SEEDS[2], k: int = 316) -> Problem:
 def config3(seed: int = CONFIG_SEEDS[3], nblocks: int = 8192) -> Problem:
     """8,192 independent netlist blocks of log-uniform 4..1,024 rows."""
     return block_diagonal_problem(seed, nblocks=nblocks, name=f"batched_{nblocks}")
+
+
+def config4(seed: int = CONFIG_SEEDS[4], n: int = 2_000_000, n_rails: int = 200,
+            rail_deg=(1000, 50000)) -> Problem:
+    """Large circuit: 30% of the n rows in BTF blocks of U{1..16} rows, the rest one
+    netlist block with ``n_rails`` supply rails (each tied to log-uniform
+    1e3..5e4 random nodes) in the root separator, ND depth 5 (32 leaves).
+    Each small block has one coupling entry into a uniformly random later block.
+    Smaller ``n`` / ``n_rails`` / ``rail_deg`` give the same structure scaled down."""
+    n_small = int(round(0.3 * n))
+    return netlist_problem(seed, n_small=n_small, small_sizes=(1, 16), m_netlist=n - n_small, depth=5,
+                           n_rails=n_rails, rail_deg=rail_deg, coupling_to="random",
+                           name=f"circuit_rails_n{n}")
+
+
+def rhs_normal(prob: Problem, nrhs: int, seed: int = 0) -> np.ndarray:
+    """n x nrhs right-hand sides drawn N(0, 1) (column-major: one column per system)."""
+    rng = np.random.default_rng(int(prob.meta.get("seed", 0)) + 7919 + seed)
+    return np.asfortranarray(rng.standard_normal((prob.n, nrhs)))
 
 
 def small_problem(seed: int, kind: str = "netlist", **kw) -> Problem:

@@ -1,0 +1,87 @@
+"""The large circuit at full size through the C ABI.
+
+n = 2,000,000, 12.6e6 entries: 70,502 BTF blocks of 1..16 rows (30% of the rows)
+and a 1.4e6-row netlist block in 32 ND leaves whose root separator holds 200
+supply rails tied to 1e3..5e4 random nodes each, so that every leaf column near
+the top of its subtree carries rail rows in L and every rail column a long U
+(|L + U| = 1.1e8 after pivoting).
+
+FP64: pivots, L/U patterns and values against the oracle, bit for bit, for the
+factorization, one refactorization and a four-column solve.  FP32 factorization
+with FP64 refinement: backward error <= 1e-12 for each of four N(0, 1)
+right-hand sides.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import oracle
+from paper_1601_05725_gb300 import basker, build
+from paper_1601_05725_gb300 import inputs as I
+from tests import helpers as H
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+NRHS = 4
+
+
+@pytest.fixture(scope="module")
+def c4():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    build.build()
+    basker.load()
+    return I.config4()
+
+
+def _dev(a):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def _solve(h, B):
+    return h.solve(_dev(B)).cpu().numpy()
+
+
+def _same(h, f):
+    prow, L, U = h.export()
+    np.testing.assert_array_equal(prow, f.prow)
+    for got, ref in ((L, f.L), (U, f.U)):
+        np.testing.assert_array_equal(got.indptr, ref.indptr)
+        np.testing.assert_array_equal(got.indices, ref.indices)
+        assert np.array_equal(got.data, ref.data)
+
+
+def test_config4_fp64_bitwise(c4):
+    prob = c4
+    o = oracle.OracleLU(prob)
+    assert o.factor() == "OK"
+    f0 = o.factors()
+    h = basker.Handle.from_problem(prob)
+    h.factor(_dev(prob.values))
+    _same(h, f0)
+    B = I.rhs_normal(prob, NRHS)
+    np.testing.assert_array_equal(_solve(h, B), o.solve(B))
+    v = I.refactor_values(prob, 1)
+    assert o.factor(v, pref=f0.prow) == "OK"
+    del f0
+    h.refactor(_dev(v))
+    _same(h, o.factors())
+    np.testing.assert_array_equal(_solve(h, B), o.solve(B))
+
+
+def test_config4_fp32_refined_four_rhs(c4):
+    prob = c4
+    h = basker.Handle.from_problem(prob, precision=1)
+    B = I.rhs_normal(prob, NRHS)
+    for values in (prob.values, I.refactor_values(prob, 2)):
+        if values is prob.values:
+            h.factor(_dev(values))
+        else:
+            h.refactor(_dev(values))
+        X = _solve(h, B)
+        inf = h.info()
+        A = sp.csc_matrix((values, prob.rowind, prob.colptr), shape=(prob.n, prob.n))
+        for q in range(NRHS):
+            assert H.solve_backward_error(A, X[:, q], B[:, q]) <= 1e-12
+        assert inf["precision_used"] in (0, 1)

@@ -118,6 +118,32 @@ def test_refactor_sequence_matches_oracle(kind, seed, kw, sigma, tau):
         assert repivots > 0, "the repivoting path was not exercised"
 
 
+@pytest.mark.parametrize("mode", [1, 2])
+def test_refactor_switch_modes_give_the_same_factors(mode):
+    """Rounds only (1) and one complete pass with the previous pivots preferred (2)
+    both compute the refactorization's definition: the oracle's factors."""
+    prob = I.small_problem(61, "netlist", n_small=80, m_netlist=600, depth=3)
+    o, s = _oracle(prob)
+    f = o.factors()
+    h = basker.Handle.from_problem(prob, refactor_switch=mode)
+    h.factor(_dev(prob.values))
+    rounds = 0
+    for k in range(1, 4):
+        v = I.refactor_values(prob, k, sigma=0.3)
+        assert o.factor(v, pref=f.prow) == "OK"
+        f = o.factors()
+        h.refactor(_dev(v))
+        rounds += h.info()["last_rounds"]
+        assert_same_factors(h, f)
+        b = I.rhs_ones(prob, v)
+        np.testing.assert_array_equal(h.solve(_dev(b)).cpu().numpy(), o.solve(b))
+    inf = h.info()
+    if mode == 1:
+        assert rounds > 0 and inf["full_refactors"] == 0
+    else:
+        assert rounds == 0 and inf["full_refactors"] == 3   # every step repivots (checked on the oracle)
+
+
 def test_config2_factor_refactor_solve():
     """The power-grid workload at full size: every pivot, pattern entry and value."""
     prob = I.config2()

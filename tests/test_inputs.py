@@ -95,3 +95,37 @@ def test_seeded_and_reproducible():
     v1, v2 = I.refactor_values(a, 1), I.refactor_values(a, 2)
     assert not np.array_equal(v1, v2)
     np.testing.assert_array_equal(v1, I.refactor_values(b, 1))
+
+
+def test_config4_shape_scaled():
+    """The large-circuit generator at a tenth of its size: 30% of the rows in BTF
+    blocks of 1..16 rows, one netlist block in 32 ND leaves whose rails sit in the
+    root separator and are tied to the requested number of nodes."""
+    n, rails, deg = 200_000, 20, (100, 5000)
+    p = I.config4(n=n, n_rails=rails, rail_deg=deg)
+    assert p.n == n and p.nd_leaves == 32 and len(p.nd_node_ptr) == 64
+    sizes = np.diff(p.block_ptr)
+    big = int(np.argmax(sizes))
+    assert big == p.nd_block and sizes[big] == n - int(round(0.3 * n))
+    assert set(np.unique(np.delete(sizes, big))) <= set(range(1, 17))
+    B = _check_structure(p)
+    # the last `rails` rows of the ND block are the rails: in the root separator,
+    # each tied (in at least one direction) to deg[0]..deg[1] ring nodes
+    k1 = p.block_ptr[p.nd_block + 1]
+    root_lo = p.nd_node_ptr[-2]
+    assert k1 - root_lo > rails
+    Bd = B[p.block_ptr[p.nd_block]:k1, p.block_ptr[p.nd_block]:k1]
+    S = ((Bd != 0).astype(np.int8) + (Bd != 0).T.astype(np.int8)).tocsr()
+    m = Bd.shape[0]
+    deg_rails = np.diff(S.indptr)[m - rails:] - 1       # minus the diagonal
+    assert (deg_rails >= 0.9 * deg[0]).all() and (deg_rails <= deg[1]).all()
+    deg_ring = np.diff(S.indptr)[: m - rails]
+    assert np.median(deg_ring) < 10
+
+
+@pytest.mark.slow
+def test_config4_full_size_counts():
+    p = I.config4()
+    assert p.n == 2_000_000 and 11e6 < p.nnz < 14e6
+    assert 60_000 < p.nblocks < 80_000
+    assert p.meta["nd_node_sizes"][-1] >= 200
