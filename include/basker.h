@@ -55,8 +55,11 @@ typedef struct {
     double tau;                   /* pivot threshold in (0,1]; default 1e-3 */
     double slack;                 /* extra L/U capacity over the symbolic count; default 1.0 */
     long long wait_budget_cycles; /* clock64 cycles any in-kernel wait may spin; default 2e10 */
-    int factor_mode;              /* must be 0: every column of basker_factor goes through
-                                     the reach of Algorithm 1 (other values: INVALID_ARG) */
+    int factor_mode;              /* 0 (default): the in-node phase of an ND separator whose
+                                     column state fits in shared memory runs as one dense
+                                     right-looking elimination by a block of threads; 1: every
+                                     in-node phase column by column in one warp.  The
+                                     factors are the same (other values: INVALID_ARG) */
     int timing;                   /* nonzero: record CUDA events around every kernel launch
                                      on the caller's stream; totals in basker_info */
     int precision;                /* 0 (default): FP64 factorization and solve.
@@ -105,7 +108,8 @@ typedef struct {
                                      the last basker_info call: [0] value gather,
                                      [1] stored-pattern refactor, [2] DAG levels,
                                      [3] in-node Algorithm 1, [4] separator descendant
-                                     phase, [5] solve, [6] pivot reset,
+                                     phase, [5] solve, [6] separators' in-node phase as
+                                     dense eliminations,
                                      [7] refactorization rounds after the stored-pattern
                                      pass, [8] factors transposed into rows for the
                                      solve, [9] FP64 refinement (precision 1) */

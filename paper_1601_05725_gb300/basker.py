@@ -61,7 +61,7 @@ class Info(ctypes.Structure):
                 ("rounds_columns", ctypes.c_int64), ("full_refactors", ctypes.c_int32), ("pad0", ctypes.c_int32)]
 
 KERNEL_KINDS = ["gather", "static_refactor", "dag_levels", "gp_in_node", "gp_descendant", "solve",
-                "pivot_reset", "refactor_rounds", "rows_transpose", "refine"]
+                "dense_node", "refactor_rounds", "rows_transpose", "refine"]
 
 
 EXPORTED = ["basker_default_options", "basker_symbolic", "basker_factor", "basker_refactor",

@@ -18,7 +18,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libbasker_gb300.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 SOURCES = ["api.cu", "kernels_gp.cu", "kernels_static.cu", "kernels_solve.cu", "symbolic.cpp",
-           "solve_plan.cpp", "noalloc.cu", "kernels_dd.cu", "refine.cu"]
+           "solve_plan.cpp", "noalloc.cu", "kernels_dd.cu", "refine.cu", "kernels_dense.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 

@@ -29,6 +29,9 @@ struct basker_s {
     std::vector<size_t> lv_smem;
     std::vector<int32_t *> lv_cols;
     std::vector<int32_t> lv_ncols;
+    std::vector<int32_t *> lv_dense;   // separators whose in-node phase runs as one dense elimination
+    std::vector<int32_t> lv_ndense;
+    std::vector<size_t> lv_dsmem;
     // redo lists (device buffers of n ints each) and their pinned staging
     int32_t *rd_tasks = nullptr, *rd_c0 = nullptr, *rd_cols = nullptr;
     int32_t *h_stage = nullptr;      // pinned, 3n + ntasks + 16 ints
@@ -69,7 +72,7 @@ struct basker_s {
 
 namespace {
 
-enum { KT_GATHER = 0, KT_STATIC = 1, KT_LEVELS = 2, KT_GP = 3, KT_DESC = 4, KT_SOLVE = 5, KT_RESET = 6, KT_SPEC = 7,
+enum { KT_GATHER = 0, KT_STATIC = 1, KT_LEVELS = 2, KT_GP = 3, KT_DESC = 4, KT_SOLVE = 5, KT_DENSE = 6, KT_SPEC = 7,
        KT_ROWS = 8, KT_REFINE = 9 };
 
 cudaEvent_t take_event(basker_t h)
@@ -320,18 +323,30 @@ int setup_device(basker_t h)
     h->lv_smem.assign(nl, 0);
     h->lv_cols.assign(nl, nullptr);
     h->lv_ncols.assign(nl, 0);
+    h->lv_dense.assign(nl, nullptr);
+    h->lv_ndense.assign(nl, 0);
+    h->lv_dsmem.assign(nl, 0);
     for (size_t l = 0; l < nl; l++) {
-        const auto &ids = pl.level_tasks[l];
-        TRY(upload(h, &h->lv_tasks[l], ids));
-        h->lv_ntasks[l] = (int32_t)ids.size();
-        size_t sm = 0;
+        std::vector<int32_t> ids, dense;
+        size_t sm = 0, dsm = 0;
         std::vector<int32_t> cols;
-        for (int32_t t : ids) {
+        for (int32_t t : pl.level_tasks[l]) {
             const bk_task &T = pl.tasks[(size_t)t];
-            if (T.wsoff < 0) sm = std::max(sm, bk_task_smem_bytes(T));
+            if (h->opt.factor_mode == 0 && bk_dense_node_eligible(T)) {
+                dense.push_back(t);
+                dsm = std::max(dsm, bk_dense_node_smem(T));
+            } else {
+                ids.push_back(t);
+                if (T.wsoff < 0) sm = std::max(sm, bk_task_smem_bytes(T));
+            }
             if (T.sp_lo < T.lo)
                 for (int32_t c = T.lo; c < T.hi; c++) cols.push_back(c);
         }
+        TRY(upload(h, &h->lv_tasks[l], ids));
+        h->lv_ntasks[l] = (int32_t)ids.size();
+        TRY(upload(h, &h->lv_dense[l], dense));
+        h->lv_ndense[l] = (int32_t)dense.size();
+        h->lv_dsmem[l] = (dsm + 15) & ~(size_t)15;
         h->lv_smem[l] = (sm + 15) & ~(size_t)15;
         TRY(upload(h, &h->lv_cols[l], cols));
         h->lv_ncols[l] = (int32_t)cols.size();
@@ -451,6 +466,13 @@ int launch_full_gp(basker_t h, cudaStream_t s, int pref_mode)
         if (h->lv_ntasks[l] > 0) {
             tbeg(h, KT_GP, s, 1);
             bk_launch_gp_tasks(h->d, h->lv_tasks[l], nullptr, h->lv_ntasks[l], h->lv_smem[l], tau, pref_mode, s);
+            CU(cudaGetLastError());
+            tend(h, s);
+            h->launches++;
+        }
+        if (h->lv_ndense[l] > 0) {
+            tbeg(h, KT_DENSE, s, 1);
+            bk_launch_dense_nodes(h->d, h->lv_dense[l], h->lv_ndense[l], h->lv_dsmem[l], tau, pref_mode, s);
             CU(cudaGetLastError());
             tend(h, s);
             h->launches++;
@@ -905,7 +927,7 @@ int basker_symbolic(int32_t n, const int32_t *colptr, const int32_t *rowind, con
     basker_default_options(&h->opt);
     if (opt) h->opt = *opt;
     if (!(h->opt.tau > 0.0 && h->opt.tau <= 1.0) || h->opt.slack < 0.0 || h->opt.wait_budget_cycles <= 0 ||
-        h->opt.factor_mode != 0 || h->opt.precision < 0 || h->opt.precision > 2 ||
+        h->opt.factor_mode < 0 || h->opt.factor_mode > 1 || h->opt.precision < 0 || h->opt.precision > 2 ||
         h->opt.refactor_switch < 0 || h->opt.refactor_switch > 2 ||
         (h->opt.precision >= 1 && (h->opt.ir_max_iter < 1 || !(h->opt.ir_tol > 0.0) || !(h->opt.growth_limit > 0.0)))) {
         delete h;

@@ -147,6 +147,12 @@ int bk_plan_build(int32_t n, const int32_t *colptr, const int32_t *rowind, const
 void bk_plan_layout(bk_plan &plan);                      // L/U regions, workspaces
 void bk_plan_regrow(bk_plan &plan, const int32_t *over); // after an overflow (per-column flags)
 size_t bk_task_smem_bytes(const bk_task &t);
+// kernels_dense.cu: the in-node phase of a separator as one dense elimination
+#define BK_DENSE_SMEM (200 * 1024)
+size_t bk_dense_node_smem(const bk_task &t);
+bool bk_dense_node_eligible(const bk_task &t);
+void bk_launch_dense_nodes(const bk_dev &d, const int32_t *task_ids, int32_t ntasks, size_t smem, double tau,
+                           int pref_mode, void *stream);
 bool bk_task_fits_smem(const bk_task &t);
 
 // kernels (launchers), kernels_*.cu
@@ -157,8 +163,6 @@ void bk_launch_gp_desc(const bk_dev &d, const int32_t *cols, int32_t ncols, int3
                        void *stream);
 void bk_launch_dd(const bk_dev &d, const int32_t *cols, int32_t ncols, int32_t *counter, double tau,
                   int32_t epoch, long long budget, int32_t refno, void *stream, int max_warps = 0);
-void bk_launch_reset_pivots(const bk_dev &d, const int32_t *task_ids, const int32_t *task_c0,
-                            int32_t ntasks, void *stream);
 void bk_launch_static(const bk_dev &d, int32_t ncols, double tau, int32_t epoch,
                       long long budget, int blocks, void *stream);
 void bk_launch_levels(const bk_dev &d, int32_t epoch, long long budget, int blocks, void *stream);

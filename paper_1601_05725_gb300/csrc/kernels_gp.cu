@@ -17,7 +17,6 @@
 //                      depends on the separator's own pivots, so all its columns
 //                      run at once; the in-node phase then continues each column
 //                      with the separator's own steps and picks the pivot.
-//   bk_reset_pivots_kernel  unmark the rows pivoted by columns that are redone.
 //
 // Within a column every entry receives its updates one fma at a time in
 // ascending pivot-step order (descendant steps, then own steps), and L is
@@ -541,18 +540,6 @@ __global__ void __launch_bounds__(128) bk_gp_desc_kernel(bk_dev d, const int32_t
     }
 }
 
-__global__ void bk_reset_pivots_kernel(bk_dev d, const int32_t *__restrict__ task_ids,
-                                       const int32_t *__restrict__ task_c0, int32_t ntasks)
-{
-    for (int t = blockIdx.x; t < ntasks; t += gridDim.x) {
-        const bk_task &T = d.tasks[task_ids[t]];
-        for (int c = task_c0[t] + threadIdx.x; c < T.hi; c += blockDim.x) {
-            const int r = d.prow[c];
-            if (r >= 0) d.pinv[r] = -1;
-        }
-    }
-}
-
 }  // namespace
 
 size_t bk_gp_smem_limit() { return 220 * 1024; }
@@ -595,9 +582,3 @@ void bk_launch_gp_desc(const bk_dev &d, const int32_t *cols, int32_t ncols, int3
         bk_gp_desc_kernel<double><<<(warps + 3) / 4, 128, 0, (cudaStream_t)stream>>>(d, cols, ncols, counter);
 }
 
-void bk_launch_reset_pivots(const bk_dev &d, const int32_t *task_ids, const int32_t *task_c0,
-                            int32_t ntasks, void *stream)
-{
-    if (ntasks <= 0) return;
-    bk_reset_pivots_kernel<<<std::min(ntasks, 1024), 128, 0, (cudaStream_t)stream>>>(d, task_ids, task_c0, ntasks);
-}

@@ -118,6 +118,46 @@ def test_refactor_sequence_matches_oracle(kind, seed, kw, sigma, tau):
         assert repivots > 0, "the repivoting path was not exercised"
 
 
+@pytest.mark.parametrize("kind,seed,kw", [
+    ("netlist", 71, dict(n_small=60, m_netlist=900, depth=3)),
+    ("grid", 72, dict(k=40, depth=3)),
+    ("netlist", 73, dict(n_small=0, m_netlist=3000, depth=4, nonlocal_links=True)),
+])
+def test_dense_separator_elimination_equals_column_by_column(kind, seed, kw):
+    """factor_mode 0 runs each separator's in-node phase as one dense
+    right-looking elimination, factor_mode 1 column by column in one warp: the
+    same factors as the oracle's, in FP64 and (between the two modes) in FP32,
+    for the factorization and a refactorization that repivots."""
+    prob = I.small_problem(seed, kind, **kw)
+    o, s = _oracle(prob)
+    f = o.factors()
+    hd = basker.Handle.from_problem(prob, factor_mode=0)
+    hw = basker.Handle.from_problem(prob, factor_mode=1)
+    for h in (hd, hw):
+        h.factor(_dev(prob.values))
+        assert_same_factors(h, f)
+    assert hd.info()["kernel_calls"]["dense_node"] > 0
+    assert hw.info()["kernel_calls"]["dense_node"] == 0
+    v = I.refactor_values(prob, 1, sigma=0.3)
+    assert o.factor(v, pref=f.prow) == "OK"
+    g = o.factors()
+    for h in (hd, hw):
+        h2 = basker.Handle.from_problem(prob, factor_mode=h is hw, refactor_switch=2)
+        h2.factor(_dev(prob.values))
+        h2.refactor(_dev(v))
+        assert_same_factors(h2, g)
+    f32 = []
+    for mode in (0, 1):
+        h = basker.Handle.from_problem(prob, factor_mode=mode, precision=1)
+        h.factor(_dev(prob.values))
+        f32.append(h.export())
+    np.testing.assert_array_equal(f32[0][0], f32[1][0])
+    for a, b in zip(f32[0][1:], f32[1][1:]):
+        np.testing.assert_array_equal(a.indptr, b.indptr)
+        np.testing.assert_array_equal(a.indices, b.indices)
+        assert np.array_equal(a.data, b.data)
+
+
 @pytest.mark.parametrize("mode", [1, 2])
 def test_refactor_switch_modes_give_the_same_factors(mode):
     """Rounds only (1) and one complete pass with the previous pivots preferred (2)
