@@ -83,7 +83,10 @@ typedef struct {
                                      complete Algorithm 1 pass with the previous pivots
                                      preferred; 1: rounds only; 2: the complete pass at once.
                                      The factors are the same in every mode. */
-    int reserved[3];
+    int graphs;                   /* nonzero (default): the launches that follow every
+                                     factorization are replayed from a CUDA graph captured
+                                     once per L/U arena; 0: launched one by one */
+    int reserved[2];
 } basker_options;
 
 typedef struct {
@@ -133,7 +136,7 @@ typedef struct {
                                      last basker_info call */
     int32_t full_refactors;       /* refactorizations finished by a complete Algorithm 1
                                      pass instead of rounds (options.refactor_switch) */
-    int32_t pad0;
+    int32_t graph_launches;       /* CUDA graph replays so far (options.graphs) */
 } basker_info_t;
 
 /* Defaults listed in basker_options. */

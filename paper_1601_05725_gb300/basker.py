@@ -39,7 +39,7 @@ class Options(ctypes.Structure):
                 ("wait_budget_cycles", ctypes.c_longlong), ("factor_mode", ctypes.c_int),
                 ("timing", ctypes.c_int), ("precision", ctypes.c_int), ("ir_max_iter", ctypes.c_int),
                 ("ir_tol", ctypes.c_double), ("growth_limit", ctypes.c_double), ("refactor_switch", ctypes.c_int),
-                ("reserved", ctypes.c_int * 3)]
+                ("graphs", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
 
 
 class Info(ctypes.Structure):
@@ -58,7 +58,7 @@ class Info(ctypes.Structure):
                 ("ir_eta", ctypes.c_double), ("growth", ctypes.c_double),
                 ("kernel_calls", ctypes.c_int32 * 10), ("cuda_error", ctypes.c_int32),
                 ("cuda_line", ctypes.c_int32),
-                ("rounds_columns", ctypes.c_int64), ("full_refactors", ctypes.c_int32), ("pad0", ctypes.c_int32)]
+                ("rounds_columns", ctypes.c_int64), ("full_refactors", ctypes.c_int32), ("graph_launches", ctypes.c_int32)]
 
 KERNEL_KINDS = ["gather", "static_refactor", "dag_levels", "gp_in_node", "gp_descendant", "solve",
                 "dense_node", "refactor_rounds", "rows_transpose", "refine"]
@@ -144,9 +144,12 @@ class Handle:
                  tau: float = 1e-3, slack: Optional[float] = None, wait_budget_cycles: Optional[int] = None,
                  factor_mode: int = 0, timing: bool = False, precision: int = 0,
                  ir_max_iter: Optional[int] = None, ir_tol: Optional[float] = None,
-                 growth_limit: Optional[float] = None, refactor_switch: Optional[int] = None):
+                 growth_limit: Optional[float] = None, refactor_switch: Optional[int] = None,
+                 graphs: Optional[bool] = None):
         self.lib = load()
         opt = default_options()
+        if graphs is not None:
+            opt.graphs = 1 if graphs else 0
         if refactor_switch is not None:
             opt.refactor_switch = int(refactor_switch)
         opt.tau = float(tau)
@@ -258,7 +261,7 @@ class Handle:
         s = self.lib.basker_info(self.h, ctypes.byref(inf))
         if s != 0:
             raise BaskerError(s, "basker_info")
-        out = {k: getattr(inf, k) for k, _ in Info._fields_ if k not in ("reserved", "pad0", "kernel_ms",
+        out = {k: getattr(inf, k) for k, _ in Info._fields_ if k not in ("reserved", "kernel_ms",
                                                                           "kernel_calls")}
         out["kernel_calls"] = {KERNEL_KINDS[i]: inf.kernel_calls[i] for i in range(len(KERNEL_KINDS))}
         out["kernel_ms"] = {KERNEL_KINDS[i]: inf.kernel_ms[i] for i in range(len(KERNEL_KINDS))}

@@ -9,6 +9,7 @@
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "basker_internal.h"
@@ -65,6 +66,11 @@ struct basker_s {
     // launch sizes chosen by basker_autotune (0: the occupancy defaults)
     int tune_static = 0, tune_solve = 0, tune_dd = 0;
     basker_t twin = nullptr;
+    // options.graphs: the launches that follow every factorization (factors into
+    // rows, the solve's leaf order), captured once per arena and replayed
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t g_finish = nullptr;
+    int32_t arena_ver = 0, g_finish_ver = -1;
     // the symbolic inputs, kept to build the twin
     std::vector<int32_t> in_colptr, in_rowind, in_P, in_Q, in_bptr, in_ndptr;
     int32_t in_nblocks = 0, in_ndblock = -1, in_ndleaves = 0;
@@ -134,12 +140,25 @@ int dalloc(basker_t h, T **p, size_t count, bool zero = false)
     return BASKER_OK;
 }
 
+// Stream capture (options.graphs) and calls that synchronize the whole device
+// (cudaDeviceSynchronize, cudaFree) must not overlap between threads: a
+// device-wide synchronization invalidates another thread's capture.  Captures are
+// short (they record launches, nothing runs), so one process-wide lock suffices.
+std::mutex g_capture_mu;
+
 void dfree(basker_t h, void *p)
 {
     if (!p) return;
     auto it = std::find(h->allocs.begin(), h->allocs.end(), p);
     if (it != h->allocs.end()) h->allocs.erase(it);
+    std::lock_guard<std::mutex> lk(g_capture_mu);
     cudaFree(p);
+}
+
+cudaError_t device_sync()
+{
+    std::lock_guard<std::mutex> lk(g_capture_mu);
+    return cudaDeviceSynchronize();
 }
 
 template <typename T>
@@ -184,6 +203,7 @@ int alloc_factors(basker_t h)
     h->d.Lx = h->d.Ux = nullptr;
     h->d.lpool_end = pl.lcap + pl.lpool;
     h->d.upool_end = pl.ucap + pl.upool;
+    h->arena_ver++;                   // captured launches hold the old arrays
     TRY(dalloc(h, &h->d.Li, (size_t)h->d.lpool_end));
     // the factors by rows (for the solve) have the same capacities
     bk_rows &r = h->sd.r;
@@ -439,7 +459,7 @@ int read_status(basker_t h, cudaStream_t s)
 int regrow(basker_t h)
 {
     std::vector<int32_t> over((size_t)h->pl.n);
-    CU(cudaDeviceSynchronize());
+    CU(device_sync());
     CU(cudaMemcpy(over.data(), h->d.col_over, over.size() * 4, cudaMemcpyDeviceToHost));
     CU(cudaMemset(h->d.col_over, 0, over.size() * 4));
     bk_plan_regrow(h->pl, over.data());
@@ -609,13 +629,43 @@ int static_pass(basker_t h, cudaStream_t s)
 // After a factorization: the column levels of the new pattern (the next
 // refactorization's claim order, and the backward order of the ND leaves in the
 // solve), the factors by rows, and the solve's order of the leaf rows.
+// The factors into rows and the solve's leaf order: 19 launches that depend on
+// nothing but the arena, recorded once into a CUDA graph (on the handle's own
+// stream, so that the caller's stream may be the legacy default stream) and
+// replayed on the caller's stream.
+int capture_finish(basker_t h)
+{
+    if (!h->cap_stream) CU(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    if (h->g_finish) {
+        cudaGraphExecDestroy(h->g_finish);
+        h->g_finish = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    std::lock_guard<std::mutex> lk(g_capture_mu);
+    CU(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    bk_launch_rows(h->d, h->sd.r, h->cap_stream);
+    bk_launch_leaf_order(h->d, h->sd, h->cap_stream);
+    CU(cudaStreamEndCapture(h->cap_stream, &g));
+    const cudaError_t e = cudaGraphInstantiate(&h->g_finish, g, 0);
+    cudaGraphDestroy(g);
+    CU(e);
+    h->g_finish_ver = h->arena_ver;
+    return BASKER_OK;
+}
+
 int finish_factorization(basker_t h, cudaStream_t s)
 {
     if (!h->schedule_valid) TRY(compute_schedule(h, s));
-    tbeg(h, KT_ROWS, s, 14);
-    bk_launch_rows(h->d, h->sd.r, s);
-    CU(cudaGetLastError());
-    bk_launch_leaf_order(h->d, h->sd, s);
+    tbeg(h, KT_ROWS, s, 19);
+    if (h->opt.graphs) {
+        if (!h->g_finish || h->g_finish_ver != h->arena_ver) TRY(capture_finish(h));
+        CU(cudaGraphLaunch(h->g_finish, s));
+        h->info.graph_launches++;
+    } else {
+        bk_launch_rows(h->d, h->sd.r, s);
+        CU(cudaGetLastError());
+        bk_launch_leaf_order(h->d, h->sd, s);
+    }
     CU(cudaGetLastError());
     tend(h, s);
     CU(cudaGetLastError());
@@ -896,6 +946,7 @@ void basker_default_options(basker_options *opt)
     opt->ir_max_iter = 10;
     opt->ir_tol = 1e-13;
     opt->growth_limit = 1e4;
+    opt->graphs = 1;
 }
 
 const char *basker_strerror(int status)
@@ -1066,7 +1117,7 @@ int basker_info(basker_t h, basker_info_t *out)
     {
         const size_t n = (size_t)h->pl.n;
         std::vector<int32_t> lc(n), uc(n);
-        CU(cudaDeviceSynchronize());
+        CU(device_sync());
         CU(cudaMemcpy(lc.data(), h->d.Lcnt, n * 4, cudaMemcpyDeviceToHost));
         CU(cudaMemcpy(uc.data(), h->d.Ucnt, n * 4, cudaMemcpyDeviceToHost));
         int64_t nl = 0, nu = 0;
@@ -1097,7 +1148,7 @@ int basker_export(basker_t h, int32_t *prow, int64_t *Lp, int32_t *Li, double *L
     if (!h || !nnz_l || !nnz_u) return BASKER_ERR_INVALID_ARG;
     if (!h->factored) return BASKER_ERR_NOT_FACTORED;
     cudaSetDevice(h->device);
-    CU(cudaDeviceSynchronize());
+    CU(device_sync());
     const size_t n = (size_t)h->pl.n;
     std::vector<int32_t> lc(n), uc(n), pr(n), pinv(n);
     std::vector<int64_t> lb(n + 1), ub(n + 1);
@@ -1218,8 +1269,11 @@ void basker_free(basker_t h)
 {
     if (!h) return;
     cudaSetDevice(h->device);
-    cudaDeviceSynchronize();
-    for (void *p : h->allocs) cudaFree(p);
+    {
+        std::lock_guard<std::mutex> lk(g_capture_mu);
+        cudaDeviceSynchronize();
+        for (void *p : h->allocs) cudaFree(p);
+    }
     if (h->h_stage) cudaFreeHost(h->h_stage);
     if (h->h_status) cudaFreeHost(h->h_status);
     if (h->h_task_fail) cudaFreeHost(h->h_task_fail);
@@ -1228,6 +1282,8 @@ void basker_free(basker_t h)
     if (h->open_ev) cudaEventDestroy(h->open_ev);
     if (h->h_norms) cudaFreeHost(h->h_norms);
     if (h->twin) basker_free(h->twin);
+    if (h->g_finish) cudaGraphExecDestroy(h->g_finish);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     delete h;
 }
 

@@ -158,6 +158,31 @@ def test_dense_separator_elimination_equals_column_by_column(kind, seed, kw):
         assert np.array_equal(a.data, b.data)
 
 
+def test_graph_replay_equals_direct_launches():
+    """options.graphs replays the post-factorization launches from a captured
+    CUDA graph (slack 0: columns move to the spill pools between replays): the
+    solves equal those of direct launches and the oracle's, bit for bit."""
+    prob = I.small_problem(81, "netlist", n_small=60, m_netlist=700, depth=3)
+    o, s = _oracle(prob)
+    f = o.factors()
+    hg = basker.Handle.from_problem(prob, slack=0.0, graphs=True)
+    hd = basker.Handle.from_problem(prob, slack=0.0, graphs=False)
+    for h in (hg, hd):
+        h.factor(_dev(prob.values))
+        assert_same_factors(h, f)
+    for k in range(1, 4):
+        v = I.refactor_values(prob, k, sigma=0.3)
+        assert o.factor(v, pref=f.prow) == "OK"
+        f = o.factors()
+        b = I.rhs_ones(prob, v)
+        xo = o.solve(b)
+        for h in (hg, hd):
+            h.refactor(_dev(v))
+            np.testing.assert_array_equal(h.solve(_dev(b)).cpu().numpy(), xo)
+    ig, idd = hg.info(), hd.info()
+    assert ig["graph_launches"] == 4 and idd["graph_launches"] == 0
+
+
 @pytest.mark.parametrize("mode", [1, 2])
 def test_refactor_switch_modes_give_the_same_factors(mode):
     """Rounds only (1) and one complete pass with the previous pivots preferred (2)

@@ -82,7 +82,7 @@ def test_memory_cap_evicts_and_results_stay_exact(stream_of_requests):
     srv = Server(pats, slots=2, mem_cap=cap)
     res = srv.run(reqs)
     srv.close()
-    assert all(r.error is None for r in res)
+    assert all(r.error is None for r in res), [r.error for r in res if r.error][:3]
     assert srv.evictions > 0 and srv.peak_bytes <= cap
     # an evicted pattern restarts from a factorization: its sequence is split there
     for r in res:
