@@ -516,7 +516,10 @@ int stage_upload(basker_t h, cudaStream_t s, int32_t *dst, const std::vector<int
 // dirty-dataflow kernel.  A task with a rejected column f starts a round at f
 // (resolve); a separator whose descendants changed starts at its first column
 // (force); after a round, each task that rejected a speculated pivot at f' runs
-// another round from f'.
+// another round from f'.  Separators whose in-node phase fits the dense
+// elimination are instead recomputed whole: descendant phase, then the dense
+// elimination with the previous pivots preferred (the refactorization's
+// definition for those columns, as in a complete pass).
 int launch_redo(basker_t h, cudaStream_t s)
 {
     bk_plan &pl = h->pl;
@@ -547,6 +550,43 @@ int launch_redo(basker_t h, cudaStream_t s)
             }
         }
         for (int32_t t : active) mark_ancestors((size_t)t);
+        if (l > 0 && h->opt.factor_mode == 0 && !active.empty()) {
+            // separators: the descendant phase and one dense elimination with the
+            // previous pivots preferred recompute each of them in two launches,
+            // instead of rounds of column-by-column recomputation
+            std::vector<int32_t> dense, rest, cols;
+            for (int32_t t : active) {
+                const bk_task &T = pl.tasks[(size_t)t];
+                if (bk_dense_node_eligible(T)) {
+                    dense.push_back(t);
+                    for (int32_t c = T.lo; c < T.hi; c++) cols.push_back(c);
+                } else {
+                    rest.push_back(t);
+                }
+            }
+            if (!dense.empty()) {
+                size_t dsm = 0;
+                for (int32_t t : dense) dsm = std::max(dsm, bk_dense_node_smem(pl.tasks[(size_t)t]));
+                CU(cudaStreamSynchronize(s));       // the staging buffer is reused
+                TRY(stage_upload(h, s, h->rd_cols, cols, 0));
+                TRY(stage_upload(h, s, h->rd_tasks, dense, (size_t)pl.n));
+                CU(cudaMemsetAsync(h->d.counter + 3, 0, sizeof(int32_t), s));
+                tbeg(h, KT_DESC, s, 1);
+                bk_launch_gp_desc(h->d, h->rd_cols, (int32_t)cols.size(), h->d.counter + 3, s);
+                CU(cudaGetLastError());
+                tend(h, s);
+                tbeg(h, KT_DENSE, s, 1);
+                bk_launch_dense_nodes(h->d, h->rd_tasks, (int32_t)dense.size(), (dsm + 15) & ~(size_t)15, tau, 1, s);
+                CU(cudaGetLastError());
+                tend(h, s);
+                h->launches += 2;
+                h->info.last_rounds++;
+                redone += (int32_t)cols.size();
+                const int st = read_status(h, s);
+                if (st != BASKER_OK) return st;
+            }
+            active.swap(rest);
+        }
         for (int round = 0; !active.empty(); round++) {
             if (round > 4 * (int)pl.n + 8) return BASKER_ERR_INVALID_ARG;   // cannot happen: each round resolves a column
             std::vector<int32_t> cols;

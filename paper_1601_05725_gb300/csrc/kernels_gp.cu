@@ -34,6 +34,8 @@ using namespace bk;
 
 namespace {
 
+constexpr int DESC_PF = 8;     // L entries per lane in flight in the descendant phase
+
 // B's values in the factorization's type (FP32: rounded to nearest from FP64).
 template <typename V>
 __global__ void bk_gather_kernel(V *__restrict__ Bx, const double *__restrict__ vals,
@@ -493,18 +495,34 @@ __global__ void __launch_bounds__(128) bk_gp_desc_kernel(bk_dev d, const int32_t
             nu++;
             const int64_t jl = d.Lbeg[j];
             const int jc = d.Lcnt[j];
-            for (int q = lane; q < jc; q += 32) {
-                const int r = d.Li[jl + q];
-                const V l = Lx[jl + q];
-                const int s = slot_of(T, base, r);
-                if (s < 0) { report_internal(d.status, c, 18); continue; }
-                x[s] = fma(-l, m, x[s]);
-                if (s < ndesc) {
-                    const int p = d.pinv[r];
-                    if (p > j && p < T.lo) set_bit(sb, p - base);
-                    else report_internal(d.status, c, 19);
-                } else {
-                    set_bit(rb, s - ndesc);
+            // L(:,j) applied eight entries per lane at a time: all loads first
+            for (int q0 = lane; q0 < jc; q0 += 32 * DESC_PF) {
+                int rr[DESC_PF], ss[DESC_PF], pp[DESC_PF];
+                V ll[DESC_PF], xv[DESC_PF];
+#pragma unroll
+                for (int u = 0; u < DESC_PF; u++) {
+                    const int q = q0 + 32 * u;
+                    rr[u] = q < jc ? d.Li[jl + q] : -1;
+                    ll[u] = q < jc ? Lx[jl + q] : V(0);
+                }
+#pragma unroll
+                for (int u = 0; u < DESC_PF; u++) {
+                    ss[u] = rr[u] >= 0 ? slot_of(T, base, rr[u]) : -2;
+                    xv[u] = ss[u] >= 0 ? x[ss[u]] : V(0);
+                    pp[u] = (ss[u] >= 0 && ss[u] < ndesc) ? d.pinv[rr[u]] : -1;
+                }
+#pragma unroll
+                for (int u = 0; u < DESC_PF; u++) {
+                    const int s = ss[u];
+                    if (s == -2) continue;
+                    if (s < 0) { report_internal(d.status, c, 18); continue; }
+                    x[s] = fma(-ll[u], m, xv[u]);
+                    if (s < ndesc) {
+                        if (pp[u] > j && pp[u] < T.lo) set_bit(sb, pp[u] - base);
+                        else report_internal(d.status, c, 19);
+                    } else {
+                        set_bit(rb, s - ndesc);
+                    }
                 }
             }
             __syncwarp();
