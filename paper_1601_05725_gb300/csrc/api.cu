@@ -30,9 +30,11 @@ struct basker_s {
     std::vector<size_t> lv_smem;
     std::vector<int32_t *> lv_cols;
     std::vector<int32_t> lv_ncols;
-    std::vector<int32_t *> lv_dense;   // separators whose in-node phase runs as one dense elimination
-    std::vector<int32_t> lv_ndense;
-    std::vector<size_t> lv_dsmem;
+    // separators whose in-node phase runs as one dense elimination, by cluster size
+    // ([0]: one block, [1]: BK_DENSE_CLUSTER blocks)
+    std::vector<int32_t *> lv_dense[2];
+    std::vector<int32_t> lv_ndense[2];
+    std::vector<size_t> lv_dsmem[2];
     // redo lists (device buffers of n ints each) and their pinned staging
     int32_t *rd_tasks = nullptr, *rd_c0 = nullptr, *rd_cols = nullptr;
     int32_t *h_stage = nullptr;      // pinned, 3n + ntasks + 16 ints
@@ -343,18 +345,21 @@ int setup_device(basker_t h)
     h->lv_smem.assign(nl, 0);
     h->lv_cols.assign(nl, nullptr);
     h->lv_ncols.assign(nl, 0);
-    h->lv_dense.assign(nl, nullptr);
-    h->lv_ndense.assign(nl, 0);
-    h->lv_dsmem.assign(nl, 0);
+    for (int g = 0; g < 2; g++) {
+        h->lv_dense[g].assign(nl, nullptr);
+        h->lv_ndense[g].assign(nl, 0);
+        h->lv_dsmem[g].assign(nl, 0);
+    }
     for (size_t l = 0; l < nl; l++) {
-        std::vector<int32_t> ids, dense;
-        size_t sm = 0, dsm = 0;
+        std::vector<int32_t> ids, dense[2];
+        size_t sm = 0, dsm[2] = {0, 0};
         std::vector<int32_t> cols;
         for (int32_t t : pl.level_tasks[l]) {
             const bk_task &T = pl.tasks[(size_t)t];
             if (h->opt.factor_mode == 0 && bk_dense_node_eligible(T)) {
-                dense.push_back(t);
-                dsm = std::max(dsm, bk_dense_node_smem(T));
+                const int g = bk_dense_node_cluster(T) > 1 ? 1 : 0;
+                dense[g].push_back(t);
+                dsm[g] = std::max(dsm[g], bk_dense_node_smem(T));
             } else {
                 ids.push_back(t);
                 if (T.wsoff < 0) sm = std::max(sm, bk_task_smem_bytes(T));
@@ -364,9 +369,11 @@ int setup_device(basker_t h)
         }
         TRY(upload(h, &h->lv_tasks[l], ids));
         h->lv_ntasks[l] = (int32_t)ids.size();
-        TRY(upload(h, &h->lv_dense[l], dense));
-        h->lv_ndense[l] = (int32_t)dense.size();
-        h->lv_dsmem[l] = (dsm + 15) & ~(size_t)15;
+        for (int g = 0; g < 2; g++) {
+            TRY(upload(h, &h->lv_dense[g][l], dense[g]));
+            h->lv_ndense[g][l] = (int32_t)dense[g].size();
+            h->lv_dsmem[g][l] = (dsm[g] + 15) & ~(size_t)15;
+        }
         h->lv_smem[l] = (sm + 15) & ~(size_t)15;
         TRY(upload(h, &h->lv_cols[l], cols));
         h->lv_ncols[l] = (int32_t)cols.size();
@@ -490,9 +497,11 @@ int launch_full_gp(basker_t h, cudaStream_t s, int pref_mode)
             tend(h, s);
             h->launches++;
         }
-        if (h->lv_ndense[l] > 0) {
+        for (int g = 0; g < 2; g++) {
+            if (h->lv_ndense[g][l] == 0) continue;
             tbeg(h, KT_DENSE, s, 1);
-            bk_launch_dense_nodes(h->d, h->lv_dense[l], h->lv_ndense[l], h->lv_dsmem[l], tau, pref_mode, s);
+            bk_launch_dense_nodes(h->d, h->lv_dense[g][l], h->lv_ndense[g][l], h->lv_dsmem[g][l], tau, pref_mode,
+                                  g ? BK_DENSE_CLUSTER : 1, s);
             CU(cudaGetLastError());
             tend(h, s);
             h->launches++;
@@ -554,32 +563,39 @@ int launch_redo(basker_t h, cudaStream_t s)
             // separators: the descendant phase and one dense elimination with the
             // previous pivots preferred recompute each of them in two launches,
             // instead of rounds of column-by-column recomputation
-            std::vector<int32_t> dense, rest, cols;
+            std::vector<int32_t> dense[2], rest, cols;
+            size_t dsm[2] = {0, 0};
             for (int32_t t : active) {
                 const bk_task &T = pl.tasks[(size_t)t];
                 if (bk_dense_node_eligible(T)) {
-                    dense.push_back(t);
+                    const int g = bk_dense_node_cluster(T) > 1 ? 1 : 0;
+                    dense[g].push_back(t);
+                    dsm[g] = std::max(dsm[g], bk_dense_node_smem(T));
                     for (int32_t c = T.lo; c < T.hi; c++) cols.push_back(c);
                 } else {
                     rest.push_back(t);
                 }
             }
-            if (!dense.empty()) {
-                size_t dsm = 0;
-                for (int32_t t : dense) dsm = std::max(dsm, bk_dense_node_smem(pl.tasks[(size_t)t]));
+            if (!cols.empty()) {
                 CU(cudaStreamSynchronize(s));       // the staging buffer is reused
                 TRY(stage_upload(h, s, h->rd_cols, cols, 0));
-                TRY(stage_upload(h, s, h->rd_tasks, dense, (size_t)pl.n));
+                TRY(stage_upload(h, s, h->rd_tasks, dense[0], (size_t)pl.n));
+                TRY(stage_upload(h, s, h->rd_tasks + dense[0].size(), dense[1], (size_t)pl.n + dense[0].size()));
                 CU(cudaMemsetAsync(h->d.counter + 3, 0, sizeof(int32_t), s));
                 tbeg(h, KT_DESC, s, 1);
                 bk_launch_gp_desc(h->d, h->rd_cols, (int32_t)cols.size(), h->d.counter + 3, s);
                 CU(cudaGetLastError());
                 tend(h, s);
-                tbeg(h, KT_DENSE, s, 1);
-                bk_launch_dense_nodes(h->d, h->rd_tasks, (int32_t)dense.size(), (dsm + 15) & ~(size_t)15, tau, 1, s);
-                CU(cudaGetLastError());
-                tend(h, s);
-                h->launches += 2;
+                for (int g = 0; g < 2; g++) {
+                    if (dense[g].empty()) continue;
+                    tbeg(h, KT_DENSE, s, 1);
+                    bk_launch_dense_nodes(h->d, h->rd_tasks + (g ? dense[0].size() : 0), (int32_t)dense[g].size(),
+                                          (dsm[g] + 15) & ~(size_t)15, tau, 1, g ? BK_DENSE_CLUSTER : 1, s);
+                    CU(cudaGetLastError());
+                    tend(h, s);
+                    h->launches++;
+                }
+                h->launches++;
                 h->info.last_rounds++;
                 redone += (int32_t)cols.size();
                 const int st = read_status(h, s);

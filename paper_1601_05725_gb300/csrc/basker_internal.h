@@ -151,8 +151,13 @@ size_t bk_task_smem_bytes(const bk_task &t);
 #define BK_DENSE_SMEM (200 * 1024)
 size_t bk_dense_node_smem(const bk_task &t);
 bool bk_dense_node_eligible(const bk_task &t);
+// separators of at least BK_DENSE_CLUSTER_MIN columns run on a cluster of
+// BK_DENSE_CLUSTER blocks (columns dealt round-robin), smaller ones on one block
+#define BK_DENSE_CLUSTER 8
+#define BK_DENSE_CLUSTER_MIN 64
+int bk_dense_node_cluster(const bk_task &t);
 void bk_launch_dense_nodes(const bk_dev &d, const int32_t *task_ids, int32_t ntasks, size_t smem, double tau,
-                           int pref_mode, void *stream);
+                           int pref_mode, int cluster, void *stream);
 bool bk_task_fits_smem(const bk_task &t);
 
 // kernels (launchers), kernels_*.cu
