@@ -43,6 +43,7 @@ struct basker_s {
     int32_t epoch = 0, solve_epoch = 0, refno = 0;
     bool factored = false, ws_dirty = false, schedule_valid = true, order_is_symbolic = true;
     double gp_wall_ms = 0.0;     // wall time of the last complete Algorithm 1 pass (host clock)
+    bool sep_dense = false;      // refactorizations recompute every separator densely
     int32_t nrhs_cap = 0;
     double *d_vals = nullptr, *d_b = nullptr, *d_x = nullptr;
     int32_t stage_nrhs = 0;
@@ -298,6 +299,21 @@ int setup_device(basker_t h)
     TRY(upload(h, (int32_t **)&d.bmap, pl.bmap));
     TRY(upload(h, (int32_t **)&d.col_task, pl.col_task));
     TRY(dalloc(h, &d.Bx, (size_t)pl.nnz, true));
+    // every separator fits the dense elimination: refactorizations recompute the
+    // separators by it, after the stored-pattern pass and rounds of the ND leaves
+    // and BTF blocks (a separator's in-node chain is the long part of the
+    // stored-pattern pass, and any change below a separator redoes it anyway)
+    h->sep_dense = false;
+    if (h->opt.factor_mode == 0) {
+        bool all = true, any = false;
+        for (const bk_task &T : pl.tasks)
+            if (T.sp_lo < T.lo) {
+                any = true;
+                all = all && bk_dense_node_eligible(T);
+            }
+        h->sep_dense = any && all;
+    }
+    for (bk_task &T : pl.tasks) T.dense = (h->sep_dense && T.sp_lo < T.lo) ? 1 : 0;
     TRY(upload(h, &d.tasks, pl.tasks));
     TRY(dalloc(h, &d.prow, (size_t)n));
     TRY(dalloc(h, &d.pinv, (size_t)n));
@@ -548,7 +564,11 @@ int launch_redo(basker_t h, cudaStream_t s)
         std::vector<int32_t> active;
         for (int32_t t : pl.level_tasks[l]) {
             const bk_task &T = pl.tasks[(size_t)t];
-            if (desc_changed[(size_t)t]) {
+            if (T.dense) {
+                active.push_back(t);
+                start[(size_t)t] = T.lo;
+                flags[(size_t)t] = BK_DD_DESC;
+            } else if (desc_changed[(size_t)t]) {
                 active.push_back(t);
                 start[(size_t)t] = T.lo;
                 flags[(size_t)t] = BK_DD_DESC;
@@ -749,8 +769,8 @@ int factor_impl(basker_t h, const double *values, cudaStream_t s, bool refactor)
         if (st == BASKER_ERR_TIMEOUT) return st;
         h->info.last_repivot_columns = 0;
         h->info.last_rounds = 0;
-        if (h->h_status->static_fail) {
-            st = h->opt.refactor_switch == 2 ? BK_SWITCH_TO_FULL : launch_redo(h, s);
+        if (h->h_status->static_fail || h->sep_dense) {
+            st = (h->opt.refactor_switch == 2 && h->h_status->static_fail) ? BK_SWITCH_TO_FULL : launch_redo(h, s);
             if (st == BASKER_OK) st = read_status(h, s);
             h->schedule_valid = false;
             if (st == BK_SWITCH_TO_FULL) {

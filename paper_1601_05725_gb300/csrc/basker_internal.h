@@ -43,7 +43,8 @@ struct bk_task {
     int32_t level;             // height in the ND tree (0: leaves and small BTF blocks)
     int32_t node;              // ND node (postorder) or -1
     int32_t block;             // BTF block
-    int32_t pad;
+    int32_t dense;             // separators: refactorizations recompute it by the descendant
+                               // phase and the dense elimination (the stored-pattern pass skips it)
 };
 
 // Status word written by the kernels (device), read back once per call.

@@ -51,6 +51,11 @@ __global__ void __launch_bounds__(128) bk_static_kernel(bk_dev d, int32_t ncols,
             load_task(T, d.tasks + tid, lane);
             cur = tid;
         }
+        if (T.dense) {
+            // a separator recomputed afterwards by the dense elimination
+            if (lane == 0) st_release(d.done + c, epoch);
+            continue;
+        }
         bool ok = false, bad = false, broken = false;
         if (!pattern_column(d, T, tid, x, c, epoch, budget, tau, lane, true, 0, ok, bad, broken)) return;
         if (broken && lane == 0) report_internal(d.status, c, 41);
