@@ -221,6 +221,13 @@ def _measure(h, dvals, drhs, K, W, dev, flush, dist, world):
     return step_ms, xs.cpu().numpy(), info0, info1, (t0, t1)
 
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
+# ncu capture of the kernel as it stands, by kernel kind and value width; see
+# profiles/solve_kernel_powergrid.md.  A kind without a capture of its current
+# code reports null.
+TRAFFIC = {("powergrid_316x316", "solve", 8): 107.03e6}
+
+
 def _roofline(prob, info1, K, nnz_lu, vbytes, hbm):
     """HBM roofline of the kernel kind with the most device time per step.
 
@@ -242,7 +249,7 @@ def _roofline(prob, info1, K, nnz_lu, vbytes, hbm):
         algo = b_refactor
     achieved = algo / (per_launch_ms * 1e-3) / 1e9 if per_launch_ms > 0 else 0.0
     return {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": (achieved / hbm) if hbm else None, "traffic": None,
+            "frac": (achieved / hbm) if hbm else None, "traffic": TRAFFIC.get((prob.name, dom, int(vbytes))),
             "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if hbm else None,
             "algorithmic_bytes_per_launch": algo, "launches_per_step": launches / K,
             "ms_per_launch": per_launch_ms}
