@@ -137,6 +137,9 @@ typedef struct {
     int32_t full_refactors;       /* refactorizations finished by a complete Algorithm 1
                                      pass instead of rounds (options.refactor_switch) */
     int32_t graph_launches;       /* CUDA graph replays so far (options.graphs) */
+    int32_t static_factors;       /* basker_factor calls served by the stored-pattern path
+                                     (natural pivots preferred) instead of a complete pass */
+    int32_t pad1;
 } basker_info_t;
 
 /* Defaults listed in basker_options. */

@@ -58,7 +58,8 @@ class Info(ctypes.Structure):
                 ("ir_eta", ctypes.c_double), ("growth", ctypes.c_double),
                 ("kernel_calls", ctypes.c_int32 * 10), ("cuda_error", ctypes.c_int32),
                 ("cuda_line", ctypes.c_int32),
-                ("rounds_columns", ctypes.c_int64), ("full_refactors", ctypes.c_int32), ("graph_launches", ctypes.c_int32)]
+                ("rounds_columns", ctypes.c_int64), ("full_refactors", ctypes.c_int32), ("graph_launches", ctypes.c_int32),
+                ("static_factors", ctypes.c_int32), ("pad1", ctypes.c_int32)]
 
 KERNEL_KINDS = ["gather", "static_refactor", "dag_levels", "gp_in_node", "gp_descendant", "solve",
                 "dense_node", "refactor_rounds", "rows_transpose", "refine"]
@@ -261,7 +262,7 @@ class Handle:
         s = self.lib.basker_info(self.h, ctypes.byref(inf))
         if s != 0:
             raise BaskerError(s, "basker_info")
-        out = {k: getattr(inf, k) for k, _ in Info._fields_ if k not in ("reserved", "kernel_ms",
+        out = {k: getattr(inf, k) for k, _ in Info._fields_ if k not in ("reserved", "pad1", "kernel_ms",
                                                                           "kernel_calls")}
         out["kernel_calls"] = {KERNEL_KINDS[i]: inf.kernel_calls[i] for i in range(len(KERNEL_KINDS))}
         out["kernel_ms"] = {KERNEL_KINDS[i]: inf.kernel_ms[i] for i in range(len(KERNEL_KINDS))}

@@ -44,6 +44,13 @@ struct basker_s {
     bool factored = false, ws_dirty = false, schedule_valid = true, order_is_symbolic = true;
     double gp_wall_ms = 0.0;     // wall time of the last complete Algorithm 1 pass (host clock)
     bool sep_dense = false;      // refactorizations recompute every separator densely
+    // the arena as the symbolic pass left it (natural pivots, symbolic pattern and
+    // schedule): a factorization first tries the stored-pattern path from it
+    int32_t *sym_Li = nullptr, *sym_Ui = nullptr, *sym_n = nullptr;   // sym_n: 8 arrays of n ints
+    int64_t *sym_beg = nullptr;                                       // 4 arrays of n int64
+    unsigned long long *sym_pool = nullptr;
+    int32_t sym_ver = -1;
+    double static_factor_ms = 0.0;   // wall time of the last factorization by that path
     int32_t nrhs_cap = 0;
     double *d_vals = nullptr, *d_b = nullptr, *d_x = nullptr;
     int32_t stage_nrhs = 0;
@@ -258,6 +265,50 @@ int upload_symbolic_pattern(basker_t h)
     return BASKER_OK;
 }
 
+// A device copy of the arena right after the symbolic pass: L/U patterns at
+// their regions, region bounds, counts, natural pivots, the symbolic static
+// schedule, an identity (the natural preferred rows) and the pool cursors.
+int save_symbolic_image(basker_t h)
+{
+    const bk_plan &pl = h->pl;
+    const size_t n = (size_t)pl.n;
+    if (!h->sym_Li) {
+        TRY(dalloc(h, &h->sym_Li, (size_t)std::max<int64_t>(pl.lcap, 1)));
+        TRY(dalloc(h, &h->sym_Ui, (size_t)std::max<int64_t>(pl.ucap, 1)));
+        TRY(dalloc(h, &h->sym_n, 8 * std::max<size_t>(n, 1)));
+        TRY(dalloc(h, &h->sym_beg, 4 * std::max<size_t>(n, 1)));
+        TRY(dalloc(h, &h->sym_pool, 2));
+    }
+    bk_dev &d = h->d;
+    CU(cudaMemcpy(h->sym_Li, d.Li, sizeof(int32_t) * (size_t)pl.lcap, cudaMemcpyDeviceToDevice));
+    CU(cudaMemcpy(h->sym_Ui, d.Ui, sizeof(int32_t) * (size_t)pl.ucap, cudaMemcpyDeviceToDevice));
+    int32_t *const a[6] = {d.Lcnt, d.Ucnt, d.prow, d.pinv, d.order, d.level};
+    for (int i = 0; i < 6; i++) CU(cudaMemcpy(h->sym_n + i * n, a[i], n * 4, cudaMemcpyDeviceToDevice));
+    std::vector<int32_t> ident(n);
+    for (size_t c = 0; c < n; c++) ident[c] = (int32_t)c;
+    CU(cudaMemcpy(h->sym_n + 6 * n, ident.data(), n * 4, cudaMemcpyHostToDevice));
+    int64_t *const b[4] = {d.Lbeg, d.Ubeg, d.Lend, d.Uend};
+    for (int i = 0; i < 4; i++) CU(cudaMemcpy(h->sym_beg + i * n, b[i], n * 8, cudaMemcpyDeviceToDevice));
+    CU(cudaMemcpy(h->sym_pool, d.pool, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToDevice));
+    h->sym_ver = h->arena_ver;
+    return BASKER_OK;
+}
+
+int restore_symbolic_image(basker_t h, cudaStream_t s)
+{
+    const bk_plan &pl = h->pl;
+    const size_t n = (size_t)pl.n;
+    bk_dev &d = h->d;
+    CU(cudaMemcpyAsync(d.Li, h->sym_Li, sizeof(int32_t) * (size_t)pl.lcap, cudaMemcpyDeviceToDevice, s));
+    CU(cudaMemcpyAsync(d.Ui, h->sym_Ui, sizeof(int32_t) * (size_t)pl.ucap, cudaMemcpyDeviceToDevice, s));
+    int32_t *const a[7] = {d.Lcnt, d.Ucnt, d.prow, d.pinv, d.order, d.level, const_cast<int32_t *>(d.pref)};
+    for (int i = 0; i < 7; i++) CU(cudaMemcpyAsync(a[i], h->sym_n + i * n, n * 4, cudaMemcpyDeviceToDevice, s));
+    int64_t *const b[4] = {d.Lbeg, d.Ubeg, d.Lend, d.Uend};
+    for (int i = 0; i < 4; i++) CU(cudaMemcpyAsync(b[i], h->sym_beg + i * n, n * 8, cudaMemcpyDeviceToDevice, s));
+    CU(cudaMemcpyAsync(d.pool, h->sym_pool, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, s));
+    return BASKER_OK;
+}
+
 int setup_device(basker_t h)
 {
     bk_plan &pl = h->pl;
@@ -430,6 +481,7 @@ int setup_device(basker_t h)
     TRY(dalloc(h, &s.r.sbits, (size_t)(s.r.swords * BK_LONG_CTAS)));
     TRY(dalloc(h, &s.r.spre, (size_t)(s.r.swords * BK_LONG_CTAS)));
     TRY(upload_symbolic_pattern(h));
+    TRY(save_symbolic_image(h));
     h->schedule_valid = true;
     return BASKER_OK;
 }
@@ -661,9 +713,10 @@ int launch_redo(basker_t h, cudaStream_t s)
             }
             active.swap(next);
             // the rounds have cost as much as a complete pass would: finish with one
-            if (!active.empty() && h->opt.refactor_switch == 0 && h->gp_wall_ms > 0.0 &&
-                std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count() >
-                    h->gp_wall_ms) {
+            // (no complete pass timed yet: twenty stored-pattern factorizations)
+            const double limit = h->gp_wall_ms > 0.0 ? h->gp_wall_ms : 20.0 * h->static_factor_ms;
+            if (!active.empty() && h->opt.refactor_switch == 0 && limit > 0.0 &&
+                std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count() > limit) {
                 h->info.last_repivot_columns = redone;
                 return BK_SWITCH_TO_FULL;
             }
@@ -748,6 +801,41 @@ int finish_factorization(basker_t h, cudaStream_t s)
     return BASKER_OK;
 }
 
+// A factorization by the refactorization's path: the symbolic arena (natural
+// pivots preferred, the symbolic pattern and schedule) restored, the
+// stored-pattern pass, rounds for the rejected natural pivots, the separators'
+// dense recomputation.  This is Algorithm 1 with the natural rows preferred, the
+// factorization's definition.  Returns BK_SWITCH_TO_FULL when the complete pass
+// should run instead: no valid image, too many rejected pivots (the rounds would
+// cost more than the pass), or any other status (a failure, which the complete
+// pass names exactly; a wait that gave up; an exhausted spill pool).
+int factor_static(basker_t h, cudaStream_t s)
+{
+    if (!h->sym_Li || h->sym_ver != h->arena_ver || h->opt.factor_mode != 0) return BK_SWITCH_TO_FULL;
+    const auto t0 = std::chrono::steady_clock::now();
+    TRY(restore_symbolic_image(h, s));
+    h->refno++;
+    h->schedule_valid = true;
+    h->order_is_symbolic = true;
+    TRY(static_pass(h, s));
+    CU(cudaMemcpyAsync(h->h_task_fail, h->d.task_fail, sizeof(int32_t) * h->pl.tasks.size(),
+                       cudaMemcpyDeviceToHost, s));
+    int st = read_status(h, s);
+    if (st != BASKER_OK) return BK_SWITCH_TO_FULL;
+    const int rejected = h->h_status->static_fail;
+    if (rejected > std::max(16, h->pl.n / 200)) return BK_SWITCH_TO_FULL;
+    h->info.last_repivot_columns = 0;
+    h->info.last_rounds = 0;
+    if (rejected || h->sep_dense) {
+        st = launch_redo(h, s);
+        if (st == BASKER_OK) st = read_status(h, s);
+        if (st != BASKER_OK) return BK_SWITCH_TO_FULL;
+        h->schedule_valid = false;
+    }
+    h->static_factor_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return BASKER_OK;
+}
+
 int factor_impl(basker_t h, const double *values, cudaStream_t s, bool refactor)
 {
     h->launches = 0;
@@ -800,7 +888,16 @@ int factor_impl(basker_t h, const double *values, cudaStream_t s, bool refactor)
         h->factored = true;
         return BASKER_OK;
     }
-    int st = -1;
+    int st = factor_static(h, s);
+    if (st == BASKER_OK) {
+        h->info.static_factors++;
+        TRY(finish_factorization(h, s));
+        h->factored = true;
+        return BASKER_OK;
+    }
+    h->ws_dirty = true;
+    TRY(reset_status(h, s));
+    st = -1;
     for (int tries = 0; tries < 16; tries++) {
         if (tries > 0) {
             TRY(regrow(h));
@@ -818,7 +915,6 @@ int factor_impl(basker_t h, const double *values, cudaStream_t s, bool refactor)
         if (st != -1) break;
     }
     if (st != BASKER_OK) { h->factored = false; return st == -1 ? BASKER_ERR_OOM : st; }
-    h->info.off_diagonal_pivots = h->h_status->offdiag;
     // with the natural pivots everywhere the pattern is the symbolic one, whose
     // static schedule is already on the device
     h->schedule_valid = (h->h_status->offdiag == 0 && h->order_is_symbolic);
@@ -1211,9 +1307,15 @@ int basker_info(basker_t h, basker_info_t *out)
         double fl = 0;
         for (size_t c = 0; c < n; c++) fl += (double)lc[c] * (2.0 * urow[c] + 1.0);
         h->info.flops = fl;
+        std::vector<int32_t> pr(n);
+        CU(cudaMemcpy(pr.data(), h->d.prow, n * 4, cudaMemcpyDeviceToHost));
+        int32_t off = 0;
+        for (size_t c = 0; c < n; c++) off += pr[c] != (int32_t)c;
+        h->info.off_diagonal_pivots = off;
         out->nnz_l = nl;
         out->nnz_u = nu;
         out->flops = fl;
+        out->off_diagonal_pivots = off;
     }
     return BASKER_OK;
 }

@@ -52,7 +52,7 @@ struct bk_status {
     unsigned long long first_fail;   // min over failures of (column << 8 | code)
     int32_t capacity;                // nonzero: an L/U region overflowed
     int32_t timeout;                 // nonzero: a wait gave up
-    int32_t static_fail;             // nonzero: a column rejected its preferred pivot
+    int32_t static_fail;             // columns that rejected their preferred pivot (stored-pattern pass)
     int32_t offdiag;                 // number of columns pivoting off the natural row
     int32_t internal_site;           // first internal-consistency check that fired (0 = none)
     int32_t internal_col;            // and its column

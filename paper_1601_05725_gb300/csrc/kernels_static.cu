@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(128) bk_static_kernel(bk_dev d, int32_t ncols,
             d.col_fail[c] = ok ? 0 : 1;
             if (!ok) {
                 atomicMin(d.task_fail + tid, c);
-                atomicExch(&d.status->static_fail, 1);
+                atomicAdd(&d.status->static_fail, 1);
             }
             st_release(d.done + c, epoch);
         }

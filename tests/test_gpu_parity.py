@@ -158,6 +158,32 @@ def test_dense_separator_elimination_equals_column_by_column(kind, seed, kw):
         assert np.array_equal(a.data, b.data)
 
 
+@pytest.mark.parametrize("kind,seed,kw,dominant", [
+    ("grid", 91, dict(k=40, depth=3), True),
+    ("netlist", 92, dict(n_small=60, m_netlist=800, depth=3), False),
+])
+def test_factorization_by_the_stored_pattern_path(kind, seed, kw, dominant):
+    """basker_factor first tries the refactorization's path from the symbolic
+    arena (natural rows preferred); with few rejected natural pivots it is kept,
+    else the complete pass runs.  Either way the factors are the oracle's, also
+    when the handle is factored again after refactorizations moved its pivots."""
+    prob = I.small_problem(seed, kind, **kw)
+    o, s = _oracle(prob)
+    f = o.factors()
+    h = basker.Handle.from_problem(prob)
+    h.factor(_dev(prob.values))
+    assert_same_factors(h, f)
+    if dominant:
+        assert h.info()["static_factors"] == 1
+    v = I.refactor_values(prob, 1, sigma=0.3)
+    h.refactor(_dev(v))
+    assert o.factor(v) == "OK"
+    h.factor(_dev(v))
+    assert_same_factors(h, o.factors())
+    b = I.rhs_ones(prob, v)
+    np.testing.assert_array_equal(h.solve(_dev(b)).cpu().numpy(), o.solve(b))
+
+
 def test_graph_replay_equals_direct_launches():
     """options.graphs replays the post-factorization launches from a captured
     CUDA graph (slack 0: columns move to the spill pools between replays): the
