@@ -407,17 +407,13 @@ struct SweepCol {
     V diag;           // U(k,k) (backward only)
 };
 
+// Every lane loads the same words (one transaction): no shuffle waits for them, so
+// the loads stay in flight until the values are used a step later.
 template <typename V>
 __device__ __forceinline__ void sweep_meta(const bk_dev &d, int k, bool lower, int64_t &beg, int &cnt, int lane)
 {
-    int64_t b = 0;
-    int c = 0;
-    if (lane == 0) {
-        b = lower ? d.Lbeg[k] : d.Ubeg[k];
-        c = lower ? d.Lcnt[k] : d.Ucnt[k];
-    }
-    beg = __shfl_sync(BK_FULL, b, 0);
-    cnt = __shfl_sync(BK_FULL, c, 0);
+    beg = lower ? d.Lbeg[k] : d.Ubeg[k];
+    cnt = lower ? d.Lcnt[k] : d.Ucnt[k];
 }
 
 template <typename V>
@@ -437,9 +433,10 @@ __device__ __forceinline__ void sweep_read(const bk_dev &d, const bk_solve_dev &
         if (t >= col.cnt) continue;
         const int64_t e = lower ? beg + t : beg + col.cnt - 1 - t;
         const int i = lower ? s.r.Ls[e] : d.Ui[e];
+        const V v = lower ? Lx[e] : Ux[e];           // read with the index, not after it
         if (lower ? i < hi : i >= lo) {
             col.row[u] = i - lo;
-            col.val[u] = lower ? Lx[e] : Ux[e];
+            col.val[u] = v;
         }
     }
 }
