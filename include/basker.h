@@ -86,7 +86,14 @@ typedef struct {
     int graphs;                   /* nonzero (default): the launches that follow every
                                      factorization are replayed from a CUDA graph captured
                                      once per L/U arena; 0: launched one by one */
-    int reserved[2];
+    int symbolic_mode;            /* 0 (default): basker_symbolic sizes L and U by a structural
+                                     Gilbert-Peierls pass under the natural pivots (exact
+                                     counts, and the pattern and schedule that let
+                                     basker_factor take the refactorization's path);
+                                     1: by Algorithm 3's elimination-tree counts of the
+                                     symmetric structure (upper bounds, no pattern stored,
+                                     cheaper; every basker_factor runs the complete pass) */
+    int reserved[1];
 } basker_options;
 
 typedef struct {
@@ -145,6 +152,19 @@ typedef struct {
 /* Defaults listed in basker_options. */
 void basker_default_options(basker_options *opt);
 
+/* The symbolic counts alone, on the host (no device, no handle): the same
+ * arguments as basker_symbolic, then mode (0: the structural pass under the
+ * natural pivots, exact for those pivots; 1: Algorithm 3's elimination-tree
+ * counts of the symmetric structure, Sec. III-C, an upper bound of mode 0's) and
+ * two host arrays of n ints (either may be NULL) receiving each column's L count
+ * (strictly lower entries) and U count (diagonal included).  Errors: INVALID_ARG,
+ * NOT_BTF, BAD_ND; the arrays are untouched on error. */
+int basker_symbolic_counts(int32_t n, const int32_t *colptr, const int32_t *rowind,
+                           const int32_t *P, const int32_t *Q,
+                           int32_t nblocks, const int32_t *block_ptr,
+                           int32_t nd_block, int32_t nd_leaves, const int32_t *nd_node_ptr,
+                           int mode, int32_t *l_count, int32_t *u_count);
+
 /* Analyse a pattern (host arrays; Sec. III-A/III-C orderings are inputs).
  *   n, colptr, rowind: pattern of A (host).
  *   P, Q: host, new -> old permutations putting A in BTF order.
@@ -155,9 +175,9 @@ void basker_default_options(basker_options *opt);
  *     the ND nodes in postorder (left subtree, right subtree, separator), from
  *     block_ptr[nd_block] to block_ptr[nd_block+1]; nodes may be empty.
  *   opt: options (NULL = defaults).  out: receives the handle.
- * Checks the BTF and ND invariants, runs the structural pass (capacities, the
- * level schedule of Algorithm 4's dependency tree), allocates the device arena
- * and uploads the plan.  Errors: INVALID_ARG, NOT_BTF, BAD_ND, OOM, CUDA;
+ * Checks the BTF and ND invariants, runs the structural pass or Algorithm 3's
+ * counts (options.symbolic_mode: capacities, the level schedule of Algorithm 4's
+ * dependency tree), allocates the device arena and uploads the plan.  Errors: INVALID_ARG, NOT_BTF, BAD_ND, OOM, CUDA;
  * *out is NULL on error. */
 int basker_symbolic(int32_t n, const int32_t *colptr, const int32_t *rowind,
                     const int32_t *P, const int32_t *Q,

@@ -39,7 +39,7 @@ class Options(ctypes.Structure):
                 ("wait_budget_cycles", ctypes.c_longlong), ("factor_mode", ctypes.c_int),
                 ("timing", ctypes.c_int), ("precision", ctypes.c_int), ("ir_max_iter", ctypes.c_int),
                 ("ir_tol", ctypes.c_double), ("growth_limit", ctypes.c_double), ("refactor_switch", ctypes.c_int),
-                ("graphs", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
+                ("graphs", ctypes.c_int), ("symbolic_mode", ctypes.c_int), ("reserved", ctypes.c_int * 1)]
 
 
 class Info(ctypes.Structure):
@@ -67,7 +67,8 @@ KERNEL_KINDS = ["gather", "static_refactor", "dag_levels", "gp_in_node", "gp_des
 
 EXPORTED = ["basker_default_options", "basker_symbolic", "basker_factor", "basker_refactor",
             "basker_solve", "basker_refactor_solve_host", "basker_info", "basker_export",
-            "basker_free", "basker_strerror", "basker_solve_noalloc", "basker_autotune"]
+            "basker_free", "basker_strerror", "basker_solve_noalloc", "basker_autotune",
+            "basker_symbolic_counts"]
 
 
 def library_path() -> str:
@@ -109,8 +110,28 @@ def load(path: Optional[str] = None):
         L.basker_free.restype = None
         L.basker_strerror.argtypes = [ctypes.c_int]
         L.basker_strerror.restype = ctypes.c_char_p
+        L.basker_symbolic_counts.argtypes = [i32, vp, vp, vp, vp, i32, vp, i32, i32, vp, ctypes.c_int, vp, vp]
+        L.basker_symbolic_counts.restype = ctypes.c_int
         _lib = L
         return L
+
+
+def symbolic_counts(prob, mode: int = 0):
+    """basker_symbolic_counts on the host: per-column L and U counts of a problem's
+    pattern (mode 0: structural pass under the natural pivots; 1: Algorithm 3's
+    elimination-tree counts).  Needs no GPU."""
+    L = load()
+    arrs = [_i32(prob.colptr), _i32(prob.rowind), _i32(prob.P), _i32(prob.Q), _i32(prob.block_ptr),
+            _i32(prob.nd_node_ptr if prob.nd_block >= 0 else [0])]
+    n = int(prob.n)
+    lc = np.zeros(max(n, 1), np.int32)
+    uc = np.zeros(max(n, 1), np.int32)
+    s = L.basker_symbolic_counts(n, *[_np_ptr(a) for a in arrs[:4]], len(arrs[4]) - 1, _np_ptr(arrs[4]),
+                                 int(prob.nd_block), int(prob.nd_leaves), _np_ptr(arrs[5]), int(mode),
+                                 _np_ptr(lc), _np_ptr(uc))
+    if s != 0:
+        raise BaskerError(s, "basker_symbolic_counts")
+    return lc[:n], uc[:n]
 
 
 def default_options() -> Options:
@@ -146,9 +167,11 @@ class Handle:
                  factor_mode: int = 0, timing: bool = False, precision: int = 0,
                  ir_max_iter: Optional[int] = None, ir_tol: Optional[float] = None,
                  growth_limit: Optional[float] = None, refactor_switch: Optional[int] = None,
-                 graphs: Optional[bool] = None):
+                 graphs: Optional[bool] = None, symbolic_mode: Optional[int] = None):
         self.lib = load()
         opt = default_options()
+        if symbolic_mode is not None:
+            opt.symbolic_mode = int(symbolic_mode)
         if graphs is not None:
             opt.graphs = 1 if graphs else 0
         if refactor_switch is not None:

@@ -245,6 +245,13 @@ int alloc_factors(basker_t h)
 int upload_symbolic_pattern(basker_t h)
 {
     bk_plan &pl = h->pl;
+    if (pl.counts_only) {
+        // no pattern or schedule: the first factorization runs the complete pass
+        // and computes the schedule of its pattern
+        if (!h->d.iorder) TRY(upload(h, (int32_t **)&h->d.iorder, pl.iorder));
+        h->order_is_symbolic = false;
+        return BASKER_OK;
+    }
     std::vector<int32_t> Li((size_t)pl.lcap, 0), Ui((size_t)pl.ucap, 0);
     int64_t l = 0, u = 0;
     for (int32_t c = 0; c < pl.n; c++) {
@@ -481,8 +488,8 @@ int setup_device(basker_t h)
     TRY(dalloc(h, &s.r.sbits, (size_t)(s.r.swords * BK_LONG_CTAS)));
     TRY(dalloc(h, &s.r.spre, (size_t)(s.r.swords * BK_LONG_CTAS)));
     TRY(upload_symbolic_pattern(h));
-    TRY(save_symbolic_image(h));
-    h->schedule_valid = true;
+    if (!pl.counts_only) TRY(save_symbolic_image(h));
+    h->schedule_valid = !pl.counts_only;
     return BASKER_OK;
 }
 
@@ -1138,6 +1145,22 @@ const char *basker_strerror(int status)
     }
 }
 
+int basker_symbolic_counts(int32_t n, const int32_t *colptr, const int32_t *rowind, const int32_t *P,
+                           const int32_t *Q, int32_t nblocks, const int32_t *block_ptr, int32_t nd_block,
+                           int32_t nd_leaves, const int32_t *nd_node_ptr, int mode, int32_t *l_count,
+                           int32_t *u_count)
+{
+    if (mode < 0 || mode > 1) return BASKER_ERR_INVALID_ARG;
+    bk_plan pl;
+    int32_t bad = -1;
+    const int st = bk_plan_build(n, colptr, rowind, P, Q, nblocks, block_ptr, nd_block, nd_leaves, nd_node_ptr,
+                                 0.0, pl, &bad, mode);
+    if (st != BASKER_OK) return st;
+    if (l_count) std::copy(pl.sLcnt.begin(), pl.sLcnt.end(), l_count);
+    if (u_count) std::copy(pl.sUcnt.begin(), pl.sUcnt.end(), u_count);
+    return BASKER_OK;
+}
+
 int basker_symbolic(int32_t n, const int32_t *colptr, const int32_t *rowind, const int32_t *P,
                     const int32_t *Q, int32_t nblocks, const int32_t *block_ptr, int32_t nd_block,
                     int32_t nd_leaves, const int32_t *nd_node_ptr, const basker_options *opt,
@@ -1151,7 +1174,8 @@ int basker_symbolic(int32_t n, const int32_t *colptr, const int32_t *rowind, con
     if (opt) h->opt = *opt;
     if (!(h->opt.tau > 0.0 && h->opt.tau <= 1.0) || h->opt.slack < 0.0 || h->opt.wait_budget_cycles <= 0 ||
         h->opt.factor_mode < 0 || h->opt.factor_mode > 1 || h->opt.precision < 0 || h->opt.precision > 2 ||
-        h->opt.refactor_switch < 0 || h->opt.refactor_switch > 2 ||
+        h->opt.refactor_switch < 0 || h->opt.refactor_switch > 2 || h->opt.symbolic_mode < 0 ||
+        h->opt.symbolic_mode > 1 ||
         (h->opt.precision >= 1 && (h->opt.ir_max_iter < 1 || !(h->opt.ir_tol > 0.0) || !(h->opt.growth_limit > 0.0)))) {
         delete h;
         return BASKER_ERR_INVALID_ARG;
@@ -1171,7 +1195,7 @@ int basker_symbolic(int32_t n, const int32_t *colptr, const int32_t *rowind, con
     }
     int32_t bad = -1;
     int st = bk_plan_build(n, colptr, rowind, P, Q, nblocks, block_ptr, nd_block, nd_leaves, nd_node_ptr,
-                           h->opt.slack, h->pl, &bad);
+                           h->opt.slack, h->pl, &bad, h->opt.symbolic_mode);
     if (st == BASKER_OK) st = setup_device(h);
     if (st != BASKER_OK) {
         h->info.failed_column = bad;

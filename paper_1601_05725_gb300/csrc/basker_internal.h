@@ -137,6 +137,7 @@ struct bk_plan {
     int32_t dd_words = 0;                             // shared-memory reach bitmaps per warp (words)
     int32_t max_space = 0;
     int32_t symbolic_singular = -1;                   // first column without a structural pivot
+    bool counts_only = false;                         // Algorithm 3's counts: no pattern, no schedule
     double slack = 0.5;
 };
 
@@ -144,7 +145,7 @@ struct bk_plan {
 int bk_plan_build(int32_t n, const int32_t *colptr, const int32_t *rowind, const int32_t *P,
                   const int32_t *Q, int32_t nblocks, const int32_t *block_ptr, int32_t nd_block,
                   int32_t nd_leaves, const int32_t *nd_node_ptr, double slack, bk_plan &plan,
-                  int32_t *bad_col);
+                  int32_t *bad_col, int mode = 0);
 void bk_plan_layout(bk_plan &plan);                      // L/U regions, workspaces
 void bk_plan_regrow(bk_plan &plan, const int32_t *over); // after an overflow (per-column flags)
 size_t bk_task_smem_bytes(const bk_task &t);

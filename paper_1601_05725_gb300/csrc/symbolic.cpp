@@ -5,11 +5,12 @@
 // every entry joins two nodes on one root path (the separators of Sec. III-C
 // disconnect their halves), builds the tasks of the level schedule (Algorithm 4's
 // dependency tree: leaves and small BTF blocks first, then separators by height),
-// and runs a structural Gilbert-Peierls pass under the preferred (natural) pivots
-// to size every column's L and U storage (the role of Algorithms 2 and 3, which
-// estimate counts; this pass computes them exactly for those pivots and adds
-// slack for pivoting).  The pass uses symmetric pruning of the reach graph
-// (Eisenstat and Liu) so that its cost stays near |L+U|.
+// and sizes every column's L and U storage: by default with a structural
+// Gilbert-Peierls pass under the preferred (natural) pivots (exact counts for
+// those pivots, plus the pattern and a static schedule for the first
+// factorization; symmetric pruning of the reach graph, Eisenstat and Liu, keeps
+// its cost near |L+U|), or with Algorithm 3's elimination-tree counts, which store
+// no pattern (options.symbolic_mode 1).  Slack covers pivoting.
 #include <algorithm>
 #include <cstring>
 #include <numeric>
@@ -59,10 +60,89 @@ size_t bk_task_smem_bytes(const bk_task &t)
 
 bool bk_task_fits_smem(const bk_task &t) { return bk_task_smem_bytes(t) <= bk_gp_smem_limit(); }
 
+// Algorithm 3's counts (Sec. III-C, parallel symbolic factorization), per BTF
+// diagonal block: the elimination tree of the symmetric structure B_dd + B_dd^T
+// (one tree for the whole ND block: its separators are the ancestors of their
+// subtrees, so the tree holds the leaves' trees, the L_ki rows and the U_ij
+// columns), then for every column c the row subtree of c (the nodes met walking
+// up from each i < c adjacent to c, stopping at a node already met for c).  Its
+// size + 1 is U(:,c)'s count; the number of later row subtrees that contain a
+// node j is L(:,j)'s count.  These are the counts of the Cholesky factor of the
+// symmetric structure, which contains the LU pattern of the natural pivots, so
+// they never fall below the structural pass's counts (equal for a symmetric
+// pattern); the paper's interval estimates of the upper tree levels (dense between
+// the minimum and the maximum row) are looser than these exact tree counts, which
+// cost O(|L + U|) node visits here.  No pattern is stored.
+static void etree_counts(bk_plan &pl)
+{
+    const int32_t n = pl.n;
+    pl.sLcnt.assign((size_t)n, 0);
+    pl.sUcnt.assign((size_t)n, 0);
+    // lower adjacency of the symmetric structure inside each diagonal block:
+    // for each column c the rows i < c with B(i,c) != 0 or B(c,i) != 0
+    std::vector<int32_t> blk((size_t)n);
+    for (int32_t d = 0; d < pl.nblocks; d++)
+        for (int32_t i = pl.block_ptr[(size_t)d]; i < pl.block_ptr[(size_t)d + 1]; i++) blk[(size_t)i] = d;
+    std::vector<int64_t> ap((size_t)n + 1, 0);
+    for (int32_t c = 0; c < n; c++)
+        for (int32_t e = pl.dstart[(size_t)c]; e < pl.Bp[(size_t)c + 1]; e++) {
+            const int32_t r = pl.Bi[(size_t)e];
+            if (r == c || blk[(size_t)r] != blk[(size_t)c]) continue;
+            ap[(size_t)std::max(r, c) + 1]++;
+        }
+    for (int32_t c = 0; c < n; c++) ap[(size_t)c + 1] += ap[(size_t)c];
+    std::vector<int32_t> ai((size_t)ap[(size_t)n]);
+    std::vector<int64_t> fill(ap.begin(), ap.end() - 1);
+    for (int32_t c = 0; c < n; c++)
+        for (int32_t e = pl.dstart[(size_t)c]; e < pl.Bp[(size_t)c + 1]; e++) {
+            const int32_t r = pl.Bi[(size_t)e];
+            if (r == c || blk[(size_t)r] != blk[(size_t)c]) continue;
+            ai[(size_t)fill[(size_t)std::max(r, c)]++] = std::min(r, c);
+        }
+    // elimination tree (Liu's algorithm with path compression)
+    std::vector<int32_t> parent((size_t)n, -1), anc((size_t)n, -1);
+    for (int32_t c = 0; c < n; c++)
+        for (int64_t e = ap[(size_t)c]; e < ap[(size_t)c + 1]; e++) {
+            int32_t r = ai[(size_t)e];
+            while (anc[(size_t)r] != -1 && anc[(size_t)r] != c) {
+                const int32_t t = anc[(size_t)r];
+                anc[(size_t)r] = c;
+                r = t;
+            }
+            if (anc[(size_t)r] == -1) {
+                anc[(size_t)r] = c;
+                parent[(size_t)r] = c;
+            }
+        }
+    // row subtrees
+    std::vector<int32_t> mark((size_t)n, -1);
+    int64_t nl = 0, nu = 0;
+    for (int32_t c = 0; c < n; c++) {
+        int32_t uc = 1;
+        mark[(size_t)c] = c;
+        for (int64_t e = ap[(size_t)c]; e < ap[(size_t)c + 1]; e++)
+            for (int32_t r = ai[(size_t)e]; r >= 0 && mark[(size_t)r] != c; r = parent[(size_t)r]) {
+                mark[(size_t)r] = c;
+                uc++;
+                pl.sLcnt[(size_t)r]++;
+            }
+        pl.sUcnt[(size_t)c] = uc;
+        nu += uc;
+    }
+    for (int32_t c = 0; c < n; c++) nl += pl.sLcnt[(size_t)c];
+    pl.nnz_l_sym = nl;
+    pl.nnz_u_sym = nu;
+    pl.sLi.clear();
+    pl.sUi.clear();
+    pl.sprow.clear();
+    pl.slevel.clear();
+    pl.sorder.clear();
+}
+
 int bk_plan_build(int32_t n, const int32_t *colptr, const int32_t *rowind, const int32_t *P,
                   const int32_t *Q, int32_t nblocks, const int32_t *block_ptr, int32_t nd_block,
                   int32_t nd_leaves, const int32_t *nd_node_ptr, double slack, bk_plan &pl,
-                  int32_t *bad_col)
+                  int32_t *bad_col, int mode)
 {
     *bad_col = -1;
     if (n < 0 || nblocks < 0 || (n > 0 && nblocks < 1) || !colptr || (n > 0 && (!P || !Q || !block_ptr)))
@@ -205,16 +285,34 @@ int bk_plan_build(int32_t n, const int32_t *colptr, const int32_t *rowind, const
     pl.iorder.clear();
     pl.iorder.reserve((size_t)n);
     for (const auto &lt : pl.level_tasks) {
+        auto len = [&](int32_t t) { return pl.tasks[(size_t)t].c1 - pl.tasks[(size_t)t].c0; };
         int32_t longest = 0;
-        for (int32_t t : lt) longest = std::max(longest, pl.tasks[(size_t)t].c1 - pl.tasks[(size_t)t].c0);
-        for (int32_t q = 0; q < longest; q++)
-            for (int32_t t : lt) {
-                const bk_task &T = pl.tasks[(size_t)t];
-                if (q < T.c1 - T.c0) pl.iorder.push_back(T.c0 + q);
+        for (int32_t t : lt) longest = std::max(longest, len(t));
+        // rounds q = 0 .. longest - 1: the tasks longer than q in the level's order;
+        // the list of active tasks shrinks as they end, so the work is O(columns)
+        std::vector<int32_t> active(lt.begin(), lt.end());
+        for (int32_t q = 0; q < longest; q++) {
+            size_t w = 0;
+            for (size_t i = 0; i < active.size(); i++) {
+                const int32_t t = active[i];
+                if (q < len(t)) {
+                    pl.iorder.push_back(pl.tasks[(size_t)t].c0 + q);
+                    active[w++] = t;
+                }
             }
+            active.resize(w);
+        }
     }
     pl.max_space = 0;
     for (auto &T : pl.tasks) pl.max_space = std::max(pl.max_space, T.space);
+
+    pl.counts_only = mode == 1;
+    if (mode == 1) {
+        etree_counts(pl);
+        pl.symbolic_singular = -1;
+        bk_plan_layout(pl);
+        return BASKER_OK;
+    }
 
     // ---- structural Gilbert-Peierls pass under the preferred pivots
     std::vector<int32_t> pinv((size_t)n, -1), mark((size_t)n, -1);
