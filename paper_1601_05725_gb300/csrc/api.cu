@@ -51,6 +51,7 @@ struct basker_s {
     unsigned long long *sym_pool = nullptr;
     int32_t sym_ver = -1;
     double static_factor_ms = 0.0;   // wall time of the last factorization by that path
+    bool static_factor_off = false;  // that path rejected too many natural pivots once: not tried again
     int32_t nrhs_cap = 0;
     double *d_vals = nullptr, *d_b = nullptr, *d_x = nullptr;
     int32_t stage_nrhs = 0;
@@ -814,11 +815,12 @@ int finish_factorization(basker_t h, cudaStream_t s)
 // dense recomputation.  This is Algorithm 1 with the natural rows preferred, the
 // factorization's definition.  Returns BK_SWITCH_TO_FULL when the complete pass
 // should run instead: no valid image, too many rejected pivots (the rounds would
-// cost more than the pass), or any other status (a failure, which the complete
+// cost more than the pass; the handle then stops trying), or any other status (a failure, which the complete
 // pass names exactly; a wait that gave up; an exhausted spill pool).
 int factor_static(basker_t h, cudaStream_t s)
 {
-    if (!h->sym_Li || h->sym_ver != h->arena_ver || h->opt.factor_mode != 0) return BK_SWITCH_TO_FULL;
+    if (!h->sym_Li || h->sym_ver != h->arena_ver || h->opt.factor_mode != 0 || h->static_factor_off)
+        return BK_SWITCH_TO_FULL;
     const auto t0 = std::chrono::steady_clock::now();
     TRY(restore_symbolic_image(h, s));
     h->refno++;
@@ -830,7 +832,10 @@ int factor_static(basker_t h, cudaStream_t s)
     int st = read_status(h, s);
     if (st != BASKER_OK) return BK_SWITCH_TO_FULL;
     const int rejected = h->h_status->static_fail;
-    if (rejected > std::max(16, h->pl.n / 200)) return BK_SWITCH_TO_FULL;
+    if (rejected > std::max(16, h->pl.n / 200)) {
+        h->static_factor_off = true;         // this pattern's values do not keep their natural pivots
+        return BK_SWITCH_TO_FULL;
+    }
     h->info.last_repivot_columns = 0;
     h->info.last_rounds = 0;
     if (rejected || h->sep_dense) {
