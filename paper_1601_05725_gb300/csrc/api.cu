@@ -1325,16 +1325,13 @@ int basker_info(basker_t h, basker_info_t *out)
         for (size_t c = 0; c < n; c++) { nl += lc[c]; nu += uc[c]; }
         h->info.nnz_l = nl;
         h->info.nnz_u = nu;
-        // flops: sum_j l_j (2 u_j + 1), u_j = entries right of the diagonal in row j of U
-        std::vector<int64_t> ub(n + 1);
-        CU(cudaMemcpy(ub.data(), h->d.Ubeg, (n + 1) * 8, cudaMemcpyDeviceToHost));
-        std::vector<int32_t> ui((size_t)h->d.upool_end);
-        CU(cudaMemcpy(ui.data(), h->d.Ui, ui.size() * 4, cudaMemcpyDeviceToHost));
-        std::vector<int32_t> urow(n, 0);
-        for (size_t c = 0; c < n; c++)
-            for (int32_t k = 0; k + 1 < uc[c]; k++) urow[(size_t)ui[(size_t)(ub[c] + k)]]++;
+        // flops: sum_j l_j (2 u_j + 1), u_j = entries right of the diagonal in row j
+        // of U, from the row starts of the factors by rows (rebuilt after every
+        // factorization)
+        std::vector<int64_t> urp(n + 1);
+        CU(cudaMemcpy(urp.data(), h->sd.r.Urp, (n + 1) * 8, cudaMemcpyDeviceToHost));
         double fl = 0;
-        for (size_t c = 0; c < n; c++) fl += (double)lc[c] * (2.0 * urow[c] + 1.0);
+        for (size_t c = 0; c < n; c++) fl += (double)lc[c] * (2.0 * (double)(urp[c + 1] - urp[c]) + 1.0);
         h->info.flops = fl;
         std::vector<int32_t> pr(n);
         CU(cudaMemcpy(pr.data(), h->d.prow, n * 4, cudaMemcpyDeviceToHost));

@@ -72,6 +72,24 @@ def test_factor_matches_oracle(kind, seed, kw, tau):
     assert_same_factors(h, o.factors())
 
 
+def test_info_counts_and_flops_match_the_oracle():
+    prob = I.small_problem(17, "netlist", n_small=60, m_netlist=500, depth=3)
+    o, s = _oracle(prob)
+    f = o.factors()
+    h = basker.Handle.from_problem(prob)
+    for values in (prob.values, I.refactor_values(prob, 1, sigma=0.3)):
+        if values is not prob.values:
+            assert o.factor(values, pref=f.prow) == "OK"
+            f = o.factors()
+            h.refactor(_dev(values))
+        else:
+            h.factor(_dev(values))
+        inf = h.info()
+        assert inf["nnz_l"] == f.L.nnz and inf["nnz_u"] == f.U.nnz
+        assert inf["flops"] == H.flops(f)
+        assert inf["off_diagonal_pivots"] == int((f.prow != np.arange(prob.n)).sum())
+
+
 def test_config1_factor_solve():
     prob = I.config1()
     o, s = _oracle(prob)
