@@ -21,7 +21,7 @@ struct basker_s {
     bk_plan pl;
     bk_solve_plan sp;
     int device = 0;
-    std::vector<void *> allocs;
+    std::vector<std::pair<void *, size_t>> allocs;   // device allocations and their bytes
     bk_dev d{};
     bk_solve_dev sd{};
     // level lists of a full factorization (device)
@@ -145,7 +145,7 @@ int dalloc(basker_t h, T **p, size_t count, bool zero = false)
         cudaGetLastError();
         return BASKER_ERR_OOM;
     }
-    h->allocs.push_back((void *)*p);
+    h->allocs.emplace_back((void *)*p, bytes);
     h->device_bytes += (int64_t)bytes;
     if (zero && cudaMemset(*p, 0, bytes) != cudaSuccess) return BASKER_ERR_CUDA;
     return BASKER_OK;
@@ -160,8 +160,13 @@ std::mutex g_capture_mu;
 void dfree(basker_t h, void *p)
 {
     if (!p) return;
-    auto it = std::find(h->allocs.begin(), h->allocs.end(), p);
-    if (it != h->allocs.end()) h->allocs.erase(it);
+    auto it = std::find_if(h->allocs.begin(), h->allocs.end(), [p](const std::pair<void *, size_t> &a) {
+        return a.first == p;
+    });
+    if (it != h->allocs.end()) {
+        h->device_bytes -= (int64_t)it->second;
+        h->allocs.erase(it);
+    }
     std::lock_guard<std::mutex> lk(g_capture_mu);
     cudaFree(p);
 }
@@ -1476,7 +1481,7 @@ void basker_free(basker_t h)
     {
         std::lock_guard<std::mutex> lk(g_capture_mu);
         cudaDeviceSynchronize();
-        for (void *p : h->allocs) cudaFree(p);
+        for (auto &a : h->allocs) cudaFree(a.first);
     }
     if (h->h_stage) cudaFreeHost(h->h_stage);
     if (h->h_status) cudaFreeHost(h->h_status);
