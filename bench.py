@@ -51,6 +51,23 @@ def _args():
     return ap.parse_args()
 
 
+def max_over_ranks(x: float, world: int, dev) -> float:
+    """The largest x over the ranks (all_reduce MAX; the job's time is its slowest
+    rank's).  One rank: x."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: int, world: int, seconds: float) -> float:
+    """Whole-job throughput: the units every rank processed over the slowest rank's time."""
+    return world * units_per_rank / seconds
+
+
 def _dist():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -300,15 +317,11 @@ def run_ours(args):
         h.factor(torch.as_tensor(prob.values, device=dev))
         tuned = h.autotune(dvals[0], drhs[0]) if args.autotune else None
         step_ms, X, info0, info1, span = _measure(h, dvals, drhs, K, W, dev, flush, dist, world)
-        total_s = sum(step_ms) / 1e3
-        if world > 1:
-            t = torch.tensor([total_s], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_s = float(t.item())
+        total_s = max_over_ranks(sum(step_ms) / 1e3, world, dev)
         etas = [_eta(prob, vals[(W + i) % 10], X[i], rhs[(W + i) % 10]) for i in range(K)]
         nnz_lu = info1["nnz_l"] + info1["nnz_u"]
         forms[name] = {
-            "value": world * K / total_s, "ms_per_step": 1e3 * total_s / K,
+            "value": job_rate(K, world, total_s), "ms_per_step": 1e3 * total_s / K,
             "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
             "max_backward_error": max(etas), "valid_steps": int(sum(e <= 1e-12 for e in etas)),
             "gpu_launches": int(info1["kernel_launches"] - info0["kernel_launches"]),
@@ -340,10 +353,7 @@ def run_ours(args):
     # factorizations (from scratch, natural rows preferred) of the same value
     # sequence with the headline form's handle, device-timed like the steps
     fac_ms = _measure_factor(h, dvals, min(K, 10), dev, flush)
-    if world > 1:
-        t = torch.tensor([e2e_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
+    e2e_total = max_over_ranks(e2e_total, world, dev)
     if rank != 0:
         dist.destroy_process_group() if world > 1 else None
         return
@@ -357,7 +367,7 @@ def run_ours(args):
         "config": _config(prob), "form": head,
         "p50_ms": hf["p50_ms"], "p99_ms": hf["p99_ms"],
         "max_backward_error": hf["max_backward_error"], "valid_steps": hf["valid_steps"],
-        "e2e": {"value": world * K / e2e_total, "unit": UNIT,
+        "e2e": {"value": job_rate(K, world, e2e_total), "unit": UNIT,
                 "h2d_bytes_per_step": int(8 * prob.nnz + 8 * prob.n), "d2h_bytes_per_step": int(8 * prob.n)},
         "gpu_launches": hf["gpu_launches"],
         "kernel_ms_per_step": hf["kernel_ms_per_step"],
