@@ -644,10 +644,12 @@ int launch_redo(basker_t h, cudaStream_t s)
             }
         }
         for (int32_t t : active) mark_ancestors((size_t)t);
-        if (l > 0 && h->opt.factor_mode == 0 && !active.empty()) {
+        if (l > 0 && h->sep_dense && !active.empty()) {
             // separators: the descendant phase and one dense elimination with the
             // previous pivots preferred recompute each of them in two launches,
-            // instead of rounds of column-by-column recomputation
+            // instead of rounds of column-by-column recomputation.  All or none:
+            // the rounds of a separator rely on the change markers that rounds
+            // leave on the columns below it, which the dense path does not set.
             std::vector<int32_t> dense[2], rest, cols;
             size_t dsm[2] = {0, 0};
             for (int32_t t : active) {
