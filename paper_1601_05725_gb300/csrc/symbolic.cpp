@@ -45,6 +45,34 @@ int32_t number_tree(int32_t height, int32_t &next, std::vector<int32_t> &first,
     return t;
 }
 
+// Sort distinct non-negative ints: a comparison sort for short lists, a bitmap
+// over the value range for long ones (linear in the count and the range / 64; the
+// reach of a column tied to much of its block lists that many steps).  bits has a
+// word per 64 values and is left zero.
+void sort_ints(std::vector<int32_t> &v, std::vector<uint64_t> &bits)
+{
+    if (v.size() < 512) {
+        std::sort(v.begin(), v.end());
+        return;
+    }
+    int32_t lo = v[0], hi = v[0];
+    for (int32_t x : v) {
+        lo = std::min(lo, x);
+        hi = std::max(hi, x);
+        bits[(size_t)x >> 6] |= 1ull << (x & 63);
+    }
+    size_t k = 0;
+    for (size_t w = (size_t)lo >> 6; w <= ((size_t)hi >> 6); w++) {
+        uint64_t b = bits[w];
+        bits[w] = 0;
+        while (b) {
+            const int t = __builtin_ctzll(b);
+            b &= b - 1;
+            v[k++] = (int32_t)(w * 64 + (size_t)t);
+        }
+    }
+}
+
 }  // namespace
 
 // Column state of the in-node kernel: x over the L-space, a bitmap of own steps,
@@ -324,6 +352,7 @@ int bk_plan_build(int32_t n, const int32_t *colptr, const int32_t *rowind, const
     std::vector<int32_t> gend((size_t)n, 0), glen((size_t)n, 0);
     std::vector<char> pruned((size_t)n, 0);
     std::vector<int32_t> stack, spos, lrow, ustep;
+    std::vector<uint64_t> sortbits(((size_t)n + 63) / 64 + 1, 0);
     pl.symbolic_singular = -1;
     for (int32_t c = 0; c < n; c++) {
         const bk_task &T = pl.tasks[(size_t)pl.col_task[(size_t)c]];
@@ -360,8 +389,8 @@ int bk_plan_build(int32_t n, const int32_t *colptr, const int32_t *rowind, const
                 }
             }
         }
-        std::sort(ustep.begin(), ustep.end());
-        std::sort(lrow.begin(), lrow.end());
+        sort_ints(ustep, sortbits);
+        sort_ints(lrow, sortbits);
         int32_t piv = -1;
         if (mark[(size_t)c] == c && pinv[(size_t)c] < 0) piv = c;
         else
