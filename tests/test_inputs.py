@@ -123,6 +123,28 @@ def test_config4_shape_scaled():
     assert np.median(deg_ring) < 10
 
 
+def test_config4_coupling_is_a_shallow_dag_of_blocks():
+    """Config 4's small blocks couple into uniformly random later blocks: the
+    longest chain of coupled blocks (the solve's critical path through the BTF
+    blocks) stays logarithmic, unlike config 1's block-to-next-block chain."""
+    p = I.config4(n=40_000, n_rails=4, rail_deg=(20, 1000))
+    B = H.b_matrix(p).tocoo()
+    blk = H.block_of(p.block_ptr, p.n)
+    off = blk[B.row] < blk[B.col]
+    src, dst = blk[B.row[off]], blk[B.col[off]]
+    assert (dst > src).all()
+    depth = np.zeros(p.nblocks, np.int64)
+    order = np.argsort(-src, kind="stable")
+    for k in order:                      # later blocks first
+        depth[src[k]] = max(depth[src[k]], depth[dst[k]] + 1)
+    assert depth.max() < 40, depth.max()
+    c1 = I.config1()
+    B1 = H.b_matrix(c1).tocoo()
+    b1 = H.block_of(c1.block_ptr, c1.n)
+    o1 = b1[B1.row] < b1[B1.col]
+    assert (b1[B1.col[o1]] == b1[B1.row[o1]] + 1).all()
+
+
 @pytest.mark.slow
 def test_config4_full_size_counts():
     p = I.config4()
