@@ -41,7 +41,8 @@ def _args():
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--cpu-sample", type=int, default=4, help="oracle steps in the cpu_baseline sample")
+    ap.add_argument("--cpu-sample", type=int, default=16,
+                    help="oracle steps in the cpu_baseline sample (about 13 s of one core)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="keep the default launch sizes instead of basker_autotune's (untimed, before the warm-up)")
