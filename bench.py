@@ -41,8 +41,9 @@ def _args():
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--cpu-sample", type=int, default=16,
-                    help="oracle steps in the cpu_baseline sample (about 13 s of one core)")
+    ap.add_argument("--cpu-sample", type=int, default=None,
+                    help="oracle steps in the cpu_baseline sample (default: 16 power-grid steps or 6 "
+                         "batched steps, 10-15 s of one core)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="keep the default launch sizes instead of basker_autotune's (untimed, before the warm-up)")
@@ -380,9 +381,10 @@ def run_ours(args):
         "clocks": clk,
     }
     if not args.no_cpu_baseline:
-        t, _ = cpu_oracle_steps(prob, vals, rhs, 0, args.cpu_sample)
-        out["cpu_baseline"] = {"value": args.cpu_sample / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-                               "sample": f"{args.cpu_sample} refactor+solve steps of the same workload, serial C oracle"}
+        ns = args.cpu_sample or (6 if WORKLOAD == "batched" else 16)
+        t, _ = cpu_oracle_steps(prob, vals, rhs, 0, ns)
+        out["cpu_baseline"] = {"value": ns / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+                               "sample": f"{ns} steps of the same workload, serial C oracle"}
     print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
