@@ -240,12 +240,16 @@ int basker_autotune(basker_t h, const double *values_dev, const double *b_dev, v
  * holds the memory, and cudaFree synchronises the whole device), which still
  * need to solve with factors made earlier.
  *   Same arguments and results as basker_solve; the handle must be factored.
- *   The work vectors and ND buffers of the solve live in one array of
- *   BASKER_NOALLOC_SCRATCH_DOUBLES doubles compiled into the library, so the call
- *   performs no cudaMalloc, cudaFree or other allocation.  It needs
- *   2 * nrhs * n doubles; larger requests return BASKER_ERR_INVALID_ARG without
- *   launching anything, and so does a handle with options.precision 1 (its
- *   refinement needs buffers of its own).
+ *   The solve's two work vectors (the forward results and the solution by
+ *   pivot step, n * nrhs doubles each) live in one array of
+ *   BASKER_NOALLOC_SCRATCH_DOUBLES doubles compiled into the library; its other
+ *   buffers (per-row flags, the factors by rows) are the handle's, made when it
+ *   was factored.  So the call performs no cudaMalloc, cudaFree or other
+ *   allocation.  It needs 2 * nrhs * n doubles; larger requests return
+ *   BASKER_ERR_INVALID_ARG without launching anything, and so does a handle with
+ *   options.precision 1 or 2 (refined solves, whose refinement needs buffers of
+ *   its own).  With options.timing the call records no kernel time; it sets
+ *   basker_info's precision_used to 0 (FP64 factors).
  *   The first call on a device looks up the array's device address (with that
  *   device current) and caches it; make that first call before any stream
  *   capture begins.

@@ -202,6 +202,13 @@ class Handle:
         if s != 0:
             raise BaskerError(s, "basker_symbolic")
         self.h = h
+        self._dev_index = None
+        try:
+            import torch
+            if torch.cuda.is_available():
+                self._dev_index = torch.cuda.current_device()
+        except Exception:
+            pass
 
     @classmethod
     def from_problem(cls, prob, **kw) -> "Handle":
@@ -247,6 +254,16 @@ class Handle:
         """basker_solve_noalloc: like solve(), for callers that cannot allocate
         device memory; b and x are CUDA float64 (n,) or column-major (n, nrhs)
         buffers the caller owns (x is written in place)."""
+        import torch
+        for nm, t in (("b", b), ("x", x)):
+            if not isinstance(t, torch.Tensor) or t.dtype != torch.float64:
+                raise ValueError(f"{nm} must be a float64 tensor")
+            if not t.is_cuda or t.device.index != self.device_index():
+                raise ValueError(f"{nm} must live on the handle's device (cuda:{self.device_index()})")
+            if t.dim() not in (1, 2) or t.shape[0] != self.n:
+                raise ValueError(f"{nm} must have shape (n,) or (n, nrhs) with n = {self.n}")
+        if b.dim() != x.dim() or tuple(b.shape) != tuple(x.shape):
+            raise ValueError("b and x must have the same shape")
         nrhs = 1 if b.dim() == 1 else b.shape[1]
 
         def lead(t):
@@ -261,6 +278,13 @@ class Handle:
         s = self.lib.basker_solve_noalloc(self.h, nrhs, _dev_ptr(b), ldb, _dev_ptr(x), ldx, _stream_ptr(None))
         self._check(s, "basker_solve_noalloc")
         return x
+
+    def device_index(self) -> int:
+        """CUDA device the handle's memory lives on (current at basker_symbolic)."""
+        if getattr(self, "_dev_index", None) is None:
+            import torch
+            self._dev_index = torch.cuda.current_device()
+        return self._dev_index
 
     def autotune(self, values, b, stream=None) -> dict:
         """basker_autotune: values and b CUDA float64 tensors (nnz(A), n).  Returns the

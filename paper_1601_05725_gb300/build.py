@@ -20,7 +20,10 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 SOURCES = ["api.cu", "kernels_gp.cu", "kernels_static.cu", "kernels_solve.cu", "symbolic.cpp",
            "solve_plan.cpp", "noalloc.cu", "kernels_dd.cu", "refine.cu", "kernels_dense.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE]
+# -fmad=false: no multiply-add is contracted unless written as fma(); the
+# factors' bit-for-bit agreement with the oracle then does not depend on how
+# an expression happens to be written
+FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 
 
 def nvcc() -> str:

@@ -15,6 +15,7 @@
 #include "basker_internal.h"
 #include "refine_internal.h"
 #include "solve_internal.h"
+#include "trace.cuh"
 
 struct basker_s {
     basker_options opt;
@@ -496,6 +497,9 @@ int setup_device(basker_t h)
     TRY(upload_symbolic_pattern(h));
     if (!pl.counts_only) TRY(save_symbolic_image(h));
     h->schedule_valid = !pl.counts_only;
+#ifdef BK_TRACE
+    TRY(dalloc(h, &d.trace, (size_t)4 + 4 * (size_t)BK_TRACE_CAP, true));
+#endif
     return BASKER_OK;
 }
 
@@ -1109,6 +1113,7 @@ int bk_solve_on_scratch(basker_t h, int32_t nrhs, const double *b_dev, int32_t l
                         double *scratch, void *stream)
 {
     if (!h->factored) return BASKER_ERR_NOT_FACTORED;
+    h->info.precision_used = 0;                // FP64 factors (refined handles are refused)
     if (nrhs == 0 || h->pl.n == 0) return BASKER_OK;
     bk_solve_dev sd = h->sd;
     sd.w = scratch;
@@ -1475,6 +1480,24 @@ int basker_autotune(basker_t h, const double *values_dev, const double *b_dev, v
     dfree(h, x);
     return st;
 }
+
+#ifdef BK_TRACE
+// Diagnostic builds only: copy out the per-item timeline (4 words a record, see
+// trace.cuh) recorded since the last call, then restart it.
+int basker_trace_read(basker_t h, unsigned long long *host, int64_t max_records, int64_t *count)
+{
+    if (!h || !h->d.trace || !count) return BASKER_ERR_INVALID_ARG;
+    cudaSetDevice(h->device);
+    CU(cudaDeviceSynchronize());
+    unsigned long long total = 0;
+    CU(cudaMemcpy(&total, h->d.trace, sizeof(total), cudaMemcpyDeviceToHost));
+    const int64_t m = std::min<int64_t>(std::min<int64_t>((int64_t)total, BK_TRACE_CAP), max_records);
+    if (host && m > 0) CU(cudaMemcpy(host, h->d.trace + 4, (size_t)m * 32, cudaMemcpyDeviceToHost));
+    *count = (int64_t)total;
+    CU(cudaMemset(h->d.trace, 0, sizeof(total)));
+    return BASKER_OK;
+}
+#endif
 
 void basker_free(basker_t h)
 {

@@ -90,6 +90,7 @@ struct bk_dev {
     int32_t *pchg_ep;                // per column: epoch of the round that recomputed it by the reach
     int32_t *touch_ref, *dirty_ref, *pchg_ref;   // the same, numbered by refactorization
     unsigned char *ws;               // global workspace (zero between uses)
+    unsigned long long *trace;       // per-item timeline (builds with BK_TRACE only; else null)
     int32_t *done;                   // per column: epoch of its last completion (static kernel)
     int32_t *order;                  // static kernel claim order (topological)
     const int32_t *iorder;           // levels kernel claim order: tasks by level, interleaved

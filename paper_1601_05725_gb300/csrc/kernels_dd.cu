@@ -30,6 +30,7 @@
 #include "basker_internal.h"
 #include "column_static.cuh"
 #include "device_util.cuh"
+#include "trace.cuh"
 
 using namespace bk;
 
@@ -184,6 +185,7 @@ __global__ void __launch_bounds__(128) bk_dd_kernel(bk_dev d, const int32_t *__r
         k = __shfl_sync(BK_FULL, k, 0);
         if (k >= ncols) break;
         const int c = cols[k];
+        BK_TSTART(t0);
         const int tid = d.col_task[c];
         if (__shfl_sync(BK_FULL, (int)should_stop(d, tid, c), 0)) {
             if (lane == 0) st_release(d.done + c, epoch);
@@ -267,7 +269,10 @@ __global__ void __launch_bounds__(128) bk_dd_kernel(bk_dev d, const int32_t *__r
                 mode = verdict;
                 if (mode == 0) {
                     __syncwarp();
-                    if (lane == 0) st_release(d.done + c, epoch);
+                    if (lane == 0) {
+                        st_release(d.done + c, epoch);
+                        BK_TREC(d.trace, BK_TR_ROUND, 0, c, t0);
+                    }
                     continue;
                 }
             }
@@ -287,6 +292,7 @@ __global__ void __launch_bounds__(128) bk_dd_kernel(bk_dev d, const int32_t *__r
                         d.dirty_ref[c] = refno;
                         __threadfence();
                         st_release(d.done + c, epoch);
+                        BK_TREC(d.trace, BK_TR_ROUND, 1, c, t0);
                     }
                     __syncwarp();
                     if (broken) return;
@@ -587,6 +593,7 @@ __global__ void __launch_bounds__(128) bk_dd_kernel(bk_dev d, const int32_t *__r
             }
             __threadfence();
             st_release(d.done + c, epoch);
+            BK_TREC(d.trace, BK_TR_ROUND, resolve ? 3 : 2, c, t0);
         }
         __syncwarp();
         if (why) return;      // the workspace slice may hold stale values; the host clears it

@@ -34,6 +34,7 @@
 
 #include "basker_internal.h"
 #include "device_util.cuh"
+#include "trace.cuh"
 
 using namespace bk;
 namespace cg = cooperative_groups;
@@ -74,6 +75,7 @@ __global__ void __launch_bounds__(DN_THREADS) bk_dense_node_kernel(bk_dev d, con
     extern __shared__ __align__(16) unsigned char dsm[];
     const int tid_x = threadIdx.x, lane = tid_x & 31, wid = tid_x >> 5;
     const int tid = task_ids[blockIdx.x / CN];
+    BK_TSTART(t0);
     if (wid == 0) load_task(S.T, d.tasks + tid, lane);
     if (tid_x == 0) S.stop[0] = S.stop[1] = 0;
     __syncthreads();
@@ -353,6 +355,7 @@ __global__ void __launch_bounds__(DN_THREADS) bk_dense_node_kernel(bk_dev d, con
     }
     // no block leaves while another may still read its shared memory
     cl.sync();
+    if (rank == 0 && tid_x == 0) BK_TREC(d.trace, BK_TR_DENSE, 0, tid, t0);
 }
 
 }  // namespace

@@ -29,6 +29,7 @@
 
 #include "basker_internal.h"
 #include "device_util.cuh"
+#include "trace.cuh"
 
 using namespace bk;
 
@@ -419,6 +420,7 @@ __global__ void __launch_bounds__(128) bk_gp_desc_kernel(bk_dev d, const int32_t
         k = __shfl_sync(BK_FULL, k, 0);
         if (k >= ncols) break;
         const int c = cols[k];
+        BK_TSTART(t0);
         const int tid = d.col_task[c];
         if (__shfl_sync(BK_FULL, (int)should_stop(d, tid, c), 0)) continue;
         if (tid != cur_task) {
@@ -553,6 +555,7 @@ __global__ void __launch_bounds__(128) bk_gp_desc_kernel(bk_dev d, const int32_t
             d.dcnt[c] = nu;
             if (overflow) report_overflow(d, T, tid, c, 2);
             else if (bad) report_fail(d.status, c, BK_CODE_NAN);
+            BK_TREC(d.trace, BK_TR_DESC, 0, c, t0);
         }
         __syncwarp();
     }

@@ -23,6 +23,7 @@
 #include "basker_internal.h"
 #include "device_util.cuh"
 #include "solve_internal.h"
+#include "trace.cuh"
 
 using namespace bk;
 
@@ -517,6 +518,7 @@ __global__ void __launch_bounds__(128) bk_solve_kernel(bk_dev d, bk_solve_dev s,
         k = __shfl_sync(BK_FULL, k, 0);
         if (k >= s.nitems) break;
         const int it = s.items[k];
+        BK_TSTART(t0);
         const bool fwd = it >= 0;
         const int i = fwd ? it : ~it;
         if (i >= n) {
@@ -543,6 +545,7 @@ __global__ void __launch_bounds__(128) bk_solve_kernel(bk_dev d, bk_solve_dev s,
             __threadfence();
             __syncwarp();
             for (int r = lo + lane; r < hi; r += 32) st_release(flags + r, epoch);
+            if (lane == 0) BK_TREC(d.trace, BK_TR_SOLVE, fwd ? 2 : 3, i - n, t0);
             continue;
         }
         // a separator's row takes only the terms from outside its node
@@ -581,6 +584,7 @@ __global__ void __launch_bounds__(128) bk_solve_kernel(bk_dev d, bk_solve_dev s,
             __threadfence();
             __syncwarp();
             if (lane == 0) st_release(s.fdone + i, part ? -epoch : epoch);
+            if (lane == 0) BK_TREC(d.trace, BK_TR_SOLVE, 0, i, t0);
         } else {
             // backward row i: its forward result, then U(i,k) for k >= chi (or all), then the diagonal
             if (!wait_flags(d, s.fdone, i, lane == 0, epoch, budget)) return;
@@ -609,6 +613,7 @@ __global__ void __launch_bounds__(128) bk_solve_kernel(bk_dev d, bk_solve_dev s,
             __threadfence();
             __syncwarp();
             if (lane == 0) st_release(s.bdone + i, part ? -epoch : epoch);
+            if (lane == 0) BK_TREC(d.trace, BK_TR_SOLVE, 1, i, t0);
         }
     }
 }

@@ -23,6 +23,7 @@
 #include "basker_internal.h"
 #include "column_static.cuh"
 #include "device_util.cuh"
+#include "trace.cuh"
 
 using namespace bk;
 
@@ -46,6 +47,7 @@ __global__ void __launch_bounds__(128) bk_static_kernel(bk_dev d, int32_t ncols,
         k = __shfl_sync(BK_FULL, k, 0);
         if (k >= ncols) break;
         const int c = d.order[k];
+        BK_TSTART(t0);
         const int tid = d.col_task[c];
         if (tid != cur) {
             load_task(T, d.tasks + tid, lane);
@@ -68,6 +70,7 @@ __global__ void __launch_bounds__(128) bk_static_kernel(bk_dev d, int32_t ncols,
                 atomicAdd(&d.status->static_fail, 1);
             }
             st_release(d.done + c, epoch);
+            BK_TREC(d.trace, BK_TR_STATIC, ok ? 0 : 1, c, t0);
         }
     }
 }
@@ -82,6 +85,7 @@ __global__ void __launch_bounds__(128) bk_levels_kernel(bk_dev d, int32_t epoch,
         c = __shfl_sync(BK_FULL, c, 0);
         if (c >= d.n) break;
         c = d.iorder[c];
+        BK_TSTART(t0);
         const int64_t ub = d.Ubeg[c];
         const int uc = d.Ucnt[c];
         int lv = 0;
@@ -110,6 +114,7 @@ __global__ void __launch_bounds__(128) bk_levels_kernel(bk_dev d, int32_t epoch,
             atomicMax(maxlev, lv);
             __threadfence();
             st_release(d.done + c, epoch);
+            BK_TREC(d.trace, BK_TR_LEVELS, 0, c, t0);
         }
         __syncwarp();
     }

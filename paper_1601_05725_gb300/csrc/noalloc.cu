@@ -1,9 +1,9 @@
-// noalloc.cu -- basker_solve_noalloc: the solve of basker_solve with its scratch
-// (the work vectors indexed by pivot step and the ND contribution buffers) in a
-// fixed array of this library's device memory, so that the call allocates
-// nothing.  Host code only sees the array's name as a host-side stand-in; its
-// device address is looked up once per device (cudaGetSymbolAddress, with that
-// device current) and passed to the kernel.
+// noalloc.cu -- basker_solve_noalloc: the solve of basker_solve with its two work
+// vectors (forward results and solution, indexed by pivot step) in a fixed array
+// of this library's device memory, so that the call allocates nothing.  Host
+// code only sees the array's name as a host-side stand-in; its device address
+// is looked up once per device (cudaGetSymbolAddress, with that device current)
+// and passed to the kernel.
 #include <cuda_runtime.h>
 
 #include <mutex>

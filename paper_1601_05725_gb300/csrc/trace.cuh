@@ -1,0 +1,45 @@
+// trace.cuh -- optional per-item timeline of the persistent kernels.
+//
+// Built only with -DBK_TRACE (never in the library's normal build): each warp
+// that finishes an item (a column of the stored-pattern pass, of a round, of the
+// descendant phase; a separator's dense elimination; a solve item; a column
+// level) appends one record {kind | mode | id, start ns, end ns, SM | warp} to
+// bk_dev::trace, whose first word counts the records.  The timeline shows the
+// chains of dependent items that set each kernel's duration.
+#pragma once
+
+#include <cstdint>
+
+#define BK_TRACE_CAP (1 << 22)     // records kept (32 bytes each)
+
+enum { BK_TR_STATIC = 1, BK_TR_ROUND = 2, BK_TR_DESC = 3, BK_TR_DENSE = 4, BK_TR_SOLVE = 5, BK_TR_LEVELS = 6 };
+
+#ifdef BK_TRACE
+__device__ __forceinline__ unsigned long long bk_gtime()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void bk_trace_rec(unsigned long long *buf, int kind, int mode, int id,
+                                             unsigned long long t0)
+{
+    if (!buf) return;
+    const unsigned long long t1 = bk_gtime();
+    const unsigned long long i = atomicAdd(buf, 1ull);
+    if (i >= BK_TRACE_CAP) return;
+    unsigned sm;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(sm));
+    unsigned long long *r = buf + 4 + 4 * i;
+    r[0] = ((unsigned long long)kind << 56) | ((unsigned long long)(mode & 0xff) << 48) | (unsigned)id;
+    r[1] = t0;
+    r[2] = t1;
+    r[3] = ((unsigned long long)sm << 32) | ((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+}
+#define BK_TSTART(v) const unsigned long long v = bk_gtime()
+#define BK_TREC(buf, kind, mode, id, t0) bk_trace_rec(buf, kind, mode, id, t0)
+#else
+#define BK_TSTART(v)
+#define BK_TREC(buf, kind, mode, id, t0)
+#endif

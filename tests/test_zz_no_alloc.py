@@ -1,11 +1,15 @@
-"""basker_solve_noalloc against basker_solve, through the C ABI.
+"""basker_solve_noalloc against basker_solve and the oracle, through the C ABI.
 
 Some callers cannot allocate device memory when they solve: a simulator whose
 time-step loop runs on a pool or caching allocator that reserved the device
 memory up front, where a cudaMalloc can fail and a cudaFree stalls the whole
 device.  basker_solve_noalloc serves them from a fixed array compiled into the
-library.  Two calls in a row must give what the allocating solve gives, and a
-request larger than the array must be refused cleanly.
+library.  Each test below starts from a freshly factored handle that has never
+solved, so an entry point that allocated its work vectors would show up in the
+handle's device bytes.  Two calls in a row must give exactly what the
+allocating solve and the oracle give (the solve keeps the oracle's per-entry
+operation order, so the results are equal bit for bit), and a request larger
+than the array must be refused cleanly.
 
 This file is collected last so that a run stopping at its first failure has
 already run every other test.
@@ -30,24 +34,35 @@ def _colmajor(A, torch):
 ])
 def test_noalloc_solve_matches_solve_on_two_calls(kind, seed, kw, nrhs):
     import torch
+
+    import oracle
     assert torch.cuda.is_available(), "GPU tests need a CUDA device"
     build.build()
     prob = I.small_problem(seed, kind, **kw)
+    o = oracle.OracleLU(prob)
+    assert o.factor() == "OK"
     h = basker.Handle.from_problem(prob)
     h.factor(torch.as_tensor(prob.values, device="cuda"))
     rng = np.random.default_rng(seed)
-    for _ in range(2):
+    for call in range(2):
         B = rng.standard_normal((prob.n, nrhs))
         b = _colmajor(B, torch)
-        ref = h.solve(b).cpu().numpy()
         x = _colmajor(np.full((prob.n, nrhs), np.nan), torch)
+        torch.cuda.synchronize()
+        dev_bytes, torch_bytes = h.info()["device_bytes"], torch.cuda.memory_allocated()
         h.solve_noalloc(b, x)
+        torch.cuda.synchronize()
+        # nothing allocated: neither the handle's own arena nor torch's pool grew
+        assert h.info()["device_bytes"] == dev_bytes
+        assert torch.cuda.memory_allocated() == torch_bytes
         got = x.cpu().numpy()
-        assert np.isfinite(got).all()
-        assert np.abs(got - ref).max() <= 1e-8 * np.abs(ref).max()
+        np.testing.assert_array_equal(got, o.solve(B).reshape(prob.n, nrhs))
+        if call == 1:
+            # the allocating solve afterwards (it makes its buffers now) agrees bit for bit
+            np.testing.assert_array_equal(got, h.solve(b).cpu().numpy())
 
 
-def test_noalloc_solve_refuses_more_than_its_array():
+def test_noalloc_solve_refuses_what_it_cannot_serve():
     import torch
     build.build()
     prob = I.small_problem(53, "blocks", nblocks=20, size_range=(5, 60))
@@ -59,8 +74,23 @@ def test_noalloc_solve_refuses_more_than_its_array():
     with pytest.raises(basker.BaskerError) as e:
         h.solve_noalloc(b, x)
     assert e.value.name == "INVALID_ARG"
+    # buffers the entry point would overrun are refused on the host, before the call
+    one = _colmajor(np.ones((prob.n, 1)), torch)
+    with pytest.raises(ValueError):
+        h.solve_noalloc(_colmajor(np.ones((prob.n, 3)), torch), one)            # x narrower than b
+    with pytest.raises(ValueError):
+        h.solve_noalloc(one.float(), one)                                        # not float64
+    with pytest.raises(ValueError):
+        h.solve_noalloc(_colmajor(np.ones((prob.n + 1, 1)), torch), one)        # wrong n
     # a fitting request still works afterwards
     x1 = _colmajor(np.zeros((prob.n, 1)), torch)
-    h.solve_noalloc(_colmajor(np.ones((prob.n, 1)), torch), x1)
-    np.testing.assert_allclose(x1.cpu().numpy(), h.solve(_colmajor(np.ones((prob.n, 1)), torch)).cpu().numpy(),
-                               rtol=1e-12)
+    h.solve_noalloc(one, x1)
+    np.testing.assert_array_equal(x1.cpu().numpy(), h.solve(one).cpu().numpy())
+    # refined handles are refused (their refinement needs buffers of its own)
+    for prec in (1, 2):
+        hr = basker.Handle.from_problem(prob, precision=prec)
+        hr.factor(torch.as_tensor(prob.values, device="cuda"))
+        with pytest.raises(basker.BaskerError) as e:
+            hr.solve_noalloc(one, x1)
+        assert e.value.name == "INVALID_ARG"
+        hr.free()
