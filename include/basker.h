@@ -76,13 +76,19 @@ typedef struct {
     double ir_tol;                /* precision 1, 2: backward error to reach; default 1e-13 */
     double growth_limit;          /* precision 1: max over BTF blocks of max|U_d| / max|B_d|
                                      above which the FP32 factors are not used; default 1e4 */
-    int refactor_switch;          /* a refactorization whose stored-pattern pass rejected
-                                     pivots continues with rounds of column recomputation;
-                                     0 (default): when the rounds have taken as long as the
-                                     handle's last complete factorization, the rest is one
-                                     complete Algorithm 1 pass with the previous pivots
-                                     preferred; 1: rounds only; 2: the complete pass at once.
-                                     The factors are the same in every mode. */
+    int refactor_switch;          /* the pivots a refactorization's stored-pattern pass
+                                     rejected are resolved, 0 (default): by rounds of
+                                     column recomputation until they have taken as long
+                                     as the handle's last complete factorization, the rest
+                                     then one complete Algorithm 1 pass with the previous
+                                     pivots preferred; 1: rounds only; 2: the complete
+                                     pass at once; 3: when every ND separator fits the
+                                     dense elimination, the repair pass (one block of
+                                     threads per ND leaf or BTF block walks its columns
+                                     from the first rejection on, in column order, on the
+                                     device, with no host round trip), else as 0.  The
+                                     factors are the same in every mode (other values:
+                                     INVALID_ARG). */
     int graphs;                   /* nonzero (default): the launches that follow every
                                      factorization are replayed from a CUDA graph captured
                                      once per L/U arena; 0: launched one by one */

@@ -45,6 +45,11 @@ struct basker_s {
     bool factored = false, ws_dirty = false, schedule_valid = true, order_is_symbolic = true;
     double gp_wall_ms = 0.0;     // wall time of the last complete Algorithm 1 pass (host clock)
     bool sep_dense = false;      // refactorizations recompute every separator densely
+    // the repair pass (sep_dense): the tasks it serves (every task without
+    // descendants), its dynamic shared memory and its persistent blocks
+    int32_t *rp_tasks = nullptr;
+    int32_t rp_ntasks = 0, rp_ctas = 0;
+    size_t rp_smem = 0;
     // the arena as the symbolic pass left it (natural pivots, symbolic pattern and
     // schedule): a factorization first tries the stored-pattern path from it
     int32_t *sym_Li = nullptr, *sym_Ui = nullptr, *sym_n = nullptr;   // sym_n: 8 arrays of n ints
@@ -380,6 +385,15 @@ int setup_device(basker_t h)
     }
     for (bk_task &T : pl.tasks) T.dense = (h->sep_dense && T.sp_lo < T.lo) ? 1 : 0;
     TRY(upload(h, &d.tasks, pl.tasks));
+    if (h->sep_dense) {
+        std::vector<int32_t> ids;
+        for (size_t t = 0; t < pl.tasks.size(); t++)
+            if (!pl.tasks[t].dense) ids.push_back((int32_t)t);
+        TRY(upload(h, &h->rp_tasks, ids));
+        h->rp_ntasks = (int32_t)ids.size();
+        h->rp_smem = bk_repair_smem(pl.tasks.data(), ids.data(), (int32_t)ids.size(), 160 * 1024);
+        h->rp_ctas = std::max(1, std::min<int>({h->rp_ntasks, pl.wsd_warps, 152 * 8}));
+    }
     TRY(dalloc(h, &d.prow, (size_t)n));
     TRY(dalloc(h, &d.pinv, (size_t)n));
     TRY(dalloc(h, (int32_t **)&d.pref, (size_t)n));
@@ -734,7 +748,7 @@ int launch_redo(basker_t h, cudaStream_t s)
             // the rounds have cost as much as a complete pass would: finish with one
             // (no complete pass timed yet: twenty stored-pattern factorizations)
             const double limit = h->gp_wall_ms > 0.0 ? h->gp_wall_ms : 20.0 * h->static_factor_ms;
-            if (!active.empty() && h->opt.refactor_switch == 0 && limit > 0.0 &&
+            if (!active.empty() && (h->opt.refactor_switch == 0 || h->opt.refactor_switch == 3) && limit > 0.0 &&
                 std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count() > limit) {
                 h->info.last_repivot_columns = redone;
                 return BK_SWITCH_TO_FULL;
@@ -743,6 +757,54 @@ int launch_redo(basker_t h, cudaStream_t s)
     }
     h->info.last_repivot_columns = redone;
     CU(cudaGetLastError());
+    return BASKER_OK;
+}
+
+// The repair pass serves refactorizations with options.refactor_switch 3 whose
+// separators are all recomputed densely.
+bool use_repair(basker_t h) { return h->sep_dense && h->opt.refactor_switch == 3 && h->rp_ntasks > 0; }
+
+// Counters of the last repair pass (from the status word just read).
+void note_repair(basker_t h)
+{
+    const int32_t rep = h->h_status->repaired;
+    h->info.last_repivot_columns = rep;
+    h->info.last_rounds = rep > 0 ? 1 : 0;
+    h->info.rounds_columns += rep;
+}
+
+// After a stored-pattern pass, when every separator is recomputed densely: the
+// repair pass over the ND leaves and BTF blocks (each task with a rejected pivot
+// walks its columns from the first rejection on, on the device), then each ND
+// level's separators by the descendant phase and the dense elimination with the
+// previous pivots preferred.  Asynchronous: nothing is read back here.
+int launch_repair_path(basker_t h, cudaStream_t s)
+{
+    CU(cudaMemsetAsync(h->d.counter + 4, 0, sizeof(int32_t), s));
+    tbeg(h, KT_SPEC, s, 1);
+    bk_launch_repair(h->d, h->rp_tasks, h->rp_ntasks, h->d.counter + 4, h->opt.tau, h->rp_smem, h->rp_ctas, s);
+    CU(cudaGetLastError());
+    tend(h, s);
+    h->launches++;
+    for (size_t l = 1; l < h->lv_tasks.size(); l++) {
+        if (h->lv_ncols[l] > 0) {
+            CU(cudaMemsetAsync(h->d.counter + 3, 0, sizeof(int32_t), s));
+            tbeg(h, KT_DESC, s, 1);
+            bk_launch_gp_desc(h->d, h->lv_cols[l], h->lv_ncols[l], h->d.counter + 3, s);
+            CU(cudaGetLastError());
+            tend(h, s);
+            h->launches++;
+        }
+        for (int g = 0; g < 2; g++) {
+            if (h->lv_ndense[g][l] == 0) continue;
+            tbeg(h, KT_DENSE, s, 1);
+            bk_launch_dense_nodes(h->d, h->lv_dense[g][l], h->lv_ndense[g][l], h->lv_dsmem[g][l], h->opt.tau, 1,
+                                  g ? BK_DENSE_CLUSTER : 1, s);
+            CU(cudaGetLastError());
+            tend(h, s);
+            h->launches++;
+        }
+    }
     return BASKER_OK;
 }
 
@@ -850,13 +912,50 @@ int factor_static(basker_t h, cudaStream_t s)
     h->info.last_repivot_columns = 0;
     h->info.last_rounds = 0;
     if (rejected || h->sep_dense) {
-        st = launch_redo(h, s);
+        st = use_repair(h) ? launch_repair_path(h, s) : launch_redo(h, s);
         if (st == BASKER_OK) st = read_status(h, s);
         if (st != BASKER_OK) return BK_SWITCH_TO_FULL;
+        if (use_repair(h)) note_repair(h);
         h->schedule_valid = false;
     }
     h->static_factor_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     return BASKER_OK;
+}
+
+// A refactorization's rejected pivots by rounds of the round kernel (host-driven
+// level by level; options.refactor_switch decides when the rest becomes one
+// complete pass), after the stored-pattern pass.  Returns the final status
+// (-1: the factors need more room even after the regrows).
+int refactor_by_rounds(basker_t h, cudaStream_t s)
+{
+    CU(cudaMemcpyAsync(h->h_task_fail, h->d.task_fail, sizeof(int32_t) * h->pl.tasks.size(),
+                       cudaMemcpyDeviceToHost, s));
+    int st = read_status(h, s);
+    if (st == BASKER_ERR_TIMEOUT) return st;
+    if (!h->h_status->static_fail && !h->sep_dense) return st;
+    st = (h->opt.refactor_switch == 2 && h->h_status->static_fail) ? BK_SWITCH_TO_FULL : launch_redo(h, s);
+    if (st == BASKER_OK) st = read_status(h, s);
+    h->schedule_valid = false;
+    if (st == BK_SWITCH_TO_FULL) {
+        // Algorithm 1 on every column with the previous pivots preferred: the
+        // refactorization's definition, computed directly
+        h->info.full_refactors++;
+        h->ws_dirty = true;
+        TRY(reset_status(h, s));
+        const auto t0 = std::chrono::steady_clock::now();
+        TRY(launch_full_gp(h, s, 1));
+        st = read_status(h, s);
+        if (st == BASKER_OK)
+            h->gp_wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
+    for (int tries = 0; st == -1 && tries < 16; tries++) {
+        // the new pivots need more room: grow and run Algorithm 1 everywhere
+        TRY(regrow(h));
+        TRY(reset_status(h, s));
+        TRY(launch_full_gp(h, s, 1));
+        st = read_status(h, s);
+    }
+    return st;
 }
 
 int factor_impl(basker_t h, const double *values, cudaStream_t s, bool refactor)
@@ -874,37 +973,26 @@ int factor_impl(basker_t h, const double *values, cudaStream_t s, bool refactor)
                            cudaMemcpyDeviceToDevice, s));
         if (!h->schedule_valid) TRY(compute_schedule(h, s));
         TRY(static_pass(h, s));
-        CU(cudaMemcpyAsync(h->h_task_fail, h->d.task_fail, sizeof(int32_t) * h->pl.tasks.size(),
-                           cudaMemcpyDeviceToHost, s));
-        int st = read_status(h, s);
-        if (st == BASKER_ERR_TIMEOUT) return st;
         h->info.last_repivot_columns = 0;
         h->info.last_rounds = 0;
-        if (h->h_status->static_fail || h->sep_dense) {
-            st = (h->opt.refactor_switch == 2 && h->h_status->static_fail) ? BK_SWITCH_TO_FULL : launch_redo(h, s);
-            if (st == BASKER_OK) st = read_status(h, s);
+        int st = BASKER_OK;
+        if (use_repair(h)) {
+            // the stored-pattern pass, the repair pass and the separators run back to
+            // back on the device; the status is read once at the end
+            TRY(launch_repair_path(h, s));
+            st = read_status(h, s);
             h->schedule_valid = false;
-            if (st == BK_SWITCH_TO_FULL) {
-                // Algorithm 1 on every column with the previous pivots preferred: the
-                // refactorization's definition, computed directly
-                h->info.full_refactors++;
-                h->ws_dirty = true;
+            if (st == BASKER_OK) note_repair(h);
+            for (int tries = 0; st == -1 && tries < 16; tries++) {
+                // the new pivots need more room: grow and run Algorithm 1 everywhere
+                TRY(regrow(h));
                 TRY(reset_status(h, s));
-                const auto t0 = std::chrono::steady_clock::now();
                 TRY(launch_full_gp(h, s, 1));
                 st = read_status(h, s);
-                if (st == BASKER_OK)
-                    h->gp_wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
             }
-            if (st == -1) {
-                // the new pivots need more room: grow and run Algorithm 1 everywhere
-                for (int tries = 0; st == -1 && tries < 16; tries++) {
-                    TRY(regrow(h));
-                    TRY(reset_status(h, s));
-                    TRY(launch_full_gp(h, s, 1));
-                    st = read_status(h, s);
-                }
-            }
+        } else {
+            st = refactor_by_rounds(h, s);
+            if (st == BASKER_ERR_TIMEOUT) return st;
         }
         if (st != BASKER_OK) { h->factored = false; return st == -1 ? BASKER_ERR_OOM : st; }
         TRY(finish_factorization(h, s));
@@ -1191,7 +1279,7 @@ int basker_symbolic(int32_t n, const int32_t *colptr, const int32_t *rowind, con
     if (opt) h->opt = *opt;
     if (!(h->opt.tau > 0.0 && h->opt.tau <= 1.0) || h->opt.slack < 0.0 || h->opt.wait_budget_cycles <= 0 ||
         h->opt.factor_mode < 0 || h->opt.factor_mode > 1 || h->opt.precision < 0 || h->opt.precision > 2 ||
-        h->opt.refactor_switch < 0 || h->opt.refactor_switch > 2 || h->opt.symbolic_mode < 0 ||
+        h->opt.refactor_switch < 0 || h->opt.refactor_switch > 3 || h->opt.symbolic_mode < 0 ||
         h->opt.symbolic_mode > 1 ||
         (h->opt.precision >= 1 && (h->opt.ir_max_iter < 1 || !(h->opt.ir_tol > 0.0) || !(h->opt.growth_limit > 0.0)))) {
         delete h;

@@ -31,8 +31,10 @@ struct bk_task {
     int32_t lo, hi;            // the node's own rows / columns
     int32_t sp_lo;             // first row of the subtree
     int32_t nanc;              // number of ancestor ranges (ascending rows)
-    int32_t anc_lo[BK_MAX_ANC];
-    int32_t anc_hi[BK_MAX_ANC];
+    int32_t anc_lo[BK_MAX_ANC];     // entries past nanc hold INT32_MAX (a sorted table
+    int32_t anc_hi[BK_MAX_ANC];     // of 16 for a branch-free search)
+    int32_t anc_cum[BK_MAX_ANC];    // rows of the ancestors before range a (INT32_MAX past nanc)
+    int32_t anc_sh[BK_MAX_ANC];     // anc_cum[a] - anc_lo[a]: slot = r + (hi - base) + anc_sh[a]
     int32_t space;             // (hi - sp_lo) + sum of ancestor sizes
     int32_t lspace;            // (hi - lo) + sum of ancestor sizes (rows that can be unpivoted)
     int64_t lbeg, lend;        // L region
@@ -56,6 +58,8 @@ struct bk_status {
     int32_t offdiag;                 // number of columns pivoting off the natural row
     int32_t internal_site;           // first internal-consistency check that fired (0 = none)
     int32_t internal_col;            // and its column
+    int32_t repaired;                // columns recomputed by the repair kernel
+    int32_t pad;
 };
 
 enum { BK_CODE_SINGULAR = 1, BK_CODE_NAN = 2, BK_CODE_INTERNAL = 3 };  // INTERNAL: an index outside its space
@@ -143,6 +147,7 @@ struct bk_plan {
 };
 
 // symbolic.cpp
+void bk_task_ranges(bk_task &T);   // the padded ancestor tables from anc_lo / anc_hi / nanc
 int bk_plan_build(int32_t n, const int32_t *colptr, const int32_t *rowind, const int32_t *P,
                   const int32_t *Q, int32_t nblocks, const int32_t *block_ptr, int32_t nd_block,
                   int32_t nd_leaves, const int32_t *nd_node_ptr, double slack, bk_plan &plan,
@@ -175,4 +180,9 @@ void bk_launch_static(const bk_dev &d, int32_t ncols, double tau, int32_t epoch,
                       long long budget, int blocks, void *stream);
 void bk_launch_levels(const bk_dev &d, int32_t epoch, long long budget, int blocks, void *stream);
 int bk_static_blocks();
+// kernels_repair.cu: the rejected pivots of the ND leaves and BTF blocks resolved
+// in column order after the stored-pattern pass (one warp per task)
+size_t bk_repair_smem(const bk_task *tasks, const int32_t *ids, int32_t count, size_t limit);
+void bk_launch_repair(const bk_dev &d, const int32_t *tasks, int32_t ntasks, int32_t *counter, double tau,
+                      size_t smem, int ctas, void *stream);
 size_t bk_gp_smem_limit();

@@ -12,18 +12,18 @@ namespace bk {
 // Slot of row r in a task's dense column space.  The space lists the rows
 // [base, hi) (base = sp_lo: subtree and own rows; base = lo: own rows only) and
 // then each ancestor node's rows, ancestors in ascending row order; so slots are
-// ascending in r.  Returns -1 for a row outside the space.
+// ascending in r.  Returns -1 for a row outside the space.  Ancestor rows (all
+// above hi) are found by a fixed binary search over the padded table anc_lo
+// (k = number of ranges starting at or below r), without a data-dependent loop.
 __device__ __forceinline__ int slot_of(const bk_task &T, int base, int r)
 {
-    if (r >= base && r < T.hi) return r - base;
-    int off = T.hi - base;
-#pragma unroll 1
-    for (int a = 0; a < T.nanc; a++) {
-        const int lo = T.anc_lo[a], hi = T.anc_hi[a];
-        if (r >= lo && r < hi) return off + (r - lo);
-        off += hi - lo;
-    }
-    return -1;
+    if (r < T.anc_lo[0]) return (r >= base && r < T.hi) ? r - base : -1;
+    int k = T.anc_lo[7] <= r ? 8 : 0;
+    k += T.anc_lo[k + 3] <= r ? 4 : 0;
+    k += T.anc_lo[k + 1] <= r ? 2 : 0;
+    k += T.anc_lo[k] <= r ? 1 : 0;
+    const int a = k - 1;                       // r >= anc_lo[0], so k >= 1
+    return r < T.anc_hi[a] ? r + (T.hi - base) + T.anc_sh[a] : -1;
 }
 
 // Row of an index of the L-space (own rows [lo, hi), then the ancestors' rows).
@@ -31,14 +31,13 @@ __device__ __forceinline__ int row_of_lslot(const bk_task &T, int ls)
 {
     const int own = T.hi - T.lo;
     if (ls < own) return T.lo + ls;
-    ls -= own;
-#pragma unroll 1
-    for (int a = 0; a < T.nanc; a++) {
-        const int sz = T.anc_hi[a] - T.anc_lo[a];
-        if (ls < sz) return T.anc_lo[a] + ls;
-        ls -= sz;
-    }
-    return -1;
+    const int v = ls - own;
+    int k = T.anc_cum[7] <= v ? 8 : 0;
+    k += T.anc_cum[k + 3] <= v ? 4 : 0;
+    k += T.anc_cum[k + 1] <= v ? 2 : 0;
+    k += T.anc_cum[k] <= v ? 1 : 0;
+    const int a = k - 1;                       // anc_cum[0] = 0 <= v when nanc > 0
+    return (a >= 0 && v - T.anc_cum[a] < T.anc_hi[a] - T.anc_lo[a]) ? v - T.anc_sh[a] : -1;
 }
 
 template <typename V>

@@ -167,6 +167,24 @@ static void etree_counts(bk_plan &pl)
     pl.sorder.clear();
 }
 
+// The ancestor ranges as sorted tables of BK_MAX_ANC entries (unused ones
+// INT32_MAX) with each range's first slot, so that a row's slot is found by a
+// fixed four-step binary search (slot_of in device_util.cuh).
+void bk_task_ranges(bk_task &T)
+{
+    int32_t cum = 0;
+    for (int32_t a = 0; a < BK_MAX_ANC; a++) {
+        if (a < T.nanc) {
+            T.anc_cum[a] = cum;
+            T.anc_sh[a] = cum - T.anc_lo[a];
+            cum += T.anc_hi[a] - T.anc_lo[a];
+        } else {
+            T.anc_lo[a] = T.anc_hi[a] = T.anc_cum[a] = INT32_MAX;
+            T.anc_sh[a] = 0;
+        }
+    }
+}
+
 int bk_plan_build(int32_t n, const int32_t *colptr, const int32_t *rowind, const int32_t *P,
                   const int32_t *Q, int32_t nblocks, const int32_t *block_ptr, int32_t nd_block,
                   int32_t nd_leaves, const int32_t *nd_node_ptr, double slack, bk_plan &pl,
@@ -285,6 +303,7 @@ int bk_plan_build(int32_t n, const int32_t *colptr, const int32_t *rowind, const
                 }
                 T.space = (T.hi - T.sp_lo) + (lsp - (T.hi - T.lo));
                 T.lspace = lsp;
+                bk_task_ranges(T);
                 T.level = pl.nd_height[(size_t)t];
                 T.node = t;
                 T.block = d;
@@ -298,6 +317,7 @@ int bk_plan_build(int32_t n, const int32_t *colptr, const int32_t *rowind, const
             T.lo = T.c0 = T.sp_lo = block_ptr[d];
             T.hi = T.c1 = block_ptr[d + 1];
             T.space = T.lspace = T.hi - T.lo;
+            bk_task_ranges(T);
             T.level = 0;
             T.node = -1;
             T.block = d;

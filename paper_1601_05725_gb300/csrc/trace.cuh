@@ -12,7 +12,7 @@
 
 #define BK_TRACE_CAP (1 << 22)     // records kept (32 bytes each)
 
-enum { BK_TR_STATIC = 1, BK_TR_ROUND = 2, BK_TR_DESC = 3, BK_TR_DENSE = 4, BK_TR_SOLVE = 5, BK_TR_LEVELS = 6 };
+enum { BK_TR_STATIC = 1, BK_TR_ROUND = 2, BK_TR_DESC = 3, BK_TR_DENSE = 4, BK_TR_SOLVE = 5, BK_TR_LEVELS = 6, BK_TR_REPAIR = 7, BK_TR_PHASE = 8 };
 
 #ifdef BK_TRACE
 __device__ __forceinline__ unsigned long long bk_gtime()
@@ -39,7 +39,16 @@ __device__ __forceinline__ void bk_trace_rec(unsigned long long *buf, int kind, 
 }
 #define BK_TSTART(v) const unsigned long long v = bk_gtime()
 #define BK_TREC(buf, kind, mode, id, t0) bk_trace_rec(buf, kind, mode, id, t0)
+// phases inside one item: v holds the start of the current phase
+#define BK_TPHASE0(v) unsigned long long v = bk_gtime()
+#define BK_TPHASE(buf, v, phase, id)                                   \
+    do {                                                               \
+        if ((threadIdx.x & 31) == 0) bk_trace_rec(buf, BK_TR_PHASE, phase, id, v); \
+        v = bk_gtime();                                                \
+    } while (0)
 #else
 #define BK_TSTART(v)
 #define BK_TREC(buf, kind, mode, id, t0)
+#define BK_TPHASE0(v)
+#define BK_TPHASE(buf, v, phase, id)
 #endif

@@ -68,14 +68,16 @@ def test_config3_fp32_refined(c3):
     assert h.info()["precision_used"] == 1
 
 
-def test_large_netlist_refactor_sequence_bitwise():
+@pytest.mark.parametrize("switch", [0, 3])
+def test_large_netlist_refactor_sequence_bitwise(switch):
     """An 81,219-row netlist block in 32 ND leaves: every refactorization that
-    repivots runs the rounds kernel with its largest shared-memory footprint."""
+    repivots runs the rounds kernel with its largest shared-memory footprint
+    (switch 0) or the repair pass (switch 3)."""
     prob = I.netlist_problem(2001, n_small=0, m_netlist=81219, depth=5, name="netlist_81k")
     o = oracle.OracleLU(prob)
     assert o.factor() == "OK"
     f = o.factors()
-    h = basker.Handle.from_problem(prob)
+    h = basker.Handle.from_problem(prob, refactor_switch=switch)
     h.factor(_dev(prob.values))
     _same(h, f)
     for k in (1, 2, 4):

@@ -256,10 +256,12 @@ def test_graph_replay_equals_direct_launches():
     assert ig["graph_launches"] == 4 and idd["graph_launches"] == 0
 
 
-@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("mode", [0, 1, 2, 3])
 def test_refactor_switch_modes_give_the_same_factors(mode):
-    """Rounds only (1) and one complete pass with the previous pivots preferred (2)
-    both compute the refactorization's definition: the oracle's factors."""
+    """Rounds with the switch to a complete pass (0), rounds only (1), one complete
+    pass with the previous pivots preferred (2) and the repair pass in column
+    order on the device (3) all compute the refactorization's definition: the
+    oracle's factors."""
     prob = I.small_problem(61, "netlist", n_small=80, m_netlist=600, depth=3)
     o, s = _oracle(prob)
     f = o.factors()
@@ -276,7 +278,12 @@ def test_refactor_switch_modes_give_the_same_factors(mode):
         b = I.rhs_ones(prob, v)
         np.testing.assert_array_equal(h.solve(_dev(b)).cpu().numpy(), o.solve(b))
     inf = h.info()
-    if mode == 1:
+    if mode == 3:
+        # one repair pass per refactorization that repivots, no complete pass
+        assert rounds == 3 and inf["full_refactors"] == 0
+    elif mode == 0:
+        assert rounds > 0
+    elif mode == 1:
         assert rounds > 0 and inf["full_refactors"] == 0
     else:
         assert rounds == 0 and inf["full_refactors"] == 3   # every step repivots (checked on the oracle)
@@ -290,7 +297,8 @@ def test_config2_factor_refactor_solve():
     h = basker.Handle.from_problem(prob)
     h.factor(_dev(prob.values))
     assert_same_factors(h, f)
-    for k in (1, 2):
+    # draw 4 rejects a cascade of consecutive pivots in one leaf
+    for k in (1, 2, 3, 4, 5):
         v = I.refactor_values(prob, k)
         assert o.factor(v, pref=f.prow) == "OK"
         f = o.factors()
