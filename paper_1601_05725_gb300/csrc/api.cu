@@ -50,6 +50,10 @@ struct basker_s {
     int32_t *rp_tasks = nullptr;
     int32_t rp_ntasks = 0, rp_ctas = 0;
     size_t rp_smem = 0;
+    // the separators' descendant phase on stored patterns: the columns left to the
+    // reach kernel (listed on the device) and the fast kernel's shared memory
+    int32_t *df_redo = nullptr;
+    size_t df_smem = 0;
     // the arena as the symbolic pass left it (natural pivots, symbolic pattern and
     // schedule): a factorization first tries the stored-pattern path from it
     int32_t *sym_Li = nullptr, *sym_Ui = nullptr, *sym_n = nullptr;   // sym_n: 8 arrays of n ints
@@ -476,6 +480,8 @@ int setup_device(basker_t h)
     TRY(dalloc(h, &h->rd_tasks, (size_t)std::max<size_t>(pl.tasks.size(), 1)));
     TRY(dalloc(h, &h->rd_c0, (size_t)std::max<size_t>(pl.tasks.size(), 1)));
     TRY(dalloc(h, &h->rd_cols, (size_t)std::max(n, 1)));
+    TRY(dalloc(h, &h->df_redo, (size_t)std::max(n, 1)));
+    h->df_smem = bk_desc_fast_smem(pl.tasks.data(), (int32_t)pl.tasks.size());
     CU(cudaMallocHost((void **)&h->h_stage, sizeof(int32_t) * ((size_t)n + 4 * pl.tasks.size() + 16)));
     CU(cudaMallocHost((void **)&h->h_status, sizeof(bk_status)));
     CU(cudaMallocHost((void **)&h->h_task_fail, sizeof(int32_t) * std::max<size_t>(pl.tasks.size(), 1)));
@@ -572,6 +578,25 @@ int regrow(basker_t h)
     TRY(alloc_factors(h));
     h->info.capacity_regrows++;
     h->ws_dirty = true;
+    return BASKER_OK;
+}
+
+// The descendant phase of separator columns cols[0..ncols) in a refactorization:
+// first on their stored patterns (verified on the device), then the reach kernel
+// over the columns that failed (their list and count stay on the device).
+int launch_desc_refactor(basker_t h, const int32_t *cols, int32_t ncols, cudaStream_t s)
+{
+    if (ncols <= 0) return BASKER_OK;
+    CU(cudaMemsetAsync(h->d.counter + 5, 0, sizeof(int32_t), s));
+    CU(cudaMemsetAsync(h->d.counter + 7, 0, sizeof(int32_t), s));
+    CU(cudaMemsetAsync(h->d.counter + 3, 0, sizeof(int32_t), s));
+    tbeg(h, KT_DESC, s, 2);
+    bk_launch_desc_fast(h->d, cols, ncols, h->d.counter + 5, h->df_redo, h->d.counter + 7, h->df_smem, s);
+    CU(cudaGetLastError());
+    bk_launch_gp_desc(h->d, h->df_redo, ncols, h->d.counter + 3, s, h->d.counter + 7);
+    CU(cudaGetLastError());
+    tend(h, s);
+    h->launches += 2;
     return BASKER_OK;
 }
 
@@ -686,11 +711,7 @@ int launch_redo(basker_t h, cudaStream_t s)
                 TRY(stage_upload(h, s, h->rd_cols, cols, 0));
                 TRY(stage_upload(h, s, h->rd_tasks, dense[0], (size_t)pl.n));
                 TRY(stage_upload(h, s, h->rd_tasks + dense[0].size(), dense[1], (size_t)pl.n + dense[0].size()));
-                CU(cudaMemsetAsync(h->d.counter + 3, 0, sizeof(int32_t), s));
-                tbeg(h, KT_DESC, s, 1);
-                bk_launch_gp_desc(h->d, h->rd_cols, (int32_t)cols.size(), h->d.counter + 3, s);
-                CU(cudaGetLastError());
-                tend(h, s);
+                TRY(launch_desc_refactor(h, h->rd_cols, (int32_t)cols.size(), s));
                 for (int g = 0; g < 2; g++) {
                     if (dense[g].empty()) continue;
                     tbeg(h, KT_DENSE, s, 1);
@@ -787,14 +808,7 @@ int launch_repair_path(basker_t h, cudaStream_t s)
     tend(h, s);
     h->launches++;
     for (size_t l = 1; l < h->lv_tasks.size(); l++) {
-        if (h->lv_ncols[l] > 0) {
-            CU(cudaMemsetAsync(h->d.counter + 3, 0, sizeof(int32_t), s));
-            tbeg(h, KT_DESC, s, 1);
-            bk_launch_gp_desc(h->d, h->lv_cols[l], h->lv_ncols[l], h->d.counter + 3, s);
-            CU(cudaGetLastError());
-            tend(h, s);
-            h->launches++;
-        }
+        TRY(launch_desc_refactor(h, h->lv_cols[l], h->lv_ncols[l], s));
         for (int g = 0; g < 2; g++) {
             if (h->lv_ndense[g][l] == 0) continue;
             tbeg(h, KT_DENSE, s, 1);
@@ -811,11 +825,13 @@ int launch_repair_path(basker_t h, cudaStream_t s)
 int compute_schedule(basker_t h, cudaStream_t s)
 {
     h->epoch++;
-    tbeg(h, KT_LEVELS, s, 4);
-    bk_launch_levels(h->d, h->epoch, h->opt.wait_budget_cycles, static_blocks(h), s);
+    tbeg(h, KT_LEVELS, s, 5);
+    // the stored levels are kept when they still order the new pattern (checked on
+    // the device: a refactorization usually changes few columns)
+    bk_launch_levels(h->d, h->epoch, h->opt.wait_budget_cycles, static_blocks(h), s, true);
     CU(cudaGetLastError());
     tend(h, s);
-    h->launches += 4;
+    h->launches += 5;
     CU(cudaGetLastError());
     h->schedule_valid = true;
     h->order_is_symbolic = false;

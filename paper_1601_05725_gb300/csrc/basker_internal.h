@@ -172,13 +172,21 @@ bool bk_task_fits_smem(const bk_task &t);
 void bk_launch_gather(const bk_dev &d, const double *values, int64_t nnz, void *stream);
 void bk_launch_gp_tasks(const bk_dev &d, const int32_t *task_ids, const int32_t *task_c0,
                         int32_t ntasks, size_t smem, double tau, int pref_mode, void *stream);
+// ncols_dev (if not null): the number of columns, read on the device (ncols is
+// then the largest it can be, for the launch size)
 void bk_launch_gp_desc(const bk_dev &d, const int32_t *cols, int32_t ncols, int32_t *counter,
-                       void *stream);
+                       void *stream, const int32_t *ncols_dev = nullptr);
+// kernels_desc.cu: the descendant phase on the stored patterns, verified; the
+// columns that fail are listed in redo[0 .. *nredo) for bk_launch_gp_desc
+size_t bk_desc_fast_smem(const bk_task *tasks, int32_t ntasks);
+void bk_launch_desc_fast(const bk_dev &d, const int32_t *cols, int32_t ncols, int32_t *counter, int32_t *redo,
+                         int32_t *nredo, size_t smem, void *stream);
 void bk_launch_dd(const bk_dev &d, const int32_t *cols, int32_t ncols, int32_t *counter, double tau,
                   int32_t epoch, long long budget, int32_t refno, void *stream, int max_warps = 0);
 void bk_launch_static(const bk_dev &d, int32_t ncols, double tau, int32_t epoch,
                       long long budget, int blocks, void *stream);
-void bk_launch_levels(const bk_dev &d, int32_t epoch, long long budget, int blocks, void *stream);
+void bk_launch_levels(const bk_dev &d, int32_t epoch, long long budget, int blocks, void *stream,
+                      bool check = false);
 int bk_static_blocks();
 // kernels_repair.cu: the rejected pivots of the ND leaves and BTF blocks resolved
 // in column order after the stored-pattern pass (one warp per task)

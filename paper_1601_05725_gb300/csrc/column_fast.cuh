@@ -20,6 +20,7 @@
 
 #include "basker_internal.h"
 #include "device_util.cuh"
+#include "trace.cuh"
 
 namespace bk {
 
@@ -222,13 +223,53 @@ __device__ __forceinline__ bool fc_nonfinite(float v) { return (__float_as_int(v
 // inside a batch the next step's metadata and first entry are read ahead, so
 // that a step's chain is x(prow j), the fmas and the barrier.  x(prow j) is not cleared
 // here (no later step reads it; the caller clears the pattern).  red: shared
-// scratch of NT / 32 ints.
+// scratch of NT / 32 ints.  allow (if not null): an entry whose slot lies below
+// nallow must have its bit set there, else vfail is set (the stored steps are
+// not the reach; the caller falls back).  map (if not null): x and mark are
+// indexed by a compact index instead of the slot: map.find(slot) for slots below
+// nallow (-1: not there, vfail), map.shift + slot for the others.
+struct FcMap {
+    const int32_t *keys, *vals;
+    int mask, shift;
+    __device__ __forceinline__ int find(int s) const
+    {
+        int h = (int)(((unsigned)s * 2654435761u) >> 7) & mask;
+        for (int probe = 0; probe <= mask; probe++) {
+            const int k = keys[h];
+            if (k == s) return vals[h];
+            if (k < 0) return -1;
+            h = (h + 1) & mask;
+        }
+        return -1;
+    }
+};
+
 template <typename V, bool MARK, int NT>
 __device__ __forceinline__ bool column_fast_update_cta(const bk_dev &d, const bk_task &T, int base,
                                                        const int32_t *Ulist, int ns, V *Uout, V *x,
                                                        FcSmem<V> &S, unsigned char *mark, int *red, int tid,
-                                                       bool &bad)
+                                                       bool &bad, const uint32_t *allow = nullptr, int nallow = 0,
+                                                       bool *vfail = nullptr, const FcMap *map = nullptr)
 {
+#ifdef BK_TRACE
+    long long cy[6] = {0, 0, 0, 0, 0, 0};   // metadata, batch bounds + copies, wait, conversion, apply, tail
+    long long cyt = clock64();
+#define FC_LAP(i)                        \
+    do {                                 \
+        const long long now = clock64(); \
+        cy[i] += now - cyt;              \
+        cyt = now;                       \
+    } while (0)
+#else
+#define FC_LAP(i)
+#endif
+    auto remap = [&](int sl, bool &vf) -> int {
+        if (!map || sl < 0) return sl;
+        if (sl >= nallow) return map->shift + sl;
+        const int ix = map->find(sl);
+        if (ix < 0) vf = true;
+        return ix;
+    };
     static_assert(NT == FC_SEG, "one step's metadata a thread");
     const int lane = tid & 31, warp = tid >> 5;
     const V *const Lx = vals<V>(d.Lx);
@@ -240,8 +281,11 @@ __device__ __forceinline__ bool column_fast_update_cta(const bk_dev &d, const bk
             const int j = __ldcg(Ulist + k0 + tid);
             const int64_t jl = __ldcg(d.Lbeg + j);
             jc = __ldcg(d.Lcnt + j);
-            const int sp = slot_of(T, base, __ldcg(d.prow + j));
+            int sp = slot_of(T, base, __ldcg(d.prow + j));
             if (sp < 0) broken = true;
+            bool vf = false;
+            sp = remap(sp, vf);
+            if (vf) *vfail = true;
             S.j[tid] = j;
             S.jl[tid] = jl;
             S.jc[tid] = jc;
@@ -259,6 +303,7 @@ __device__ __forceinline__ bool column_fast_update_cta(const bk_dev &d, const bk
         if (tid < nseg) S.off[tid] = wofs + pre;
         if (tid == 0) S.off[nseg] = E;
         __syncthreads();
+        FC_LAP(0);
         // the batch starting at step bs: as many steps as fit one buffer (at least
         // one); the steps that fit form a prefix, so their count decides
         auto batch_end = [&](int bs) {
@@ -285,13 +330,12 @@ __device__ __forceinline__ bool column_fast_update_cta(const bk_dev &d, const bk
         issue(bs, be, 0);
         while (bs < nseg) {
             const int nbs = be, nbe = nbs < nseg ? batch_end(nbs) : nbs;
-            if (nbs < nseg) {
-                issue(nbs, nbe, buf ^ 1);
-                fc_wait_prev();
-            } else {
-                fc_wait_all();
-            }
+            if (nbs < nseg) issue(nbs, nbe, buf ^ 1);
+            FC_LAP(1);
+            if (nbs < nseg) fc_wait_prev();
+            else fc_wait_all();
             __syncthreads();
+            FC_LAP(2);
             const int e0 = S.off[bs], e1 = S.off[be];
             const bool direct = e1 - e0 > FC_CAP;
             int32_t *const bi = S.bi[buf];
@@ -299,12 +343,16 @@ __device__ __forceinline__ bool column_fast_update_cta(const bk_dev &d, const bk
             if (!direct) {
                 // the batch's rows become slots (once, all threads), so that the
                 // step chain below has no slot search in it
+                bool vf = false;
                 for (int e = e0 + tid; e < e1; e += NT) {
                     const int sl = slot_of(T, base, bi[e - e0]);
                     if (sl < 0) broken = true;
-                    bi[e - e0] = sl;
+                    else if (allow && sl < nallow && !((allow[sl >> 5] >> (sl & 31)) & 1u)) vf = true;
+                    bi[e - e0] = remap(sl, vf);
                 }
+                if (vf) *vfail = true;
                 __syncthreads();
+                FC_LAP(3);
                 // steps; the next step's metadata and this thread's first entry of
                 // it are read while the current step is applied
                 int sp_n = S.sp[bs], a_n = S.off[bs], z_n = S.off[bs + 1];
@@ -361,21 +409,32 @@ __device__ __forceinline__ bool column_fast_update_cta(const bk_dev &d, const bk
                 if (tid == 0) S.u[t] = m;
                 if (fc_nonfinite(m)) bad = true;
                 for (int q = a + tid; q < z; q += NT) {
-                    const int sq = slot_of(T, base, __ldcg(d.Li + gl + q));
+                    int sq = slot_of(T, base, __ldcg(d.Li + gl + q));
                     const V lq = __ldcg(Lx + gl + q);
                     if (sq < 0) { broken = true; continue; }
+                    if (allow && sq < nallow && !((allow[sq >> 5] >> (sq & 31)) & 1u)) *vfail = true;
+                    bool vf = false;
+                    sq = remap(sq, vf);
+                    if (vf) { *vfail = true; continue; }
                     x[sq] = fma(-lq, m, x[sq]);
                     if (MARK) mark[sq] = 1;
                 }
                 __syncthreads();
             }
+            FC_LAP(4);
             bs = nbs;
             be = nbe;
             buf ^= 1;
         }
         for (int q = tid; q < nseg; q += NT) Uout[k0 + q] = S.u[q];
         __syncthreads();
+        FC_LAP(5);
     }
+#ifdef BK_TRACE
+    if (tid == 0)
+        for (int i = 0; i < 6; i++) bk_trace_raw(d.trace, BK_TR_PHASE, 20 + i, ns, 0ull, (unsigned long long)cy[i]);
+#endif
+#undef FC_LAP
     return !__syncthreads_or(broken);
 }
 }  // namespace bk

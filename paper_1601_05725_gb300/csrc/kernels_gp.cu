@@ -400,8 +400,10 @@ __global__ void __launch_bounds__(32) bk_gp_task_kernel(bk_dev d, const int32_t 
 // bitmap covers descendant steps [sp_lo, lo) only.
 template <typename V>
 __global__ void __launch_bounds__(128) bk_gp_desc_kernel(bk_dev d, const int32_t *__restrict__ cols,
-                                                         int32_t ncols, int32_t *counter)
+                                                         int32_t ncols, int32_t *counter,
+                                                         const int32_t *__restrict__ ncols_dev)
 {
+    if (ncols_dev) ncols = *ncols_dev;      // a list made on the device (columns left by the fast path)
     const V *const Bx = vals<V>(d.Bx);
     V *const Lx = vals<V>(d.Lx);
     V *const Ux = vals<V>(d.Ux);
@@ -593,13 +595,15 @@ void bk_launch_gp_tasks(const bk_dev &d, const int32_t *task_ids, const int32_t 
 }
 
 void bk_launch_gp_desc(const bk_dev &d, const int32_t *cols, int32_t ncols, int32_t *counter,
-                       void *stream)
+                       void *stream, const int32_t *ncols_dev)
 {
     if (ncols <= 0) return;
     int warps = std::min<int>(ncols, d.wsd_warps);
     if (d.prec)
-        bk_gp_desc_kernel<float><<<(warps + 3) / 4, 128, 0, (cudaStream_t)stream>>>(d, cols, ncols, counter);
+        bk_gp_desc_kernel<float><<<(warps + 3) / 4, 128, 0, (cudaStream_t)stream>>>(d, cols, ncols, counter,
+                                                                                   ncols_dev);
     else
-        bk_gp_desc_kernel<double><<<(warps + 3) / 4, 128, 0, (cudaStream_t)stream>>>(d, cols, ncols, counter);
+        bk_gp_desc_kernel<double><<<(warps + 3) / 4, 128, 0, (cudaStream_t)stream>>>(d, cols, ncols, counter,
+                                                                                    ncols_dev);
 }
 

@@ -528,6 +528,7 @@ __global__ void __launch_bounds__(128) bk_solve_kernel(bk_dev d, bk_solve_dev s,
             int32_t *flags = fwd ? s.fdone : s.bdone;
             for (int r0 = lo; r0 < hi; r0 += 32)
                 if (!wait_flags(d, flags, r0 + lane, r0 + lane < hi, -epoch, budget)) return;
+            BK_TPHASE0(tp);
             for (int q = 0; q < nrhs; q++) {
                 V *vq = (fwd ? w : zz) + q * n;
                 V *zs = nown <= SEP_SMEM_ROWS ? zsm : vq + lo;
@@ -546,6 +547,7 @@ __global__ void __launch_bounds__(128) bk_solve_kernel(bk_dev d, bk_solve_dev s,
             __syncwarp();
             for (int r = lo + lane; r < hi; r += 32) st_release(flags + r, epoch);
             if (lane == 0) BK_TREC(d.trace, BK_TR_SOLVE, fwd ? 2 : 3, i - n, t0);
+            BK_TPHASE(d.trace, tp, fwd ? 10 : 11, i - n);     // the sweep itself
             continue;
         }
         // a separator's row takes only the terms from outside its node

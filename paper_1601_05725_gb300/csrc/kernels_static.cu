@@ -75,9 +75,29 @@ __global__ void __launch_bounds__(128) bk_static_kernel(bk_dev d, int32_t ncols,
     }
 }
 
-__global__ void __launch_bounds__(128) bk_levels_kernel(bk_dev d, int32_t epoch, long long budget,
-                                                        int32_t *maxlev)
+// The stored levels are still a topological order of the current pattern if
+// every step of every U(:,c) has a lower level than c; any violation sets *stale.
+__global__ void bk_level_check_kernel(bk_dev d, int32_t *stale)
 {
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    bool bad = false;
+    for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < d.n; c += warps) {
+        const int64_t ub = d.Ubeg[c];
+        const int uc = d.Ucnt[c];
+        const int lc = __ldg(d.level + c);
+        for (int q = lane; q < uc - 1; q += 32) {
+            const int j = d.Ui[ub + q];
+            if ((unsigned)j >= (unsigned)d.n || __ldg(d.level + j) >= lc) bad = true;
+        }
+    }
+    if (__any_sync(BK_FULL, bad) && lane == 0) atomicExch(stale, 1);
+}
+
+__global__ void __launch_bounds__(128) bk_levels_kernel(bk_dev d, int32_t epoch, long long budget,
+                                                        int32_t *maxlev, const int32_t *stale)
+{
+    if (!*stale) return;                 // the stored levels still hold
     const int lane = threadIdx.x & 31;
     for (;;) {
         int c = 0;
@@ -120,15 +140,17 @@ __global__ void __launch_bounds__(128) bk_levels_kernel(bk_dev d, int32_t epoch,
     }
 }
 
-__global__ void bk_level_count(const int32_t *__restrict__ level, int32_t n, int32_t *cnt)
+__global__ void bk_level_count(const int32_t *__restrict__ level, int32_t n, int32_t *cnt, const int32_t *stale)
 {
+    if (!*stale) return;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x)
         atomicAdd(cnt + level[c], 1);
 }
 
 // Exclusive scan of cnt[0..m) in place, one block of 1024 threads.
-__global__ void __launch_bounds__(1024) bk_level_scan(int32_t *cnt, int32_t m)
+__global__ void __launch_bounds__(1024) bk_level_scan(int32_t *cnt, int32_t m, const int32_t *stale)
 {
+    if (!*stale) return;
     __shared__ int part[1024];
     const int t = threadIdx.x;
     const int chunk = (m + 1023) / 1024;
@@ -152,8 +174,9 @@ __global__ void __launch_bounds__(1024) bk_level_scan(int32_t *cnt, int32_t m)
 }
 
 __global__ void bk_level_scatter(const int32_t *__restrict__ level, int32_t n, int32_t *cursor,
-                                 int32_t *order)
+                                 int32_t *order, const int32_t *stale)
 {
+    if (!*stale) return;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x)
         order[atomicAdd(cursor + level[c], 1)] = c;
 }
@@ -184,17 +207,26 @@ void bk_launch_static(const bk_dev &d, int32_t ncols, double tau, int32_t epoch,
 }
 
 // Levels of the current pattern's column DAG and the claim order sorted by level.
-// scratch: n + 2 ints (counts), last one receives the maximum level.
-void bk_launch_levels(const bk_dev &d, int32_t epoch, long long budget, int blocks, void *stream)
+// scratch: n + 2 ints (counts), last one receives the maximum level.  With
+// check, the stored levels are kept (and nothing else runs) when they are still
+// a topological order of the pattern; the decision stays on the device.
+void bk_launch_levels(const bk_dev &d, int32_t epoch, long long budget, int blocks, void *stream, bool check)
 {
     cudaStream_t s = (cudaStream_t)stream;
     int32_t *cnt = d.level + d.n;               // level array holds n + (n + 2) ints
     int32_t *maxlev = cnt + d.n + 1;
+    int32_t *stale = d.counter + 6;
+    int g = std::max(1, std::min((d.n + 255) / 256, 152 * 8));
+    if (check) {
+        cudaMemsetAsync(stale, 0, sizeof(int32_t), s);
+        bk_level_check_kernel<<<std::max(1, std::min((d.n + 7) / 8, 152 * 16)), 256, 0, s>>>(d, stale);
+    } else {
+        cudaMemsetAsync(stale, 0xff, sizeof(int32_t), s);
+    }
     cudaMemsetAsync(cnt, 0, sizeof(int32_t) * ((size_t)d.n + 2), s);
     cudaMemsetAsync(d.counter + 1, 0, sizeof(int32_t), s);
-    bk_levels_kernel<<<blocks, 128, 0, s>>>(d, epoch, budget, maxlev);
-    int g = std::max(1, std::min((d.n + 255) / 256, 152 * 8));
-    bk_level_count<<<g, 256, 0, s>>>(d.level, d.n, cnt);
-    bk_level_scan<<<1, 1024, 0, s>>>(cnt, d.n + 1);
-    bk_level_scatter<<<g, 256, 0, s>>>(d.level, d.n, cnt, d.order);
+    bk_levels_kernel<<<blocks, 128, 0, s>>>(d, epoch, budget, maxlev, stale);
+    bk_level_count<<<g, 256, 0, s>>>(d.level, d.n, cnt, stale);
+    bk_level_scan<<<1, 1024, 0, s>>>(cnt, d.n + 1, stale);
+    bk_level_scatter<<<g, 256, 0, s>>>(d.level, d.n, cnt, d.order, stale);
 }

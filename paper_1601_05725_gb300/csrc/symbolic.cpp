@@ -551,7 +551,10 @@ void bk_plan_layout(bk_plan &pl)
     for (auto &T : pl.tasks) {
         T.ahoff = T.aboff = 0;
         const int64_t own = T.hi - T.lo, words = (T.lspace + 31) / 32;
-        int64_t sl = (int64_t)T.space * 8 + ((int64_t)(T.hi - T.sp_lo) + 31) / 32 * 4 + words * 4;
+        // x over the space, then the reach's step and row bitmaps, or (the
+        // descendant phase on stored patterns) a mark byte per slot
+        int64_t sl = (int64_t)T.space * 8 +
+                     std::max<int64_t>(((int64_t)(T.hi - T.sp_lo) + 31) / 32 * 4 + words * 4, (int64_t)T.space);
         slice = std::max(slice, (sl + 255) & ~(int64_t)255);
         level_cols[(size_t)T.level] += own;
         if (T.sp_lo >= T.lo) continue;

@@ -37,6 +37,19 @@ __device__ __forceinline__ void bk_trace_rec(unsigned long long *buf, int kind, 
     r[2] = t1;
     r[3] = ((unsigned long long)sm << 32) | ((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
 }
+// a record whose two time fields carry other numbers (cycle counts)
+__device__ __forceinline__ void bk_trace_raw(unsigned long long *buf, int kind, int mode, int id,
+                                             unsigned long long a, unsigned long long b)
+{
+    if (!buf) return;
+    const unsigned long long i = atomicAdd(buf, 1ull);
+    if (i >= BK_TRACE_CAP) return;
+    unsigned long long *r = buf + 4 + 4 * i;
+    r[0] = ((unsigned long long)kind << 56) | ((unsigned long long)(mode & 0xff) << 48) | (unsigned)id;
+    r[1] = a;
+    r[2] = b;
+    r[3] = 0;
+}
 #define BK_TSTART(v) const unsigned long long v = bk_gtime()
 #define BK_TREC(buf, kind, mode, id, t0) bk_trace_rec(buf, kind, mode, id, t0)
 // phases inside one item: v holds the start of the current phase
