@@ -490,6 +490,9 @@ int setup_device(basker_t h)
     bk_solve_dev &s = h->sd;
     s.nitems = (int32_t)h->sp.items.size();
     TRY(upload(h, &s.items, h->sp.items));
+    s.nsweeps = (int32_t)h->sp.sweeps.size();
+    TRY(upload(h, (int32_t **)&s.sweeps, h->sp.sweeps));
+    bk_solve_sweep_setup(s, h->sp.sw_maxm);
     TRY(upload(h, (int32_t **)&s.offp, h->sp.offp));
     TRY(upload(h, (int32_t **)&s.offj, h->sp.offj));
     TRY(upload(h, (int32_t **)&s.offpos, h->sp.offpos));

@@ -340,13 +340,10 @@ __global__ void bk_leaf_scatter(bk_dev d, bk_solve_dev s)
 
 // ---------------------------------------------------------------- the solve
 
-// Bounded wait until flags[j] == epoch for every lane with want.  Each lane
-// checks its flag once; lane 0 alone then polls the flags still unset, in lane
-// order (one poller per warp, and no rereads of the other flags meanwhile), and
-// finally each of those lanes rereads its own flag with an acquiring load, which
-// orders its later reads.  False if a wait ran out (the timeout status is then
-// set).
-__device__ __forceinline__ bool lane0_poll(const bk_dev &d, const int32_t *flag, int epoch, long long budget)
+// One lane's bounded wait until *flag == epoch (an acquiring load, which orders
+// the lane's later reads), sleeping between polls.  False if the wait ran out
+// (the timeout status is then set).
+__device__ __forceinline__ bool poll_flag(const bk_dev &d, const int32_t *flag, int epoch, long long budget)
 {
     const long long t0 = clock64();
     unsigned ns = 32;
@@ -356,11 +353,16 @@ __device__ __forceinline__ bool lane0_poll(const bk_dev &d, const int32_t *flag,
             return false;
         }
         __nanosleep(ns);
-        ns = min(ns * 2, 256u);
+        ns = min(ns * 2, 128u);
     }
     return true;
 }
 
+// Bounded wait until flags[j] == epoch for every lane with want.  Each lane
+// checks its flag once; lane 0 alone then polls the flags still unset, in lane
+// order (one poller per warp, and no rereads of the other flags meanwhile), and
+// finally each of those lanes rereads its own flag with an acquiring load, which
+// orders its later reads.  False if a wait ran out.
 __device__ __forceinline__ bool wait_flags(const bk_dev &d, const int32_t *flags, int j, bool want, int epoch,
                                            long long budget)
 {
@@ -370,129 +372,230 @@ __device__ __forceinline__ bool wait_flags(const bk_dev &d, const int32_t *flags
     int ok = 1;
     for (uint32_t p = pending; p; p &= p - 1) {
         const int jt = __shfl_sync(BK_FULL, j, __ffs(p) - 1);
-        if (lane == 0 && ok) ok = lane0_poll(d, flags + jt, epoch, budget);
+        if (lane == 0 && ok) ok = poll_flag(d, flags + jt, epoch, budget);
     }
     if (!__shfl_sync(BK_FULL, ok, 0)) return false;
     int mine = 1;
-    if ((pending >> lane) & 1u) mine = lane0_poll(d, flags + j, epoch, budget);
+    if ((pending >> lane) & 1u) mine = poll_flag(d, flags + j, epoch, budget);
     return __all_sync(BK_FULL, mine);
 }
 
-// z -= sum over up to 32 terms a_t * v_t, in lane order (every lane computes the
-// same chain).
+// z -= sum over up to 32 terms a_t * v_t, v_t = vals[j_t] once flags[j_t] ==
+// epoch, in lane order (every lane computes the same chain).  The terms whose
+// flags are set are applied as soon as every earlier term is, and the first term
+// still waited for is polled by its own lane: the term that arrives last (in a
+// chain of rows, the previous row) costs one fma after its flag, not a batch.
+// False if a wait ran out (the timeout status is then set).
 template <typename V>
-__device__ __forceinline__ V chain(V z, V a, V v, int cnt)
+__device__ __forceinline__ bool chain_wait(const bk_dev &d, const int32_t *flags, const V *vals, int j, bool have,
+                                           V a, int cnt, int epoch, long long budget, V &z)
 {
-    for (int t = 0; t < cnt; t++) z = fma(-__shfl_sync(BK_FULL, a, t), __shfl_sync(BK_FULL, v, t), z);
-    return z;
+    const int lane = threadIdx.x & 31;
+    bool ready = !have || ld_acquire(flags + j) == epoch;
+    V v = (have && ready) ? __ldcg(vals + j) : V(0);
+    for (int done = 0;;) {
+        const uint32_t nr = __ballot_sync(BK_FULL, !ready);
+        const int upto = nr ? __ffs(nr) - 1 : cnt;
+        for (int t = done; t < upto; t++) z = fma(-__shfl_sync(BK_FULL, a, t), __shfl_sync(BK_FULL, v, t), z);
+        if (upto >= cnt) return true;
+        done = upto;
+        int ok = 1;
+        if (lane == done) {
+            ok = poll_flag(d, flags + j, epoch, budget);
+            if (ok) {
+                v = __ldcg(vals + j);
+                ready = true;
+            }
+        }
+        if (!__shfl_sync(BK_FULL, ok, done)) return false;
+        if (!ready && ld_acquire(flags + j) == epoch) {
+            v = __ldcg(vals + j);
+            ready = true;
+        }
+    }
 }
 
-// One warp solves a separator's own triangle, its rows' outside terms already
-// applied (the rows' values are in zs, in shared memory or in place in global
+// ---------------------------------------------------------------- separator sweeps
+//
+// One block solves a separator's own triangle, its rows' outside terms already
+// applied (the rows' values in zs, in shared memory or in place in global
 // memory).  Forward: for k ascending, w_k = zs[k] is final and L(i,k) w_k is
 // subtracted from the node's rows i > k; backward: for k descending, z_k =
 // zs[k] / U(k,k) is final and U(j,k) z_k is subtracted from the node's rows
 // j < k.  Per row the terms come in the order of the row sweeps (ascending k
-// forward, descending backward), after the outside terms.
-// The node's own entries of a column, read ahead: up to SW_PF * 32 entries of
-// L(:,k) from its start (own rows come before ancestor rows) or of U(:,k) from
-// just above its diagonal downwards (own steps come after descendant steps).
-constexpr int SW_PF = 8;
+// forward, descending backward), after the outside terms; each step's terms go
+// to distinct rows, spread over the block's threads, with one barrier a step.
+// A column's own entries (the first ones of L(:,k), the last ones above the
+// diagonal of U(:,k)) are copied into shared memory SW_P - 1 steps ahead
+// (cp.async, a ring of SW_P stages of sw_win entries), and the columns' extents
+// 2 SW_P steps ahead, so that a step waits for no global load.
+constexpr int SW_NT = 128;     // threads of a block (the kernel's block size)
+constexpr int SW_P = 8;        // pipeline stages
+constexpr int SW_MR = 4 * SW_P;  // ring of column extents
+constexpr int SW_WMAX = 448;   // most entries of a column a stage holds
+constexpr int SW_MAXB = 64;    // most sweeper blocks
+constexpr int SEP_SMEM_ROWS = 1024;   // most rows of a node swept in shared memory
 
-template <typename V>
-struct SweepCol {
-    int row[SW_PF];   // node-local row (-1: none)
-    V val[SW_PF];
-    int cnt;          // entries of the column (L) or strictly above the diagonal (U)
-    int64_t beg;
-    V diag;           // U(k,k) (backward only)
+__host__ __device__ constexpr size_t sw_align(size_t b) { return (b + 15) & ~(size_t)15; }
+
+struct SwLayout {
+    size_t ri, rv, rd, mb, mc, total;
 };
 
-// Every lane loads the same words (one transaction): no shuffle waits for them, so
-// the loads stay in flight until the values are used a step later.
-template <typename V>
-__device__ __forceinline__ void sweep_meta(const bk_dev &d, int k, bool lower, int64_t &beg, int &cnt, int lane)
+__host__ __device__ inline SwLayout sw_layout(int win, int zrows, size_t vsize)
 {
-    beg = lower ? d.Lbeg[k] : d.Ubeg[k];
-    cnt = lower ? d.Lcnt[k] : d.Ucnt[k];
+    SwLayout L;
+    L.ri = sw_align((size_t)zrows * vsize);
+    L.rv = L.ri + (size_t)SW_P * win * 4;
+    L.rd = L.rv + (size_t)SW_P * win * vsize;
+    L.mb = L.rd + sw_align((size_t)SW_P * vsize);
+    L.mc = L.mb + (size_t)SW_MR * 8;
+    L.total = L.mc + (size_t)SW_MR * 4;
+    return L;
+}
+
+__device__ __forceinline__ void sw_cp4(void *dst, const void *src)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void sw_cp8(void *dst, const void *src)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(src) : "memory");
 }
 
 template <typename V>
-__device__ __forceinline__ void sweep_read(const bk_dev &d, const bk_solve_dev &s, SweepCol<V> &col, int64_t beg,
-                                           int cnt, bool lower, int lo, int hi, int lane)
+__device__ __forceinline__ void sw_cpv(V *dst, const V *src)
 {
+    if (sizeof(V) == 8) sw_cp8(dst, src);
+    else sw_cp4(dst, src);
+}
+
+__device__ __forceinline__ void sw_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void sw_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+template <typename V>
+__device__ void sep_sweep_block(const bk_dev &d, const bk_solve_dev &s, int it, int nrhs, double *x, int ldx,
+                                int epoch, long long budget, const int32_t *Qout, unsigned char *smem)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t n = d.n;
+    const bool fwd = it >= 0;
+    const int t = (fwd ? it : ~it) - (int)n;
+    const int lo = d.tasks[t].lo, hi = d.tasks[t].hi, m = hi - lo;
+    const int W = s.sw_win;
     const V *const Lx = vals<V>(d.Lx);
     const V *const Ux = vals<V>(d.Ux);
-    col.beg = beg;
-    col.cnt = lower ? cnt : cnt - 1;
-    if (!lower) col.diag = Ux[beg + cnt - 1];
-#pragma unroll
-    for (int u = 0; u < SW_PF; u++) {
-        const int t = lane + 32 * u;
-        col.row[u] = -1;
-        col.val[u] = V(0);
-        if (t >= col.cnt) continue;
-        const int64_t e = lower ? beg + t : beg + col.cnt - 1 - t;
-        const int i = lower ? s.r.Ls[e] : d.Ui[e];
-        const V v = lower ? Lx[e] : Ux[e];           // read with the index, not after it
-        if (lower ? i < hi : i >= lo) {
-            col.row[u] = i - lo;
-            col.val[u] = v;
+    V *const w = vals<V>(s.w);
+    V *const zz = vals<V>(s.z);
+    const SwLayout Ly = sw_layout(W, s.sw_zrows, sizeof(V));
+    V *const zsm = reinterpret_cast<V *>(smem);
+    int32_t *const ri = reinterpret_cast<int32_t *>(smem + Ly.ri);
+    V *const rv = reinterpret_cast<V *>(smem + Ly.rv);
+    V *const rd = reinterpret_cast<V *>(smem + Ly.rd);
+    int64_t *const mb = reinterpret_cast<int64_t *>(smem + Ly.mb);
+    int32_t *const mc = reinterpret_cast<int32_t *>(smem + Ly.mc);
+    BK_TSTART(t0);
+    int32_t *flags = fwd ? s.fdone : s.bdone;
+    bool ok = true;
+    for (int r0 = lo + 32 * warp; r0 < hi && ok; r0 += SW_NT)
+        ok = wait_flags(d, flags, r0 + lane, r0 + lane < hi, -epoch, budget);
+    if (__syncthreads_or(!ok)) return;
+    BK_TPHASE0(tp);
+    // the column at sweep position p, and its own entries held by a stage
+    auto col_of = [&](int p) { return lo + (fwd ? p : m - 1 - p); };
+    auto own_win = [&](int p, int cnt) {
+        const int kl = fwd ? p : m - 1 - p;
+        return fwd ? min(min(cnt, m - 1 - kl), W) : min(min(cnt - 1, kl), W);
+    };
+    auto issue = [&](int p) {
+        const int slot = p % SW_MR, st = p % SW_P;
+        const int64_t beg = mb[slot];
+        const int cnt = mc[slot];
+        const int wn = own_win(p, cnt);
+        const int64_t g0 = fwd ? beg : beg + cnt - 1 - wn;
+        for (int e = tid; e < wn; e += SW_NT) {
+            sw_cp4(ri + st * W + e, (fwd ? s.r.Ls : d.Ui) + g0 + e);
+            sw_cpv(rv + st * W + e, (fwd ? Lx : Ux) + g0 + e);
         }
+        if (!fwd && tid == 0) sw_cpv(rd + st, Ux + beg + cnt - 1);
+    };
+    for (int q = 0; q < nrhs; q++) {
+        V *vq = (fwd ? w : zz) + q * n;
+        V *zs = m <= s.sw_zrows ? zsm : vq + lo;
+        if (zs == zsm)
+            for (int r = tid; r < m; r += SW_NT) zs[r] = __ldcg(vq + lo + r);
+        for (int p = tid; p < min(2 * SW_P, m); p += SW_NT) {
+            const int c = col_of(p);
+            mb[p % SW_MR] = fwd ? d.Lbeg[c] : d.Ubeg[c];
+            mc[p % SW_MR] = fwd ? d.Lcnt[c] : d.Ucnt[c];
+        }
+        __syncthreads();
+        for (int p = 0; p < SW_P - 1; p++) {
+            if (p < m) issue(p);
+            sw_commit();
+        }
+        V zprev = V(0);
+        int kprev = -1;
+        for (int p = 0; p < m; p++) {
+            sw_wait<SW_P - 2>();
+            __syncthreads();
+            // the previous step's z (backward) is stored once every thread read it
+            if (kprev >= 0 && tid == 0) zs[kprev] = zprev;
+            const int kl = fwd ? p : m - 1 - p;
+            const int st = p % SW_P, slot = p % SW_MR;
+            const int cnt = mc[slot];
+            const int64_t beg = mb[slot];
+            V v = zs[kl];
+            if (!fwd) v = v / rd[st];
+            const int wn = own_win(p, cnt);
+            for (int e = tid; e < wn; e += SW_NT) {
+                const int r = ri[st * W + e];
+                if (fwd ? r < hi : r >= lo) zs[r - lo] = fma(-rv[st * W + e], v, zs[r - lo]);
+            }
+            // own entries past the stage's window, read directly
+            const int own = fwd ? min(cnt, m - 1 - kl) : min(cnt - 1, kl);
+            for (int e = W + tid; e < own; e += SW_NT) {
+                const int64_t g = fwd ? beg + e : beg + cnt - 2 - e;
+                const int r = fwd ? s.r.Ls[g] : d.Ui[g];
+                if (fwd ? r >= hi : r < lo) break;
+                zs[r - lo] = fma(-(fwd ? Lx[g] : Ux[g]), v, zs[r - lo]);
+            }
+            if (!fwd) {
+                zprev = v;
+                kprev = kl;
+            }
+            // extents 2 SW_P positions ahead; entries SW_P - 1 positions ahead (into
+            // the stage every thread finished reading in the previous step)
+            if (tid == 0 && p + 2 * SW_P < m) {
+                const int pn = p + 2 * SW_P, c = col_of(pn);
+                sw_cp8(mb + pn % SW_MR, fwd ? d.Lbeg + c : d.Ubeg + c);
+                sw_cp4(mc + pn % SW_MR, fwd ? d.Lcnt + c : d.Ucnt + c);
+            }
+            if (p + SW_P - 1 < m) issue(p + SW_P - 1);
+            sw_commit();
+        }
+        sw_wait<0>();
+        __syncthreads();
+        if (kprev >= 0 && tid == 0) zs[kprev] = zprev;
+        __syncthreads();
+        for (int r = tid; r < m; r += SW_NT) {
+            const V v = zs[r];
+            vq[lo + r] = v;
+            if (!fwd) x[(int64_t)q * ldx + (Qout ? Qout[lo + r] : lo + r)] = (double)v;
+        }
+        __syncthreads();
     }
+    __threadfence();
+    __syncthreads();
+    for (int r = lo + tid; r < hi; r += SW_NT) st_release(flags + r, epoch);
+    if (tid == 0) BK_TREC(d.trace, BK_TR_SOLVE, fwd ? 2 : 3, t, t0);
+    BK_TPHASE(d.trace, tp, fwd ? 10 : 11, t);     // the sweep itself
 }
-
-// One warp solves a separator's own triangle, its rows' outside terms already
-// applied (the rows' values are in zs, in shared memory or in place in global
-// memory).  Forward: for k ascending, w_k = zs[k] is final and L(i,k) w_k is
-// subtracted from the node's rows i > k; backward: for k descending, z_k =
-// zs[k] / U(k,k) is final and U(j,k) z_k is subtracted from the node's rows
-// j < k.  Per row the terms come in the order of the row sweeps (ascending k
-// forward, descending backward), after the outside terms.  The next column's
-// entries and the one after's extent are read while a column is applied.
-template <typename V>
-__device__ __forceinline__ void sweep(const bk_dev &d, const bk_solve_dev &s, int lo, int hi, V *zs, bool fwd,
-                                      int lane)
-{
-    const V *const Lx = vals<V>(d.Lx);
-    const V *const Ux = vals<V>(d.Ux);
-    const int nown = hi - lo;
-    SweepCol<V> cur, nxt;
-    int64_t nbeg = 0;
-    int ncnt = 0;
-    {
-        int64_t b0;
-        int c0;
-        sweep_meta<V>(d, fwd ? lo : hi - 1, fwd, b0, c0, lane);
-        sweep_read(d, s, cur, b0, c0, fwd, lo, hi, lane);
-        if (nown > 1) sweep_meta<V>(d, fwd ? lo + 1 : hi - 2, fwd, nbeg, ncnt, lane);
-    }
-    for (int step = 0; step < nown; step++) {
-        const int kl = fwd ? step : nown - 1 - step;      // node-local column
-        if (step + 1 < nown) sweep_read(d, s, nxt, nbeg, ncnt, fwd, lo, hi, lane);
-        if (step + 2 < nown) sweep_meta<V>(d, lo + (fwd ? step + 2 : nown - 3 - step), fwd, nbeg, ncnt, lane);
-        V vk = zs[kl];
-        if (!fwd) {
-            vk = vk / cur.diag;
-            __syncwarp();
-            if (lane == 0) zs[kl] = vk;
-        }
-#pragma unroll
-        for (int u = 0; u < SW_PF; u++)
-            if (cur.row[u] >= 0) zs[cur.row[u]] = fma(-cur.val[u], vk, zs[cur.row[u]]);
-        // entries past the read-ahead window, up to the first outside the node
-        for (int t = 32 * SW_PF + lane; t < cur.cnt; t += 32) {
-            const int64_t e = fwd ? cur.beg + t : cur.beg + cur.cnt - 1 - t;
-            const int i = fwd ? s.r.Ls[e] : d.Ui[e];
-            if (fwd ? i >= hi : i < lo) break;
-            zs[i - lo] = fma(-(fwd ? Lx[e] : Ux[e]), vk, zs[i - lo]);
-        }
-        __syncwarp();
-        cur = nxt;
-    }
-}
-
-constexpr int SEP_SMEM_ROWS = 1024;   // separator rows a warp sweeps in shared memory
 
 template <typename V>
 __global__ void __launch_bounds__(128) bk_solve_kernel(bk_dev d, bk_solve_dev s, int32_t nrhs,
@@ -503,15 +606,23 @@ __global__ void __launch_bounds__(128) bk_solve_kernel(bk_dev d, bk_solve_dev s,
 {
     extern __shared__ __align__(16) double solve_smem[];
     const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
     const int64_t n = d.n;
+    // the first blocks sweep the separators' own triangles, in claim order
+    const int nsb = min(s.nsweeps, SW_MAXB);
+    if ((int)blockIdx.x < nsb) {
+        for (int k = blockIdx.x; k < s.nsweeps; k += nsb) {
+            sep_sweep_block<V>(d, s, s.sweeps[k], nrhs, x, ldx, epoch, budget, Qout,
+                               reinterpret_cast<unsigned char *>(solve_smem));
+            if (__syncthreads_or(*reinterpret_cast<const volatile int *>(&d.status->timeout) != 0)) return;
+        }
+        return;
+    }
     const V *const Bx = vals<V>(d.Bx);
     const V *const Lrx = vals<V>(s.r.Lrx);
     const V *const Urx = vals<V>(s.r.Urx);
     const V *const Ud = vals<V>(s.r.Ud);
     V *const w = vals<V>(s.w);
     V *const zz = vals<V>(s.z);
-    V *const zsm = reinterpret_cast<V *>(solve_smem) + (int64_t)wib * SEP_SMEM_ROWS;
     for (;;) {
         int k = 0;
         if (lane == 0) k = atomicAdd(d.counter + 2, 1);
@@ -521,35 +632,7 @@ __global__ void __launch_bounds__(128) bk_solve_kernel(bk_dev d, bk_solve_dev s,
         BK_TSTART(t0);
         const bool fwd = it >= 0;
         const int i = fwd ? it : ~it;
-        if (i >= n) {
-            // a separator's own triangle (forward or backward sweep)
-            const bk_task &T = d.tasks[i - n];
-            const int lo = T.lo, hi = T.hi, nown = hi - lo;
-            int32_t *flags = fwd ? s.fdone : s.bdone;
-            for (int r0 = lo; r0 < hi; r0 += 32)
-                if (!wait_flags(d, flags, r0 + lane, r0 + lane < hi, -epoch, budget)) return;
-            BK_TPHASE0(tp);
-            for (int q = 0; q < nrhs; q++) {
-                V *vq = (fwd ? w : zz) + q * n;
-                V *zs = nown <= SEP_SMEM_ROWS ? zsm : vq + lo;
-                if (zs == zsm)
-                    for (int r = lane; r < nown; r += 32) zs[r] = __ldcg(vq + lo + r);
-                __syncwarp();
-                sweep(d, s, lo, hi, zs, fwd, lane);
-                for (int r = lane; r < nown; r += 32) {
-                    const V v = zs[r];
-                    vq[lo + r] = v;
-                    if (!fwd) x[(int64_t)q * ldx + (Qout ? Qout[lo + r] : lo + r)] = (double)v;
-                }
-                __syncwarp();
-            }
-            __threadfence();
-            __syncwarp();
-            for (int r = lo + lane; r < hi; r += 32) st_release(flags + r, epoch);
-            if (lane == 0) BK_TREC(d.trace, BK_TR_SOLVE, fwd ? 2 : 3, i - n, t0);
-            BK_TPHASE(d.trace, tp, fwd ? 10 : 11, i - n);     // the sweep itself
-            continue;
-        }
+        if (i >= n) continue;     // a separator's sweep (the sweeper blocks take it)
         // a separator's row takes only the terms from outside its node
         const int clo = s.cutlo[i], chi = s.cuthi[i];
         const bool part = clo >= 0;
@@ -565,9 +648,7 @@ __global__ void __launch_bounds__(128) bk_solve_kernel(bk_dev d, bk_solve_dev s,
                     const bool have = lane < cnt;
                     const int j = have ? s.offj[e + lane] : 0;
                     const V a = have ? Bx[s.offpos[e + lane]] : V(0);
-                    if (!wait_flags(d, s.bdone, j, have, epoch, budget)) return;
-                    const V v = have ? __ldcg(zz + q * n + j) : V(0);
-                    z = chain(z, a, v, cnt);
+                    if (!chain_wait(d, s.bdone, zz + q * n, j, have, a, cnt, epoch, budget, z)) return;
                 }
                 for (int64_t e = l0; e < l1; e += 32) {
                     int cnt = (int)min((int64_t)32, l1 - e);
@@ -576,9 +657,7 @@ __global__ void __launch_bounds__(128) bk_solve_kernel(bk_dev d, bk_solve_dev s,
                     const bool have = lane < cnt;
                     const int j = have ? j0 : 0;
                     const V a = have ? Lrx[e + lane] : V(0);
-                    if (!wait_flags(d, s.fdone, j, have, epoch, budget)) return;
-                    const V v = have ? __ldcg(w + q * n + j) : V(0);
-                    z = chain(z, a, v, cnt);
+                    if (!chain_wait(d, s.fdone, w + q * n, j, have, a, cnt, epoch, budget, z)) return;
                     if (cnt < 32) break;
                 }
                 if (lane == 0) w[q * n + i] = z;
@@ -601,9 +680,7 @@ __global__ void __launch_bounds__(128) bk_solve_kernel(bk_dev d, bk_solve_dev s,
                     const bool have = lane < cnt;
                     const int j = have ? j0 : 0;
                     const V a = have ? Urx[e + lane] : V(0);
-                    if (!wait_flags(d, s.bdone, j, have, epoch, budget)) return;
-                    const V v = have ? __ldcg(zz + q * n + j) : V(0);
-                    z = chain(z, a, v, cnt);
+                    if (!chain_wait(d, s.bdone, zz + q * n, j, have, a, cnt, epoch, budget, z)) return;
                     if (cnt < 32) break;
                 }
                 if (!part) z = z / ud;
@@ -634,6 +711,29 @@ int bk_solve_blocks()
         return std::max(1, sms) * std::max(1, std::min(per, 8));
     }();
     return blocks;
+}
+
+void bk_solve_sweep_setup(bk_solve_dev &s, int32_t sw_maxm)
+{
+    const int own = std::max(1, sw_maxm - 1);
+    s.sw_win = std::min(SW_WMAX, (own + 3) & ~3);
+    s.sw_zrows = std::min(std::max(sw_maxm, 1), SEP_SMEM_ROWS);
+    // the FP64 layout, the larger one, serves both kernels
+    s.sw_smem = sw_layout(s.sw_win, s.sw_zrows, sizeof(double)).total;
+    int dev = 0, sms = 0, per[2] = {0, 0};
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // the function attribute is shared by every handle: the largest layout, once
+    static const bool raised = [] {
+        const int most = (int)sw_layout(SW_WMAX, SEP_SMEM_ROWS, sizeof(double)).total;
+        cudaFuncSetAttribute(bk_solve_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+        cudaFuncSetAttribute(bk_solve_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+        return true;
+    }();
+    (void)raised;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[0], bk_solve_kernel<double>, SW_NT, s.sw_smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[1], bk_solve_kernel<float>, SW_NT, s.sw_smem);
+    for (int k = 0; k < 2; k++) s.sw_cap[k] = std::max(1, sms) * std::max(1, std::min(per[k], 8));
 }
 
 namespace {
@@ -701,12 +801,16 @@ void bk_launch_solve(const bk_dev &d, const bk_solve_dev &s, int32_t nrhs, const
 {
     const int32_t *Pin = permute ? d.P : nullptr, *Qout = permute ? d.Q : nullptr;
     if (s.nitems <= 0) return;
-    const int ctas = std::min<int>((s.nitems + 3) / 4, max_ctas > 0 ? max_ctas : bk_solve_blocks());
-    const size_t smem = (size_t)4 * SEP_SMEM_ROWS * sizeof(double);
+    // sweeper blocks first, then the row warps' blocks; every block co-resident
+    const int nsb = std::min(s.nsweeps, SW_MAXB);
+    const int cap = s.sw_cap[d.prec ? 1 : 0];
+    const int limit = max_ctas > 0 ? std::min(max_ctas, cap) : cap;
+    const int ctas = nsb + std::max(1, std::min<int>((s.nitems + 3) / 4, limit - nsb));
+    const size_t smem = s.sw_smem;
     if (d.prec)
-        bk_solve_kernel<float><<<ctas, 128, smem, (cudaStream_t)stream>>>(d, s, nrhs, b, ldb, x, ldx, epoch, budget, Pin,
+        bk_solve_kernel<float><<<ctas, SW_NT, smem, (cudaStream_t)stream>>>(d, s, nrhs, b, ldb, x, ldx, epoch, budget, Pin,
                                                                         Qout);
     else
-        bk_solve_kernel<double><<<ctas, 128, smem, (cudaStream_t)stream>>>(d, s, nrhs, b, ldb, x, ldx, epoch, budget, Pin,
+        bk_solve_kernel<double><<<ctas, SW_NT, smem, (cudaStream_t)stream>>>(d, s, nrhs, b, ldb, x, ldx, epoch, budget, Pin,
                                                                          Qout);
 }

@@ -49,11 +49,21 @@ struct bk_solve_dev {
     double *w;                    // n x nrhs, forward results by step
     double *z;                    // n x nrhs, the solution by step
     bk_rows r;
+    // the separators' own triangles: the sweep items of items (n + t forward,
+    // ~(n + t) backward) in claim order; sweeper block b of nsb takes the sweeps
+    // b, b + nsb, ... (a whole block a sweep; the row warps skip them)
+    int32_t nsweeps;
+    const int32_t *sweeps;
+    int32_t sw_win;               // entries of a column copied ahead per pipeline stage
+    int32_t sw_zrows;             // a node of up to this many rows is swept in shared memory
+    size_t sw_smem;               // the kernel's dynamic shared memory (a sweeper's needs)
+    int32_t sw_cap[2];            // co-resident blocks with it (FP64, FP32 kernel)
 };
 
 struct bk_solve_plan {
-    std::vector<int32_t> items, offp, offj, offpos, cutlo, cuthi, leaf_tasks;
+    std::vector<int32_t> items, offp, offj, offpos, cutlo, cuthi, leaf_tasks, sweeps;
     int32_t leaf_rows = 0, leaf_f0 = -1, leaf_b0 = -1, leaf_maxrows = 0;
+    int32_t sw_maxm = 0;          // rows of the largest separator
 };
 
 void bk_solve_plan_build(const bk_plan &pl, bk_solve_plan &sp);
@@ -65,3 +75,6 @@ void bk_launch_solve(const bk_dev &d, const bk_solve_dev &s, int32_t nrhs, const
                      double *x, int32_t ldx, int32_t epoch, long long budget, void *stream, bool permute = true,
                      int max_ctas = 0);
 int bk_solve_blocks();   // persistent blocks of the solve kernel at full occupancy (4 warps each)
+// The sweep geometry of a plan (sw_win, sw_zrows) and the kernel's dynamic
+// shared memory for it.
+void bk_solve_sweep_setup(bk_solve_dev &s, int32_t sw_maxm);

@@ -40,8 +40,10 @@ void bk_solve_plan_build(const bk_plan &pl, bk_solve_plan &sp)
     // A leaf's rows are complete row items.  A separator (a node above others)
     // is dense: its row items take only the terms from outside the node
     // (coupling and descendants forward, ancestors backward), and one sweep item
-    // per separator, after its rows, solves the node's own triangle in one warp.
+    // per separator, after its rows, solves the node's own triangle in one block.
     sp.items.clear();
+    sp.sweeps.clear();
+    sp.sw_maxm = 0;
     sp.items.reserve((size_t)2 * (size_t)n + 2 * pl.tasks.size());
     sp.cutlo.assign((size_t)n, -1);
     sp.cuthi.assign((size_t)n, -1);
@@ -64,7 +66,11 @@ void bk_solve_plan_build(const bk_plan &pl, bk_solve_plan &sp)
                 sp.items.push_back(fwd ? T.lo + q : ~(T.hi - 1 - q));
             }
         for (int32_t t : tasks)
-            if (is_sep(pl.tasks[(size_t)t])) sp.items.push_back(fwd ? n + t : ~(n + t));
+            if (is_sep(pl.tasks[(size_t)t])) {
+                sp.items.push_back(fwd ? n + t : ~(n + t));
+                sp.sweeps.push_back(fwd ? n + t : ~(n + t));
+                sp.sw_maxm = std::max(sp.sw_maxm, pl.tasks[(size_t)t].hi - pl.tasks[(size_t)t].lo);
+            }
     };
     // Height-0 tasks (ND leaves, and BTF blocks when no coupling entry ties
     // the blocks together) get their order after each factorization (leaf_*).
