@@ -235,6 +235,16 @@ int basker_refactor_solve_host(basker_t h, const double *values_host, int32_t nr
  * (the handle then keeps the default sizes). */
 int basker_autotune(basker_t h, const double *values_dev, const double *b_dev, void *stream);
 
+/* The latencies that bound one link of a dependency chain of the factorization
+ * or the solve (Sec. IV: a thread waits point to point for what it reads), on
+ * the current device, for performance models: ns_out[0] = one flag handoff
+ * between two blocks through global memory (a release store seen by an acquire
+ * load), ns_out[1] = one dependent FP64 fma, ns_out[2] = one dependent FP64
+ * division.  ns_out: 3 host doubles.  No handle; synchronous; allocates and
+ * frees a few bytes of device memory.  Errors: INVALID_ARG (null), OOM, CUDA,
+ * TIMEOUT (a handoff wait ran past 2e9 cycles; nothing is written). */
+int basker_probe_latency(double *ns_out);
+
 /* Size, in doubles, of the fixed device array basker_solve_noalloc works in
  * (8 MiB on every GPU that loads the library, held until the process exits). */
 #define BASKER_NOALLOC_SCRATCH_DOUBLES (1 << 20)

@@ -68,7 +68,7 @@ KERNEL_KINDS = ["gather", "static_refactor", "dag_levels", "gp_in_node", "gp_des
 EXPORTED = ["basker_default_options", "basker_symbolic", "basker_factor", "basker_refactor",
             "basker_solve", "basker_refactor_solve_host", "basker_info", "basker_export",
             "basker_free", "basker_strerror", "basker_solve_noalloc", "basker_autotune",
-            "basker_symbolic_counts"]
+            "basker_symbolic_counts", "basker_probe_latency"]
 
 
 def library_path() -> str:
@@ -112,6 +112,8 @@ def load(path: Optional[str] = None):
         L.basker_strerror.restype = ctypes.c_char_p
         L.basker_symbolic_counts.argtypes = [i32, vp, vp, vp, vp, i32, vp, i32, i32, vp, ctypes.c_int, vp, vp]
         L.basker_symbolic_counts.restype = ctypes.c_int
+        L.basker_probe_latency.argtypes = [vp]
+        L.basker_probe_latency.restype = ctypes.c_int
         _lib = L
         return L
 
@@ -132,6 +134,17 @@ def symbolic_counts(prob, mode: int = 0):
     if s != 0:
         raise BaskerError(s, "basker_symbolic_counts")
     return lc[:n], uc[:n]
+
+
+def probe_latency() -> dict:
+    """basker_probe_latency on the current device: ns of one flag handoff between
+    two blocks, one dependent FP64 fma, one dependent FP64 division."""
+    L = load()
+    out = (ctypes.c_double * 3)()
+    s = L.basker_probe_latency(ctypes.cast(out, ctypes.c_void_p))
+    if s != 0:
+        raise BaskerError(s, "basker_probe_latency")
+    return {"flag_handoff_ns": out[0], "dfma_ns": out[1], "ddiv_ns": out[2]}
 
 
 def default_options() -> Options:

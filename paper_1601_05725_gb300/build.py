@@ -19,7 +19,7 @@ LIB = os.path.join(BUILD, "libbasker_gb300.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 SOURCES = ["api.cu", "kernels_gp.cu", "kernels_static.cu", "kernels_solve.cu", "symbolic.cpp",
            "solve_plan.cpp", "noalloc.cu", "kernels_dd.cu", "refine.cu", "kernels_dense.cu",
-           "kernels_repair.cu", "kernels_desc.cu"]
+           "kernels_repair.cu", "kernels_desc.cu", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # -fmad=false: no multiply-add is contracted unless written as fma(); the
 # factors' bit-for-bit agreement with the oracle then does not depend on how

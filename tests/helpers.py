@@ -112,6 +112,46 @@ def solve_backward_error(A: sp.csc_matrix, x: np.ndarray, b: np.ndarray) -> floa
     return float(eta.max())
 
 
+def forward_error(x: np.ndarray, xo: np.ndarray) -> float:
+    """max over right-hand sides of ||x - xo||_inf / ||xo||_inf."""
+    x2 = np.asarray(x).reshape(len(x), -1)
+    o2 = np.asarray(xo).reshape(len(xo), -1)
+    return float((np.abs(x2 - o2).max(axis=0) / np.abs(o2).max(axis=0)).max())
+
+
+def oracle_solution(prob, values, b) -> np.ndarray:
+    """The FP64 oracle's solution of A(values) x = b (a factorization from scratch)."""
+    import oracle
+    o = oracle.OracleLU(prob)
+    assert o.factor(values) == "OK"
+    return o.solve(b)
+
+
+def kappa_inf_blocks(prob) -> float:
+    """kappa_inf(A) of a block-diagonal B = A(P, Q): ||A||_inf times the largest
+    ||B_d^-1||_inf over the diagonal blocks (dense inverses; small blocks)."""
+    B = sp.csc_matrix((prob.values, (np.argsort(prob.P)[prob.rowind],
+                                     np.argsort(prob.Q)[np.repeat(np.arange(prob.n), np.diff(prob.colptr))])),
+                      shape=(prob.n, prob.n)).tocsr()
+    bp = np.asarray(prob.block_ptr)
+    inv = 0.0
+    for d in range(len(bp) - 1):
+        lo, hi = bp[d], bp[d + 1]
+        Bd = B[lo:hi, lo:hi].toarray()
+        inv = max(inv, float(np.abs(np.linalg.inv(Bd)).sum(axis=1).max()))
+    return float(np.abs(B).sum(axis=1).max() * inv)
+
+
+def kappa_inf(A: sp.csc_matrix) -> float:
+    """kappa_inf(A) = ||A||_inf ||A^-1||_inf, the inverse's norm by the 1-norm
+    estimate of A^-T (Hager-Higham, scipy's onenormest; small matrices)."""
+    import scipy.sparse.linalg as spla
+    lu = spla.splu(A.T.tocsc())
+    inv_t = spla.LinearOperator(A.shape, matvec=lu.solve, rmatvec=lambda y: lu.solve(y, trans="T"),
+                                dtype=np.float64)
+    return float(np.abs(A).sum(axis=1).max() * spla.onenormest(inv_t))
+
+
 def a_matrix(prob) -> sp.csc_matrix:
     return sp.csc_matrix((prob.values, prob.rowind, prob.colptr), shape=(prob.n, prob.n))
 

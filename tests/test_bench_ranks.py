@@ -71,3 +71,31 @@ def test_reference_arm_prints_once_under_torchrun():
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["steps"] == 1
     assert d["cpu_baseline"]["kind"] == "oracle" and d["value"] > 0
     assert d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_block_parallel_oracle_partition_matches_the_whole():
+    """The CPU baseline's block-parallel mode: the blocks of B split into groups,
+    each group a problem of its own; the oracle on every group gives, bit for bit,
+    the oracle's solution of the whole system restricted to the group's rows."""
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import bench
+    import oracle
+    from paper_1601_05725_gb300 import inputs as I
+    prob = I.block_diagonal_problem(5, nblocks=40, size_range=(3, 60))
+    vals = [I.refactor_values(prob, k) for k in (1, 2)]
+    rhs = [I.rhs_ones(prob, v) for v in vals]
+    groups = bench._block_groups(prob, 3)
+    assert sorted(b for g in groups for b in g) == list(range(prob.nblocks))
+    whole = oracle.OracleLU(prob)
+    assert whole.factor(vals[1]) == "OK"
+    xw = whole.solve(rhs[1])                       # by A's columns
+    bp = np.asarray(prob.block_ptr)
+    for g, (sub, sv, sb) in zip(groups, bench._sub_problems(prob, groups, vals, rhs)):
+        o = oracle.OracleLU(sub)
+        assert o.factor(sv[1]) == "OK"
+        xs = o.solve(sb[1])
+        cols = np.concatenate([np.arange(bp[b], bp[b + 1]) for b in g])   # B columns, new order
+        np.testing.assert_array_equal(xs, xw[prob.Q[cols]])
+    t = bench._par_worker((sub, sv, sb, 0, 2))
+    assert len(t) == 2 and min(t) > 0

@@ -9,7 +9,7 @@ the top of its subtree carries rail rows in L and every rail column a long U
 FP64: pivots, L/U patterns and values against the oracle, bit for bit, for the
 factorization, one refactorization and a four-column solve.  FP32 factorization
 with FP64 refinement: backward error <= 1e-12 for each of four N(0, 1)
-right-hand sides.
+right-hand sides, and the error against the FP64 oracle's solution stated.
 """
 import numpy as np
 import pytest
@@ -85,3 +85,9 @@ def test_config4_fp32_refined_four_rhs(c4):
         for q in range(NRHS):
             assert H.solve_backward_error(A, X[:, q], B[:, q]) <= 1e-12
         assert inf["precision_used"] in (0, 1)
+        # the error against the FP64 oracle's solution, stated; its bound 2 kappa
+        # eta needs kappa(A), which is not computed at n = 2e6 (the smaller FP32
+        # cases check the bound), so only a coarse ceiling is asserted here
+        err = H.forward_error(X, H.oracle_solution(prob, values, B))
+        print(f"config 4 FP32+IR vs FP64 oracle rel err {err:.2e}")
+        assert err <= 1e-3

@@ -66,6 +66,13 @@ def test_config3_fp32_refined(c3):
     x = h.solve(_dev(b)).cpu().numpy()
     assert H.solve_backward_error(A, x, b) <= 1e-12
     assert h.info()["precision_used"] == 1
+    # against the FP64 oracle's solution (independent blocks of at most 1,024 rows)
+    # the error against the FP64 oracle's solution, within 2 kappa_inf(A) eta
+    eta = H.solve_backward_error(A, x, b)
+    err = H.forward_error(x, H.oracle_solution(prob, prob.values, b))
+    kappa = H.kappa_inf_blocks(prob)
+    print(f"config 3 FP32+IR vs FP64 oracle rel err {err:.2e} (eta {eta:.1e}, kappa {kappa:.1e})")
+    assert err <= 2.0 * kappa * max(eta, 1e-16)
 
 
 @pytest.mark.parametrize("switch", [0, 3])

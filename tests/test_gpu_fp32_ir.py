@@ -2,7 +2,8 @@
 
 The FP32 factors are checked by their own backward error; every solve by the
 FP64 backward error eta <= 1e-12 of the refined solution, computed here on the
-host from A, x and b.  The fallbacks to an FP64 factorization (pivot growth
+host from A, x and b, and by its error against the FP64 oracle's solution,
+bounded by 2 kappa(A) eta (with slack for the estimate of kappa).  The fallbacks to an FP64 factorization (pivot growth
 above the limit, a refinement that stalls) must give the FP64 handle's result.
 """
 import numpy as np
@@ -62,8 +63,14 @@ def test_fp32_factors_and_refined_solve(kind, seed, kw):
     x = _solve(h, b)
     inf = h.info()
     assert inf["precision_used"] == 1 and inf["ir_iterations"] >= 1
-    assert H.solve_backward_error(A, x, b) <= ETA
+    eta = H.solve_backward_error(A, x, b)
+    assert eta <= ETA
     assert inf["ir_eta"] <= 1e-13
+    # the error against the FP64 oracle's solution, within what eta allows
+    err = H.forward_error(x, H.oracle_solution(prob, prob.values, b))
+    kappa = H.kappa_inf(A)
+    print(f"{kind} {seed}: FP32+IR vs FP64 oracle rel err {err:.2e} (eta {eta:.1e}, kappa {kappa:.1e})")
+    assert err <= 20.0 * kappa * max(eta, 1e-16)
 
 
 def test_fp32_refactor_sequence_and_multiple_rhs():
@@ -77,7 +84,10 @@ def test_fp32_refactor_sequence_and_multiple_rhs():
         A = sp.csc_matrix((v, prob.rowind, prob.colptr), shape=(prob.n, prob.n))
         B = rng.standard_normal((prob.n, 3))
         X = h.solve(_dev(B)).cpu().numpy()
-        assert H.solve_backward_error(A, X, B) <= ETA
+        eta = H.solve_backward_error(A, X, B)
+        assert eta <= ETA
+        err = H.forward_error(X, H.oracle_solution(prob, v, B))
+        assert err <= 20.0 * H.kappa_inf(A) * max(eta, 1e-16), err
     # the host entry point refines the same way
     v = I.refactor_values(prob, 9, sigma=0.05)
     b = rng.standard_normal(prob.n)
