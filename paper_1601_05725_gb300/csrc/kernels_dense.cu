@@ -43,16 +43,49 @@ namespace {
 
 constexpr int DN_THREADS = 1024;
 constexpr int DN_WARPS = DN_THREADS / 32;
+constexpr int DN_CG = 4;             // warps of the owner block that build a step's column
+
+// |v| as an unsigned integer whose order is that of |v| over the finite values
+// and the infinities (NaNs above them): the bits with the sign cleared
+__device__ __forceinline__ unsigned long long mag_bits(double v)
+{
+    return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
+}
+__device__ __forceinline__ unsigned long long mag_bits(float v)
+{
+    return (unsigned long long)((unsigned)__float_as_int(v) & 0x7fffffffu);
+}
+template <typename V> __device__ __forceinline__ unsigned long long mag_inf();
+template <> __device__ __forceinline__ unsigned long long mag_inf<double>() { return 0x7ff0000000000000ull; }
+template <> __device__ __forceinline__ unsigned long long mag_inf<float>() { return 0x7f800000ull; }
+template <typename V> __device__ __forceinline__ V mag_value(unsigned long long k);
+template <> __device__ __forceinline__ double mag_value<double>(unsigned long long k)
+{
+    return __longlong_as_double((long long)k);
+}
+template <> __device__ __forceinline__ float mag_value<float>(unsigned long long k)
+{
+    return __int_as_float((int)(unsigned)k);
+}
+
+// the column group's barrier (named barrier 1, DN_CG warps)
+__device__ __forceinline__ void cg_bar() { asm volatile("bar.sync 1, %0;" ::"n"(DN_CG * 32) : "memory"); }
 
 struct DnShared {
     bk_task T;
     // nonzero: leave (failure, overflow, or an earlier failure elsewhere).  Read
-    // right after the cluster barrier of step k from stop[k & 1], which is written
-    // only before that barrier: by step k's first phase or step k - 1's second
-    // phase.  Every block thus leaves after the same step.
+    // right after the first cluster barrier of step k from stop[k & 1], which is
+    // written only before that barrier: by step k's first phase or step k - 1's
+    // second phase.  Every block thus leaves after the same step.
     int stop[2];
     int pslot[2];        // pivot slot of the step (by step parity), in the step owner's copy
     int cnt[2];          // L count of the step (by step parity), in the step owner's copy
+    double xp[2];        // the pivot's value (the step owner's copy)
+    long long lb[2];     // start of L(:,c) (the step owner's copy)
+    int cstop;           // the column group's stop decision
+    int bnd[BK_DENSE_CLUSTER + 1];   // first L position of each block's share of the division
+    unsigned long long redk[DN_CG];  // the column group's reductions
+    int redc[DN_CG], redb[DN_CG], redi[DN_CG];
 };
 
 // Every block of the cluster sees stop[parity]: written into each block's copy.
@@ -61,9 +94,25 @@ __device__ __forceinline__ void cluster_stop(cg::cluster_group &cl, DnShared &S,
     for (unsigned r = 0; r < cl.num_blocks(); r++) *cl.map_shared_rank(&S.stop[parity], r) = 1;
 }
 
+// Shared memory of a block, in bytes: the base layout, and the block's own
+// columns of the dense block with their pattern words (columns k with
+// k mod cluster == rank), kept on chip when they fit.
+__host__ __device__ inline size_t dn_base_bytes(int own, int lsp)
+{
+    const size_t nrw = ((size_t)lsp + 31) / 32;
+    return (size_t)own * 16 + 3 * (size_t)lsp * 8 + (size_t)own * 8 + (size_t)own * 8 + 2 * (size_t)lsp * 4 +
+           (4 * nrw + 1) * 4 + 2 * (size_t)own + 16;
+}
+
+__host__ __device__ inline size_t dn_local_bytes(int own, int lsp, int cluster)
+{
+    const size_t nloc = ((size_t)own + cluster - 1) / cluster, nrw = ((size_t)lsp + 31) / 32;
+    return nloc * (size_t)lsp * 8 + nloc * nrw * 4;
+}
+
 template <typename V>
 __global__ void __launch_bounds__(DN_THREADS) bk_dense_node_kernel(bk_dev d, const int32_t *__restrict__ task_ids,
-                                                                   double tau, int pref_mode)
+                                                                   double tau, int pref_mode, size_t smem_bytes)
 {
     V *const Lx = vals<V>(d.Lx);
     V *const Ux = vals<V>(d.Ux);
@@ -81,10 +130,14 @@ __global__ void __launch_bounds__(DN_THREADS) bk_dense_node_kernel(bk_dev d, con
     __syncthreads();
     const bk_task &T = S.T;
     const int nown = T.hi - T.lo, lsp = T.lspace, nrw = (lsp + 31) >> 5;
+    // the block's columns on chip when they fit in the shared memory given
+    const bool onchip = dn_base_bytes(nown, lsp) + dn_local_bytes(nown, lsp, CN) <= smem_bytes;
+    const int nloc = onchip ? (nown + CN - 1) / CN : 0;
     // shared layout (8-byte slots first): ub[nown] ue[nown] (int64) | lval[2][lsp] colv[lsp]
-    // mval[nown] (V in 8-byte slots) | nu[nown] spiv[nown] lsl[2][lsp] wpre[nrw] lbits[2][nrw]
-    // colb[nrw] (32-bit) | cbad[nown] chit[nown] (bytes).  Per-column state is kept by
-    // the block that owns the column (column k: block k mod CN); spiv by every block.
+    // mval[nown] loc[nloc][lsp] (V in 8-byte slots) | nus[nown] spiv[nown] lsl[2][lsp] wpre[nrw + 1]
+    // lbits[2][nrw] colb[nrw] locb[nloc][nrw] (32-bit) | cbad[nown] chit[nown] (bytes).
+    // Per-column state is kept by the block that owns the column (column k: block
+    // k mod CN, local index k / CN); spiv by every block.
     int64_t *ubs = reinterpret_cast<int64_t *>(dsm);
     int64_t *ues = ubs + nown;
     double *slots = reinterpret_cast<double *>(ues + nown);
@@ -92,19 +145,26 @@ __global__ void __launch_bounds__(DN_THREADS) bk_dense_node_kernel(bk_dev d, con
     V *lval1 = reinterpret_cast<V *>(slots + lsp);
     V *colv = reinterpret_cast<V *>(slots + 2 * lsp);
     V *mval = reinterpret_cast<V *>(slots + 3 * lsp);
-    int32_t *nus = reinterpret_cast<int32_t *>(slots + 3 * lsp + nown);
+    double *locslots = slots + 3 * lsp + nown;
+    int32_t *nus = reinterpret_cast<int32_t *>(locslots + (int64_t)nloc * lsp);
     int32_t *spiv = nus + nown;
     int32_t *lsl0 = spiv + nown;
     int32_t *lsl1 = lsl0 + lsp;
     int32_t *wpre = lsl1 + lsp;
-    uint32_t *lbits0 = reinterpret_cast<uint32_t *>(wpre + nrw);
+    uint32_t *lbits0 = reinterpret_cast<uint32_t *>(wpre + nrw + 1);
     uint32_t *lbits1 = lbits0 + nrw;
     uint32_t *colb = lbits1 + nrw;
-    unsigned char *cbad = reinterpret_cast<unsigned char *>(colb + nrw);
+    uint32_t *locb = colb + nrw;
+    unsigned char *cbad = reinterpret_cast<unsigned char *>(locb + (int64_t)nloc * nrw);
     unsigned char *chit = cbad + nown;
 
     V *const A = Ahat + T.ahoff;                       // column k at A + k * lsp
     uint32_t *const AB = d.abits + T.aboff;            // column k at AB + k * nrw
+    // column k of this block (values, pattern words): on chip or in the scratch
+    auto colA = [&](int k) -> V * {
+        return onchip ? reinterpret_cast<V *>(locslots + (int64_t)(k / CN) * lsp) : A + (int64_t)k * lsp;
+    };
+    auto colB = [&](int k) -> uint32_t * { return onchip ? locb + (int64_t)(k / CN) * nrw : AB + (int64_t)k * nrw; };
     for (int k = tid_x; k < nown; k += DN_THREADS) {
         const int c = T.lo + k;
         if (k % CN == rank) {
@@ -116,14 +176,34 @@ __global__ void __launch_bounds__(DN_THREADS) bk_dense_node_kernel(bk_dev d, con
         cbad[k] = 0;
         chit[k] = 0;
     }
-    // entries outside the patterns hold stale values: zero them (own columns)
+    // the block's columns (entries outside the patterns hold stale values: zero)
     for (int64_t e = tid_x; e < (int64_t)nown * lsp; e += DN_THREADS) {
-        const int k = (int)(e / lsp), s = (int)(e % lsp);
+        const int k = (int)(e / lsp), sl = (int)(e % lsp);
         if (k % CN != rank) continue;
-        if (!((AB[(int64_t)k * nrw + (s >> 5)] >> (s & 31)) & 1u)) A[e] = V(0);
+        const bool in = (AB[(int64_t)k * nrw + (sl >> 5)] >> (sl & 31)) & 1u;
+        if (onchip) colA(k)[sl] = in ? A[e] : V(0);
+        else if (!in) A[e] = V(0);
     }
+    if (onchip)
+        for (int64_t e = tid_x; e < (int64_t)nown * nrw; e += DN_THREADS) {
+            const int k = (int)(e / nrw);
+            if (k % CN == rank) colB(k)[e % nrw] = AB[e];
+        }
     cl.sync();
 
+#ifdef BK_TRACE
+    // trace builds: per-phase cycles of thread 0 (owner steps, other steps)
+    long long cyc[2][5] = {{0, 0, 0, 0, 0}, {0, 0, 0, 0, 0}};
+    long long lap_t = clock64();
+#define DN_LAP(i)                                                        \
+    do {                                                                 \
+        const long long t_ = clock64();                                  \
+        cyc[rank == owner ? 0 : 1][i] += t_ - lap_t;                     \
+        lap_t = t_;                                                      \
+    } while (0)
+#else
+#define DN_LAP(i)
+#endif
     for (int k = 0; k < nown; ++k) {
         const int c = T.lo + k;
         const int b = k & 1;
@@ -135,16 +215,16 @@ __global__ void __launch_bounds__(DN_THREADS) bk_dense_node_kernel(bk_dev d, con
         const int32_t *const lsl_p = b ? lsl0 : lsl1;
         const uint32_t *const lbits_p = b ? lbits0 : lbits1;
         const int cnt_p = k > 0 ? S.cnt[b ^ 1] : 0;
-        if (rank != owner || wid > 0) {
+        if (rank != owner || wid >= DN_CG) {
             // ---- step k - 1 on this block's columns after k (one warp a column)
-            const int nw = rank == owner ? DN_WARPS - 1 : DN_WARPS;
-            const int w0 = rank == owner ? wid - 1 : wid;
+            const int nw = rank == owner ? DN_WARPS - DN_CG : DN_WARPS;
+            const int w0 = rank == owner ? wid - DN_CG : wid;
             int first = k + 1 + ((rank - (k + 1) % CN) + CN) % CN;   // first own column after k
             for (int k2 = first + w0 * CN; k2 < nown && k > 0; k2 += nw * CN) {
                 if (!chit[k2]) continue;
-                uint32_t *const b2 = AB + (int64_t)k2 * nrw;
+                uint32_t *const b2 = colB(k2);
                 for (int w = lane; w < nrw; w += 32) b2[w] |= lbits_p[w];
-                V *const a2 = A + (int64_t)k2 * lsp;
+                V *const a2 = colA(k2);
                 const V m = mval[k2];
                 int q = lane;
                 for (; q + 7 * 32 < cnt_p; q += 8 * 32) {
@@ -163,115 +243,139 @@ __global__ void __launch_bounds__(DN_THREADS) bk_dense_node_kernel(bk_dev d, con
                 }
             }
         } else {
-            // ---- the owner's warp 0: column k into shared memory, step k - 1
-            // applied to it, then its pivot and L(:,k)
+            // ---- the owner's column group (DN_CG warps): column k, step k - 1
+            // applied to it, its pivot; then warp 0 ranks its L entries and takes
+            // its L region (the division follows after the cluster barrier, spread
+            // over the cluster)
+            constexpr int CT = DN_CG * 32;
+            const int ct = tid_x;
             const int pref = pref_mode ? d.pref[c] : c;
-            int64_t lb = d.Lbeg[c], le = d.Lend[c];
-            bool stop = false;
-            if ((k & 15) == 0) stop = __shfl_sync(BK_FULL, (int)should_stop(d, tid, c), 0) != 0;
-            const V *const ac = A + (int64_t)k * lsp;
-            const uint32_t *const bc = AB + (int64_t)k * nrw;
-            for (int w = lane; w < nrw; w += 32) colb[w] = bc[w];
-#pragma unroll 8
-            for (int s = lane; s < lsp; s += 32) colv[s] = ac[s];
-            __syncwarp();
-            if (k > 0 && chit[k]) {
+            int64_t lb = d.Lbeg[c], le = d.Lend[c];      // read early: used after the pivot
+            const V *const ac = colA(k);
+            const uint32_t *const bc = colB(k);
+            const bool upd = k > 0 && chit[k];
+            for (int w = ct; w < nrw; w += CT) colb[w] = bc[w] | (upd ? lbits_p[w] : 0u);
+            for (int sl = ct; sl < lsp; sl += CT) colv[sl] = ac[sl];
+            if (ct == 0) S.cstop = (k & 15) == 0 ? (int)should_stop(d, tid, c) : 0;
+            cg_bar();
+            if (upd) {
                 const V m = mval[k];
-                for (int w = lane; w < nrw; w += 32) colb[w] |= lbits_p[w];
-                for (int q = lane; q < cnt_p; q += 32) {
+                for (int q = ct; q < cnt_p; q += CT) {
                     const int s0 = lsl_p[q];
                     colv[s0] = fma(-lval_p[q], m, colv[s0]);
                 }
-                __syncwarp();
             }
-            V amax = V(0);
+            cg_bar();
+            // magnitudes compared as integers: for finite values the order of |v|
+            // is that of the bits with the sign cleared (the non-finite ones are
+            // caught by bad first), so the maximum and the rows holding it need no
+            // floating-point instruction
+            unsigned long long kmax = 0;
             int ncand = 0;
             bool bad = cbad[k] != 0;
-            for (int s = lane; s < lsp; s += 32) {
-                if (!((colb[s >> 5] >> (s & 31)) & 1u)) continue;
-                const V v = colv[s];
-                if (!isfinite(v)) bad = true;
-                if (s < nown) {
+            for (int sl = ct; sl < lsp; sl += CT) {
+                if (!((colb[sl >> 5] >> (sl & 31)) & 1u)) continue;
+                const unsigned long long key = mag_bits(colv[sl]);
+                if (key >= mag_inf<V>()) bad = true;
+                if (sl < nown) {
                     ncand++;
-                    amax = fmax(amax, fabs(v));
+                    kmax = key > kmax ? key : kmax;
                 }
             }
-            amax = warp_max(amax);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long t = __shfl_xor_sync(BK_FULL, kmax, o);
+                kmax = t > kmax ? t : kmax;
+            }
             ncand = warp_sum(ncand);
             bad = __any_sync(BK_FULL, bad);
+            if (lane == 0) {
+                S.redk[wid] = kmax;
+                S.redc[wid] = ncand;
+                S.redb[wid] = bad ? 1 : 0;
+            }
+            cg_bar();
+            kmax = 0;
+            ncand = 0;
+            bad = false;
+#pragma unroll
+            for (int g = 0; g < DN_CG; g++) {
+                kmax = S.redk[g] > kmax ? S.redk[g] : kmax;
+                ncand += S.redc[g];
+                bad = bad || S.redb[g] != 0;
+            }
+            const V amax = mag_value<V>(kmax);
+            const bool stop = S.cstop != 0;
             int ps = -1;
-            if (!stop && !bad && ncand > 0 && amax > V(0)) {
-                const int pr = pref - T.lo;
-                if (pr >= 0 && pr < nown && spiv[pr] < 0 && ((colb[pr >> 5] >> (pr & 31)) & 1u) &&
-                    (double)fabs(colv[pr]) >= tau * (double)amax) {
-                    ps = pr;
-                } else {
-                    // the lowest candidate row holding the maximum
-                    int best = INT_MAX;
-                    for (int s = lane; s < nown; s += 32)
-                        if (((colb[s >> 5] >> (s & 31)) & 1u) && fabs(colv[s]) == amax) { best = s; break; }
-                    ps = warp_min(best);
-                    if (ps == INT_MAX) {             // cannot happen: amax is one of the values
-                        if (lane == 0) report_internal(d.status, c, 40);
-                        ps = -1;
-                    }
+            const bool ok = !stop && !bad && ncand > 0 && kmax > 0;
+            const int pr = pref - T.lo;
+            const bool take_pref = ok && pr >= 0 && pr < nown && spiv[pr] < 0 && ((colb[pr >> 5] >> (pr & 31)) & 1u) &&
+                                   (double)fabs(colv[pr]) >= tau * (double)amax;
+            if (ok && !take_pref) {
+                // the lowest candidate row holding the maximum
+                int best = INT_MAX;
+                for (int sl = ct; sl < nown; sl += CT)
+                    if (((colb[sl >> 5] >> (sl & 31)) & 1u) && mag_bits(colv[sl]) == kmax) { best = sl; break; }
+                best = warp_min(best);
+                if (lane == 0) S.redi[wid] = best;
+            }
+            cg_bar();
+            if (take_pref) {
+                ps = pr;
+            } else if (ok) {
+                int best = INT_MAX;
+#pragma unroll
+                for (int g = 0; g < DN_CG; g++) best = min(best, S.redi[g]);
+                ps = best;
+                if (ps == INT_MAX) {                 // cannot happen: amax is one of the values
+                    if (ct == 0) report_internal(d.status, c, 40);
+                    ps = -1;
                 }
-            } else if (!stop && lane == 0) {
+            } else if (!stop && ct == 0) {
                 report_fail(d.status, c, bad ? BK_CODE_NAN : BK_CODE_SINGULAR);
             }
-            if (ps >= 0) {
-                // ranks of the L entries (the pattern without the pivot, ascending
-                // slots) and the pattern words they add to the columns they update
-                int carry = 0;
-                for (int w0 = 0; w0 < nrw; w0 += 32) {
-                    const int w = w0 + lane;
-                    uint32_t bits = w < nrw ? colb[w] : 0u;
-                    if (w == (ps >> 5)) bits &= ~(1u << (ps & 31));
-                    const int cnt = __popc(bits);
-                    const int pre = warp_exscan(cnt, lane);
-                    if (w < nrw) {
-                        wpre[w] = carry + pre;
-                        lbits[w] = bits;
+            if (wid == 0) {
+                if (ps >= 0) {
+                    // ranks of the L entries (the pattern without the pivot, ascending
+                    // slots) and the pattern words they add to the columns they update
+                    int carry = 0;
+                    for (int w0 = 0; w0 < nrw; w0 += 32) {
+                        const int w = w0 + lane;
+                        uint32_t bits = w < nrw ? colb[w] : 0u;
+                        if (w == (ps >> 5)) bits &= ~(1u << (ps & 31));
+                        const int cnt = __popc(bits);
+                        const int pre = warp_exscan(cnt, lane);
+                        if (w < nrw) {
+                            wpre[w] = carry + pre;
+                            lbits[w] = bits;
+                        }
+                        carry += __shfl_sync(BK_FULL, pre + cnt, 31);
                     }
-                    carry += __shfl_sync(BK_FULL, pre + cnt, 31);
-                }
-                // L region (a larger pool region when the count outgrows it)
-                bool fail = false;
-                if (lb + carry > le) {
-                    const int64_t cap = min((long long)(2 * (int64_t)carry + 16),
-                                            (long long)((T.hi - c - 1) + (lsp - nown)));
-                    int64_t nb = 0;
-                    if (lane == 0) nb = pool_alloc(d.pool, d.lpool_end, cap);
-                    nb = __shfl_sync(BK_FULL, nb, 0);
-                    if (nb < 0) {
-                        fail = true;
-                        if (lane == 0) report_overflow(d, T, tid, c, 1);
-                    } else {
-                        lb = nb;
-                        if (lane == 0) {
-                            d.Lbeg[c] = lb;
-                            d.Lend[c] = nb + cap;
+                    if (lane == 0) wpre[nrw] = carry;
+                    // L region (a larger pool region when the count outgrows it)
+                    bool fail = false;
+                    if (lb + carry > le) {
+                        const int64_t cap = min((long long)(2 * (int64_t)carry + 16),
+                                                (long long)((T.hi - c - 1) + (lsp - nown)));
+                        int64_t nb = 0;
+                        if (lane == 0) nb = pool_alloc(d.pool, d.lpool_end, cap);
+                        nb = __shfl_sync(BK_FULL, nb, 0);
+                        if (nb < 0) {
+                            fail = true;
+                            if (lane == 0) report_overflow(d, T, tid, c, 1);
+                        } else {
+                            lb = nb;
+                            if (lane == 0) {
+                                d.Lbeg[c] = lb;
+                                d.Lend[c] = nb + cap;
+                            }
                         }
                     }
-                }
-                __syncwarp();
-                if (fail) {
-                    if (lane == 0) cluster_stop(cl, S, b);
-                } else {
-                    const V xp = colv[ps];
-                    // L(:,c) = x / pivot over the pattern
-                    for (int s = lane; s < lsp; s += 32) {
-                        const int w = s >> 5, bt = s & 31;
-                        const uint32_t bits = lbits[w];
-                        if (!((bits >> bt) & 1u)) continue;
-                        const int pos = wpre[w] + __popc(bits & ((1u << bt) - 1u));
-                        const V q = colv[s] / xp;
-                        d.Li[lb + pos] = row_of_lslot(T, s);
-                        Lx[lb + pos] = q;
-                        lsl[pos] = s;
-                        lval[pos] = q;
-                    }
-                    if (lane == 0) {
+                    __syncwarp();
+                    if (fail) {
+                        if (lane == 0) cluster_stop(cl, S, b);
+                    } else if (lane == 0) {
+                        const V xp = colv[ps];
                         const int piv = T.lo + ps;
                         const int64_t u = ubs[k] + nus[k];
                         d.Ui[u] = c;
@@ -283,42 +387,56 @@ __global__ void __launch_bounds__(DN_THREADS) bk_dense_node_kernel(bk_dev d, con
                         if (piv != c) atomicAdd(&d.status->offdiag, 1);
                         S.pslot[b] = ps;
                         S.cnt[b] = carry;
+                        S.xp[b] = (double)xp;
+                        S.lb[b] = lb;
                     }
+                } else if (lane == 0) {
+                    cluster_stop(cl, S, b);
                 }
-            } else if (lane == 0) {
-                cluster_stop(cl, S, b);
             }
         }
+        DN_LAP(0);
         cl.sync();
+        DN_LAP(1);
         if (S.stop[b]) break;
-        // ---- the step's pivot and L(:,k) from its owner's shared memory
         DnShared *const So = cl.map_shared_rank(&S, owner);
         const int ps = So->pslot[b], cnt = So->cnt[b];
-        if (rank != owner) {
-            const V *const rv = cl.map_shared_rank(lval, owner);
-            const int32_t *const rs = cl.map_shared_rank(lsl, owner);
-            const uint32_t *const rb = cl.map_shared_rank(lbits, owner);
-            for (int q = tid_x; q < cnt; q += DN_THREADS) {
-                lsl[q] = rs[q];
-                lval[q] = rv[q];
-            }
-            for (int w = tid_x; w < nrw; w += DN_THREADS) lbits[w] = rb[w];
-            if (tid_x == 0) {
-                S.pslot[b] = ps;
-                S.cnt[b] = cnt;
-            }
-        }
         if (tid_x == 0) spiv[ps] = k;
+        {
+            // ---- L(:,c) = x / pivot over the pattern, one entry a thread: this
+            // block's share, the pattern words [rank cw, (rank + 1) cw)
+            const uint32_t *const rb = cl.map_shared_rank(lbits, owner);
+            const int32_t *const rw = cl.map_shared_rank(wpre, owner);
+            const V *const rc = cl.map_shared_rank(colv, owner);
+            const V xp = (V)So->xp[b];
+            const int64_t lb = So->lb[b];
+            const int cw = (nrw + CN - 1) / CN;
+            const int wl = min(nrw, rank * cw), wh = min(nrw, wl + cw);
+            for (int sl = wl * 32 + tid_x; sl < min(lsp, wh * 32); sl += DN_THREADS) {
+                const int w = sl >> 5, bt = sl & 31;
+                const uint32_t bits = rb[w];
+                if (!((bits >> bt) & 1u)) continue;
+                const int pos = rw[w] + __popc(bits & ((1u << bt) - 1u));
+                const V q = rc[sl] / xp;
+                d.Li[lb + pos] = row_of_lslot(T, sl);
+                Lx[lb + pos] = q;
+                lsl[pos] = sl;
+                lval[pos] = q;
+            }
+            if (rank != owner)
+                for (int w = tid_x; w < nrw; w += DN_THREADS) lbits[w] = rb[w];
+            if (tid_x <= CN) S.bnd[tid_x] = rw[min(nrw, tid_x * cw)];
+        }
         // ---- this block's later columns whose pattern holds the pivot row (one
         // thread a column): U(c, c2) = that entry, which leaves the column
         const int first = k + 1 + ((rank - (k + 1) % CN) + CN) % CN;
         for (int k2 = first + tid_x * CN; k2 < nown; k2 += DN_THREADS * CN) {
-            uint32_t *const b2 = AB + (int64_t)k2 * nrw;
+            uint32_t *const b2 = colB(k2);
             const uint32_t w = b2[ps >> 5];
             const bool hit = (w >> (ps & 31)) & 1u;
             chit[k2] = hit;
             if (!hit) continue;
-            V *const a2 = A + (int64_t)k2 * lsp;
+            V *const a2 = colA(k2);
             const V m = a2[ps];
             mval[k2] = m;
             int64_t ub = ubs[k2], ue = ues[k2];
@@ -351,8 +469,31 @@ __global__ void __launch_bounds__(DN_THREADS) bk_dense_node_kernel(bk_dev d, con
             a2[ps] = V(0);
             b2[ps >> 5] = w & ~(1u << (ps & 31));
         }
+        // ---- the other blocks' shares of L(:,k), from their shared memory
+        DN_LAP(2);
+        cl.sync();
+        DN_LAP(3);
+        for (int q = tid_x; q < cnt; q += DN_THREADS) {
+            int src = CN - 1;
+            while (src > 0 && S.bnd[src] > q) src--;
+            if (src == rank) continue;
+            lsl[q] = *cl.map_shared_rank(lsl + q, src);
+            lval[q] = *cl.map_shared_rank(lval + q, src);
+        }
+        if (rank != owner && tid_x == 0) {
+            S.pslot[b] = ps;
+            S.cnt[b] = cnt;
+        }
         __syncthreads();
+        DN_LAP(4);
     }
+#undef DN_LAP
+#ifdef BK_TRACE
+    if (tid_x == 0)
+        for (int i = 0; i < 5; i++)
+            bk_trace_raw(d.trace, BK_TR_PHASE, 40 + i, tid * 16 + rank, (unsigned long long)cyc[0][i],
+                         (unsigned long long)cyc[1][i]);
+#endif
     // no block leaves while another may still read its shared memory
     cl.sync();
     if (rank == 0 && tid_x == 0) BK_TREC(d.trace, BK_TR_DENSE, 0, tid, t0);
@@ -362,13 +503,15 @@ __global__ void __launch_bounds__(DN_THREADS) bk_dense_node_kernel(bk_dev d, con
 
 size_t bk_dense_node_smem(const bk_task &T)
 {
-    const size_t own = (size_t)(T.hi - T.lo), lsp = (size_t)T.lspace, nrw = (lsp + 31) / 32;
-    return own * 16 + 3 * lsp * 8 + own * 8 + own * 8 + 2 * lsp * 4 + 4 * nrw * 4 + 2 * own + 16;
+    const int own = T.hi - T.lo;
+    const size_t base = dn_base_bytes(own, T.lspace);
+    const size_t full = base + dn_local_bytes(own, T.lspace, bk_dense_node_cluster(T));
+    return full <= BK_DENSE_SMEM ? full : base;
 }
 
 bool bk_dense_node_eligible(const bk_task &T)
 {
-    return T.sp_lo < T.lo && T.hi > T.lo && bk_dense_node_smem(T) <= BK_DENSE_SMEM;
+    return T.sp_lo < T.lo && T.hi > T.lo && dn_base_bytes(T.hi - T.lo, T.lspace) <= BK_DENSE_SMEM;
 }
 
 void bk_launch_dense_nodes(const bk_dev &d, const int32_t *task_ids, int32_t ntasks, size_t smem, double tau,
@@ -393,9 +536,9 @@ void bk_launch_dense_nodes(const bk_dev &d, const int32_t *task_ids, int32_t nta
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     if (d.prec)
-        cudaLaunchKernelEx(&cfg, bk_dense_node_kernel<float>, d, task_ids, tau, pref_mode);
+        cudaLaunchKernelEx(&cfg, bk_dense_node_kernel<float>, d, task_ids, tau, pref_mode, smem);
     else
-        cudaLaunchKernelEx(&cfg, bk_dense_node_kernel<double>, d, task_ids, tau, pref_mode);
+        cudaLaunchKernelEx(&cfg, bk_dense_node_kernel<double>, d, task_ids, tau, pref_mode, smem);
 }
 
 int bk_dense_node_cluster(const bk_task &T)
