@@ -662,7 +662,7 @@ __global__ void __launch_bounds__(128) bk_solve_kernel(bk_dev d, bk_solve_dev s,
                 }
                 if (lane == 0) w[q * n + i] = z;
             }
-            __threadfence();
+            // lane 0 alone wrote what the flag publishes: its release store orders it
             __syncwarp();
             if (lane == 0) st_release(s.fdone + i, part ? -epoch : epoch);
             if (lane == 0) BK_TREC(d.trace, BK_TR_SOLVE, 0, i, t0);
@@ -689,7 +689,6 @@ __global__ void __launch_bounds__(128) bk_solve_kernel(bk_dev d, bk_solve_dev s,
                     if (!part) x[(int64_t)q * ldx + (Qout ? Qout[i] : i)] = (double)z;
                 }
             }
-            __threadfence();
             __syncwarp();
             if (lane == 0) st_release(s.bdone + i, part ? -epoch : epoch);
             if (lane == 0) BK_TREC(d.trace, BK_TR_SOLVE, 1, i, t0);

@@ -132,8 +132,7 @@ __global__ void __launch_bounds__(128) bk_levels_kernel(bk_dev d, int32_t epoch,
         if (lane == 0) {
             d.level[c] = lv;
             atomicMax(maxlev, lv);
-            __threadfence();
-            st_release(d.done + c, epoch);
+            st_release(d.done + c, epoch);          // orders this thread's write of the level
             BK_TREC(d.trace, BK_TR_LEVELS, 0, c, t0);
         }
         __syncwarp();
