@@ -224,7 +224,7 @@ __device__ __forceinline__ bool pattern_column(const bk_dev &d, const bk_task &T
     }
     // Algorithm 1's pivot selection, validated for the stored pivot row
     const V xp = x[sp_c];
-    V amax = fabs(xp);
+    unsigned long long km = mag_key(xp);
     if (!isfinite(xp)) bad = true;
     V v[FIX_PF];
 #pragma unroll
@@ -233,7 +233,7 @@ __device__ __forceinline__ bool pattern_column(const bk_dev &d, const bk_task &T
     for (int u = 0; u < FIX_PF; u++) {
         if (fs[u] < 0) continue;
         if (!isfinite(v[u])) bad = true;
-        if (fs[u] >= own_lo && fs[u] < own_hi) amax = fmax(amax, fabs(v[u]));
+        if (fs[u] >= own_lo && fs[u] < own_hi) km = key_max(km, mag_key(v[u]));
         x[fs[u]] = 0.0;
         Lx[lb + lane + 32 * u] = v[u] / xp;
     }
@@ -243,10 +243,11 @@ __device__ __forceinline__ bool pattern_column(const bk_dev &d, const bk_task &T
         const V w = x[s];
         x[s] = 0.0;
         if (!isfinite(w)) bad = true;
-        if (s >= own_lo && s < own_hi) amax = fmax(amax, fabs(w));
+        if (s >= own_lo && s < own_hi) km = key_max(km, mag_key(w));
         Lx[lb + t] = w / xp;
     }
-    amax = warp_max(amax);
+    km = warp_max_key(km);
+    const V amax = key_value<V>(km);
     bad = __any_sync(BK_FULL, bad);
     broken = __any_sync(BK_FULL, broken);
     __syncwarp();

@@ -40,6 +40,43 @@ __device__ __forceinline__ int row_of_lslot(const bk_task &T, int ls)
     return (a >= 0 && v - T.anc_cum[a] < T.anc_hi[a] - T.anc_lo[a]) ? v - T.anc_sh[a] : -1;
 }
 
+// |v| as an unsigned integer key (the bits with the sign cleared): over the
+// finite values and the infinities the keys are ordered as the magnitudes, so a
+// largest magnitude, and the rows that reach it, are found with integer
+// instructions only (NaNs, above the infinities, are caught as non-finite first)
+__device__ __forceinline__ unsigned long long mag_key(double v)
+{
+    return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
+}
+__device__ __forceinline__ unsigned long long mag_key(float v)
+{
+    return (unsigned long long)((unsigned)__float_as_int(v) & 0x7fffffffu);
+}
+template <typename V> __device__ __forceinline__ V key_value(unsigned long long k);
+template <> __device__ __forceinline__ double key_value<double>(unsigned long long k)
+{
+    return __longlong_as_double((long long)k);
+}
+template <> __device__ __forceinline__ float key_value<float>(unsigned long long k)
+{
+    return __int_as_float((int)(unsigned)k);
+}
+template <typename V> __device__ __forceinline__ unsigned long long key_inf();
+template <> __device__ __forceinline__ unsigned long long key_inf<double>() { return 0x7ff0000000000000ull; }
+template <> __device__ __forceinline__ unsigned long long key_inf<float>() { return 0x7f800000ull; }
+
+__device__ __forceinline__ unsigned long long key_max(unsigned long long a, unsigned long long b)
+{
+    return a > b ? a : b;
+}
+
+__device__ __forceinline__ unsigned long long warp_max_key(unsigned long long k)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) k = key_max(k, __shfl_xor_sync(BK_FULL, k, o));
+    return k;
+}
+
 template <typename V>
 __device__ __forceinline__ V warp_max(V v)
 {

@@ -426,7 +426,7 @@ __global__ void __launch_bounds__(128) bk_dd_kernel(bk_dev d, const int32_t *__r
         // pattern's row slots are listed in ascending order, a segment of at most
         // RLIST at a time, and their values read eight per lane at once.
         int *list = rlist + wib * RLIST;
-        V amax = 0.0;
+        unsigned long long km = 0;          // largest own magnitude, as a key
         int ncand = 0, nrows = 0;
         for (int wcur = 0; wcur < nrw;) {
             const int filled = build_list(rb, nrw, wcur, list, lane);
@@ -446,13 +446,14 @@ __global__ void __launch_bounds__(128) bk_dd_kernel(bk_dev d, const int32_t *__r
                     if (!isfinite(v[u])) bad = true;
                     if (ls[u] < nown) {
                         ncand++;
-                        amax = fmax(amax, fabs(v[u]));
+                        km = key_max(km, mag_key(v[u]));
                     }
                 }
             }
             __syncwarp();
         }
-        amax = warp_max(amax);
+        km = warp_max_key(km);
+        const V amax = key_value<V>(km);
         ncand = warp_sum(ncand);
         bad = __any_sync(BK_FULL, bad);
         const int pcur = __ldcg(d.prow + c);
@@ -484,7 +485,7 @@ __global__ void __launch_bounds__(128) bk_dd_kernel(bk_dev d, const int32_t *__r
                         }
 #pragma unroll
                         for (int u = 0; u < RL_PF; u++)
-                            if (ls[u] >= 0 && ls[u] < nown && fabs(v[u]) == amax) best = min(best, ls[u]);
+                            if (ls[u] >= 0 && ls[u] < nown && mag_key(v[u]) == km) best = min(best, ls[u]);
                     }
                     best = warp_min(best);
                     __syncwarp();

@@ -45,29 +45,6 @@ constexpr int DN_THREADS = 1024;
 constexpr int DN_WARPS = DN_THREADS / 32;
 constexpr int DN_CG = 4;             // warps of the owner block that build a step's column
 
-// |v| as an unsigned integer whose order is that of |v| over the finite values
-// and the infinities (NaNs above them): the bits with the sign cleared
-__device__ __forceinline__ unsigned long long mag_bits(double v)
-{
-    return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
-}
-__device__ __forceinline__ unsigned long long mag_bits(float v)
-{
-    return (unsigned long long)((unsigned)__float_as_int(v) & 0x7fffffffu);
-}
-template <typename V> __device__ __forceinline__ unsigned long long mag_inf();
-template <> __device__ __forceinline__ unsigned long long mag_inf<double>() { return 0x7ff0000000000000ull; }
-template <> __device__ __forceinline__ unsigned long long mag_inf<float>() { return 0x7f800000ull; }
-template <typename V> __device__ __forceinline__ V mag_value(unsigned long long k);
-template <> __device__ __forceinline__ double mag_value<double>(unsigned long long k)
-{
-    return __longlong_as_double((long long)k);
-}
-template <> __device__ __forceinline__ float mag_value<float>(unsigned long long k)
-{
-    return __int_as_float((int)(unsigned)k);
-}
-
 // the column group's barrier (named barrier 1, DN_CG warps)
 __device__ __forceinline__ void cg_bar() { asm volatile("bar.sync 1, %0;" ::"n"(DN_CG * 32) : "memory"); }
 
@@ -275,18 +252,14 @@ __global__ void __launch_bounds__(DN_THREADS) bk_dense_node_kernel(bk_dev d, con
             bool bad = cbad[k] != 0;
             for (int sl = ct; sl < lsp; sl += CT) {
                 if (!((colb[sl >> 5] >> (sl & 31)) & 1u)) continue;
-                const unsigned long long key = mag_bits(colv[sl]);
-                if (key >= mag_inf<V>()) bad = true;
+                const unsigned long long key = mag_key(colv[sl]);
+                if (key >= key_inf<V>()) bad = true;
                 if (sl < nown) {
                     ncand++;
                     kmax = key > kmax ? key : kmax;
                 }
             }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const unsigned long long t = __shfl_xor_sync(BK_FULL, kmax, o);
-                kmax = t > kmax ? t : kmax;
-            }
+            kmax = warp_max_key(kmax);
             ncand = warp_sum(ncand);
             bad = __any_sync(BK_FULL, bad);
             if (lane == 0) {
@@ -304,7 +277,7 @@ __global__ void __launch_bounds__(DN_THREADS) bk_dense_node_kernel(bk_dev d, con
                 ncand += S.redc[g];
                 bad = bad || S.redb[g] != 0;
             }
-            const V amax = mag_value<V>(kmax);
+            const V amax = key_value<V>(kmax);
             const bool stop = S.cstop != 0;
             int ps = -1;
             const bool ok = !stop && !bad && ncand > 0 && kmax > 0;
@@ -315,7 +288,7 @@ __global__ void __launch_bounds__(DN_THREADS) bk_dense_node_kernel(bk_dev d, con
                 // the lowest candidate row holding the maximum
                 int best = INT_MAX;
                 for (int sl = ct; sl < nown; sl += CT)
-                    if (((colb[sl >> 5] >> (sl & 31)) & 1u) && mag_bits(colv[sl]) == kmax) { best = sl; break; }
+                    if (((colb[sl >> 5] >> (sl & 31)) & 1u) && mag_key(colv[sl]) == kmax) { best = sl; break; }
                 best = warp_min(best);
                 if (lane == 0) S.redi[wid] = best;
             }

@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(32) bk_gp_task_kernel(bk_dev d, const int32_t 
         }
 
         // Algorithm 1's pivot selection: threshold pivot among the unpivoted own rows
-        V amax = 0.0;
+        unsigned long long km = 0;          // largest own magnitude, as a key
         int ncand = 0;
         for (int w = lane; w < nrw; w += 32) {
             uint32_t bits = rb[w];
@@ -287,11 +287,12 @@ __global__ void __launch_bounds__(32) bk_gp_task_kernel(bk_dev d, const int32_t 
                 if (!isfinite(v)) bad = true;
                 if (ls < nown) {
                     ncand++;
-                    amax = fmax(amax, fabs(v));
+                    km = key_max(km, mag_key(v));
                 }
             }
         }
-        amax = warp_max(amax);
+        km = warp_max_key(km);
+        const V amax = key_value<V>(km);
         ncand = warp_sum(ncand);
         bad = __any_sync(BK_FULL, bad);
         int piv = -1;
@@ -308,7 +309,7 @@ __global__ void __launch_bounds__(32) bk_gp_task_kernel(bk_dev d, const int32_t 
                         const int b = __ffs(bits) - 1;
                         bits &= bits - 1;
                         const int ls = (w << 5) + b;
-                        if (ls < nown && fabs(x[ls]) == amax) { best = ls; break; }
+                        if (ls < nown && mag_key(x[ls]) == km) { best = ls; break; }
                     }
                     if (best != INT_MAX) break;
                 }

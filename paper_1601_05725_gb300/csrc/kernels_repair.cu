@@ -396,7 +396,7 @@ __global__ void __launch_bounds__(RP_NT, 1) bk_repair_kernel(bk_dev d, const int
             why = warp_max_i(why);
             if (lane == 0) BK_TPHASE(d.trace, tp, 4, c);       // the reach (if needed)
                 // the pivot rule over the task's unpivoted rows of the pattern
-                V amax = V(0);
+                unsigned long long km = 0;      // largest own magnitude, as a key
                 int ncand = 0, nrows = 0;
                 for (int wcur = 0; wcur < nrw;) {
                     const int filled = list_rows(rb, nrw, wcur, list, lane);
@@ -416,13 +416,14 @@ __global__ void __launch_bounds__(RP_NT, 1) bk_repair_kernel(bk_dev d, const int
                             if (!isfinite(v[u])) bad = true;
                             if (ls[u] < nown) {
                                 ncand++;
-                                amax = fmax(amax, fabs(v[u]));
+                                km = key_max(km, mag_key(v[u]));
                             }
                         }
                     }
                     __syncwarp();
                 }
-                amax = warp_max(amax);
+                km = warp_max_key(km);
+                const V amax = key_value<V>(km);
                 ncand = warp_sum(ncand);
                 bad = __any_sync(BK_FULL, bad);
                 const int pcur = __ldcg(d.prow + c);
@@ -442,7 +443,7 @@ __global__ void __launch_bounds__(RP_NT, 1) bk_repair_kernel(bk_dev d, const int
                             for (int i0 = 0; i0 < filled; i0 += 32) {
                                 const int i = i0 + lane;
                                 const int ls = i < filled ? list[i] : -1;
-                                if (ls >= 0 && ls < nown && fabs(x[ls]) == amax) best = min(best, ls);
+                                if (ls >= 0 && ls < nown && mag_key(x[ls]) == km) best = min(best, ls);
                             }
                             best = warp_min(best);
                             __syncwarp();
