@@ -98,7 +98,13 @@ typedef struct {
                                      basker_factor take the refactorization's path);
                                      1: by Algorithm 3's elimination-tree counts of the
                                      symmetric structure (upper bounds, no pattern stored,
-                                     cheaper; every basker_factor runs the complete pass) */
+                                     cheaper; every basker_factor runs the complete pass);
+                                     2: by Algorithm 3 with its interval estimates (Sec.
+                                     III-C): the leaves and BTF blocks counted as in 1,
+                                     every separator column taken dense between the lowest
+                                     and highest row its descendants' lest ranges give
+                                     (looser upper bounds of 1's, column by column; no
+                                     pattern stored); other values: INVALID_ARG */
     int reserved[1];
 } basker_options;
 
@@ -161,7 +167,9 @@ void basker_default_options(basker_options *opt);
 /* The symbolic counts alone, on the host (no device, no handle): the same
  * arguments as basker_symbolic, then mode (0: the structural pass under the
  * natural pivots, exact for those pivots; 1: Algorithm 3's elimination-tree
- * counts of the symmetric structure, Sec. III-C, an upper bound of mode 0's) and
+ * counts of the symmetric structure, Sec. III-C, an upper bound of mode 0's; 2:
+ * Algorithm 3 with the interval (lest) estimates for the separators, an upper
+ * bound of mode 1's) and
  * two host arrays of n ints (either may be NULL) receiving each column's L count
  * (strictly lower entries) and U count (diagonal included).  Errors: INVALID_ARG,
  * NOT_BTF, BAD_ND; the arrays are untouched on error. */

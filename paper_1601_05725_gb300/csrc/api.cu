@@ -1274,7 +1274,7 @@ int basker_symbolic_counts(int32_t n, const int32_t *colptr, const int32_t *rowi
                            int32_t nd_leaves, const int32_t *nd_node_ptr, int mode, int32_t *l_count,
                            int32_t *u_count)
 {
-    if (mode < 0 || mode > 1) return BASKER_ERR_INVALID_ARG;
+    if (mode < 0 || mode > 2) return BASKER_ERR_INVALID_ARG;
     bk_plan pl;
     int32_t bad = -1;
     const int st = bk_plan_build(n, colptr, rowind, P, Q, nblocks, block_ptr, nd_block, nd_leaves, nd_node_ptr,
@@ -1299,7 +1299,7 @@ int basker_symbolic(int32_t n, const int32_t *colptr, const int32_t *rowind, con
     if (!(h->opt.tau > 0.0 && h->opt.tau <= 1.0) || h->opt.slack < 0.0 || h->opt.wait_budget_cycles <= 0 ||
         h->opt.factor_mode < 0 || h->opt.factor_mode > 1 || h->opt.precision < 0 || h->opt.precision > 2 ||
         h->opt.refactor_switch < 0 || h->opt.refactor_switch > 3 || h->opt.symbolic_mode < 0 ||
-        h->opt.symbolic_mode > 1 ||
+        h->opt.symbolic_mode > 2 ||
         (h->opt.precision >= 1 && (h->opt.ir_max_iter < 1 || !(h->opt.ir_tol > 0.0) || !(h->opt.growth_limit > 0.0)))) {
         delete h;
         return BASKER_ERR_INVALID_ARG;

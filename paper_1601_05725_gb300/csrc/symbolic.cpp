@@ -9,8 +9,10 @@
 // Gilbert-Peierls pass under the preferred (natural) pivots (exact counts for
 // those pivots, plus the pattern and a static schedule for the first
 // factorization; symmetric pruning of the reach graph, Eisenstat and Liu, keeps
-// its cost near |L+U|), or with Algorithm 3's elimination-tree counts, which store
-// no pattern (options.symbolic_mode 1).  Slack covers pivoting.
+// its cost near |L+U|), or with Algorithm 3's counts, which store no pattern:
+// exact elimination-tree counts everywhere (options.symbolic_mode 1), or exact at
+// the leaves and the paper's interval estimates for the separators
+// (options.symbolic_mode 2).  Slack covers pivoting.
 #include <algorithm>
 #include <cstring>
 #include <numeric>
@@ -88,6 +90,69 @@ size_t bk_task_smem_bytes(const bk_task &t)
 
 bool bk_task_fits_smem(const bk_task &t) { return bk_task_smem_bytes(t) <= bk_gp_smem_limit(); }
 
+// The lower adjacency of the symmetric structure inside each diagonal block (for
+// each column c the rows i < c with B(i,c) != 0 or B(c,i) != 0) and its
+// elimination tree (Liu's algorithm with path compression).
+struct SymTree {
+    std::vector<int64_t> ap;
+    std::vector<int32_t> ai, parent;
+};
+
+static void sym_tree(const bk_plan &pl, SymTree &st)
+{
+    const int32_t n = pl.n;
+    std::vector<int32_t> blk((size_t)n);
+    for (int32_t d = 0; d < pl.nblocks; d++)
+        for (int32_t i = pl.block_ptr[(size_t)d]; i < pl.block_ptr[(size_t)d + 1]; i++) blk[(size_t)i] = d;
+    st.ap.assign((size_t)n + 1, 0);
+    for (int32_t c = 0; c < n; c++)
+        for (int32_t e = pl.dstart[(size_t)c]; e < pl.Bp[(size_t)c + 1]; e++) {
+            const int32_t r = pl.Bi[(size_t)e];
+            if (r == c || blk[(size_t)r] != blk[(size_t)c]) continue;
+            st.ap[(size_t)std::max(r, c) + 1]++;
+        }
+    for (int32_t c = 0; c < n; c++) st.ap[(size_t)c + 1] += st.ap[(size_t)c];
+    st.ai.assign((size_t)st.ap[(size_t)n], 0);
+    std::vector<int64_t> fill(st.ap.begin(), st.ap.end() - 1);
+    for (int32_t c = 0; c < n; c++)
+        for (int32_t e = pl.dstart[(size_t)c]; e < pl.Bp[(size_t)c + 1]; e++) {
+            const int32_t r = pl.Bi[(size_t)e];
+            if (r == c || blk[(size_t)r] != blk[(size_t)c]) continue;
+            st.ai[(size_t)fill[(size_t)std::max(r, c)]++] = std::min(r, c);
+        }
+    st.parent.assign((size_t)n, -1);
+    std::vector<int32_t> anc((size_t)n, -1);
+    for (int32_t c = 0; c < n; c++)
+        for (int64_t e = st.ap[(size_t)c]; e < st.ap[(size_t)c + 1]; e++) {
+            int32_t r = st.ai[(size_t)e];
+            while (anc[(size_t)r] != -1 && anc[(size_t)r] != c) {
+                const int32_t t = anc[(size_t)r];
+                anc[(size_t)r] = c;
+                r = t;
+            }
+            if (anc[(size_t)r] == -1) {
+                anc[(size_t)r] = c;
+                st.parent[(size_t)r] = c;
+            }
+        }
+}
+
+static void finish_counts(bk_plan &pl)
+{
+    int64_t nl = 0, nu = 0;
+    for (int32_t c = 0; c < pl.n; c++) {
+        nl += pl.sLcnt[(size_t)c];
+        nu += pl.sUcnt[(size_t)c];
+    }
+    pl.nnz_l_sym = nl;
+    pl.nnz_u_sym = nu;
+    pl.sLi.clear();
+    pl.sUi.clear();
+    pl.sprow.clear();
+    pl.slevel.clear();
+    pl.sorder.clear();
+}
+
 // Algorithm 3's counts (Sec. III-C, parallel symbolic factorization), per BTF
 // diagonal block: the elimination tree of the symmetric structure B_dd + B_dd^T
 // (one tree for the whole ND block: its separators are the ancestors of their
@@ -98,73 +163,152 @@ bool bk_task_fits_smem(const bk_task &t) { return bk_task_smem_bytes(t) <= bk_gp
 // node j is L(:,j)'s count.  These are the counts of the Cholesky factor of the
 // symmetric structure, which contains the LU pattern of the natural pivots, so
 // they never fall below the structural pass's counts (equal for a symmetric
-// pattern); the paper's interval estimates of the upper tree levels (dense between
-// the minimum and the maximum row) are looser than these exact tree counts, which
-// cost O(|L + U|) node visits here.  No pattern is stored.
+// pattern); they cost O(|L + U|) node visits.  No pattern is stored
+// (options.symbolic_mode 1).
 static void etree_counts(bk_plan &pl)
 {
     const int32_t n = pl.n;
     pl.sLcnt.assign((size_t)n, 0);
     pl.sUcnt.assign((size_t)n, 0);
-    // lower adjacency of the symmetric structure inside each diagonal block:
-    // for each column c the rows i < c with B(i,c) != 0 or B(c,i) != 0
-    std::vector<int32_t> blk((size_t)n);
-    for (int32_t d = 0; d < pl.nblocks; d++)
-        for (int32_t i = pl.block_ptr[(size_t)d]; i < pl.block_ptr[(size_t)d + 1]; i++) blk[(size_t)i] = d;
-    std::vector<int64_t> ap((size_t)n + 1, 0);
-    for (int32_t c = 0; c < n; c++)
-        for (int32_t e = pl.dstart[(size_t)c]; e < pl.Bp[(size_t)c + 1]; e++) {
-            const int32_t r = pl.Bi[(size_t)e];
-            if (r == c || blk[(size_t)r] != blk[(size_t)c]) continue;
-            ap[(size_t)std::max(r, c) + 1]++;
-        }
-    for (int32_t c = 0; c < n; c++) ap[(size_t)c + 1] += ap[(size_t)c];
-    std::vector<int32_t> ai((size_t)ap[(size_t)n]);
-    std::vector<int64_t> fill(ap.begin(), ap.end() - 1);
-    for (int32_t c = 0; c < n; c++)
-        for (int32_t e = pl.dstart[(size_t)c]; e < pl.Bp[(size_t)c + 1]; e++) {
-            const int32_t r = pl.Bi[(size_t)e];
-            if (r == c || blk[(size_t)r] != blk[(size_t)c]) continue;
-            ai[(size_t)fill[(size_t)std::max(r, c)]++] = std::min(r, c);
-        }
-    // elimination tree (Liu's algorithm with path compression)
-    std::vector<int32_t> parent((size_t)n, -1), anc((size_t)n, -1);
-    for (int32_t c = 0; c < n; c++)
-        for (int64_t e = ap[(size_t)c]; e < ap[(size_t)c + 1]; e++) {
-            int32_t r = ai[(size_t)e];
-            while (anc[(size_t)r] != -1 && anc[(size_t)r] != c) {
-                const int32_t t = anc[(size_t)r];
-                anc[(size_t)r] = c;
-                r = t;
-            }
-            if (anc[(size_t)r] == -1) {
-                anc[(size_t)r] = c;
-                parent[(size_t)r] = c;
-            }
-        }
+    SymTree st;
+    sym_tree(pl, st);
     // row subtrees
     std::vector<int32_t> mark((size_t)n, -1);
-    int64_t nl = 0, nu = 0;
     for (int32_t c = 0; c < n; c++) {
         int32_t uc = 1;
         mark[(size_t)c] = c;
-        for (int64_t e = ap[(size_t)c]; e < ap[(size_t)c + 1]; e++)
-            for (int32_t r = ai[(size_t)e]; r >= 0 && mark[(size_t)r] != c; r = parent[(size_t)r]) {
+        for (int64_t e = st.ap[(size_t)c]; e < st.ap[(size_t)c + 1]; e++)
+            for (int32_t r = st.ai[(size_t)e]; r >= 0 && mark[(size_t)r] != c; r = st.parent[(size_t)r]) {
                 mark[(size_t)r] = c;
                 uc++;
                 pl.sLcnt[(size_t)r]++;
             }
         pl.sUcnt[(size_t)c] = uc;
-        nu += uc;
     }
-    for (int32_t c = 0; c < n; c++) nl += pl.sLcnt[(size_t)c];
-    pl.nnz_l_sym = nl;
-    pl.nnz_u_sym = nu;
-    pl.sLi.clear();
-    pl.sUi.clear();
-    pl.sprow.clear();
-    pl.slevel.clear();
-    pl.sorder.clear();
+    finish_counts(pl);
+}
+
+// Algorithm 3's reading of the upper tree levels (options.symbolic_mode 2).  The
+// ND leaves and the BTF blocks (tree levels -1 and 0) are counted exactly, by the
+// row subtrees above; for each of their columns t the rows of L(:,t) in every
+// ancestor node are kept as a range (lest: the lowest and the highest row).  The
+// separators are then estimated level by level up the tree: a row t below
+// separator column c is taken to reach c (an entry U(t,c)) when c lies in t's
+// range for c's node (for the symmetric structure the columns of U's row t are
+// the rows of L's column t, so lest also serves as uest), and column c's rows in
+// each node (its own, each ancestor) are taken dense between the lowest and the
+// highest row of the ranges of those t, of the column's own entries, and of the
+// earlier columns of its node that reach it.  Each range holds the exact rows,
+// so the estimates bound the tree counts (mode 1) from above, column by column.
+static void interval_counts(bk_plan &pl)
+{
+    const int32_t n = pl.n;
+    pl.sLcnt.assign((size_t)n, 0);
+    pl.sUcnt.assign((size_t)n, 0);
+    SymTree st;
+    sym_tree(pl, st);
+    auto task_of = [&](int32_t c) -> const bk_task & { return pl.tasks[(size_t)pl.col_task[(size_t)c]]; };
+    auto exact = [&](int32_t c) { return task_of(c).level == 0; };
+    // lest: per column, one range per ancestor node and one for its own node
+    std::vector<int64_t> off((size_t)n + 1, 0);
+    for (int32_t c = 0; c < n; c++) off[(size_t)c + 1] = off[(size_t)c] + task_of(c).nanc + 1;
+    std::vector<int32_t> lmin((size_t)off[(size_t)n], INT32_MAX), lmax((size_t)off[(size_t)n], -1);
+    auto anc_slot = [](const bk_task &K, int32_t r) {
+        for (int32_t a = 0; a < K.nanc; a++)
+            if (r >= K.anc_lo[a] && r < K.anc_hi[a]) return a;
+        return -1;
+    };
+    // exact levels: row subtrees, which stop at the first separator column
+    std::vector<int32_t> mark((size_t)n, -1);
+    for (int32_t c = 0; c < n; c++) {
+        const bool crow = exact(c);
+        int32_t uc = 1;
+        mark[(size_t)c] = c;
+        for (int64_t e = st.ap[(size_t)c]; e < st.ap[(size_t)c + 1]; e++)
+            for (int32_t r = st.ai[(size_t)e]; r >= 0 && mark[(size_t)r] != c; r = st.parent[(size_t)r]) {
+                if (!exact(r)) break;                // a separator column: estimated below
+                mark[(size_t)r] = c;
+                uc++;
+                pl.sLcnt[(size_t)r]++;
+                if (!crow) {                         // row c of an ancestor node in L(:,r)
+                    const int32_t a = anc_slot(task_of(r), c);
+                    if (a >= 0) {
+                        const int64_t k = off[(size_t)r] + a;
+                        lmin[(size_t)k] = std::min(lmin[(size_t)k], c);
+                        lmax[(size_t)k] = std::max(lmax[(size_t)k], c);
+                    }
+                }
+            }
+        if (crow) pl.sUcnt[(size_t)c] = uc;
+    }
+    // the upper adjacency (rows r > c of each column's symmetric structure)
+    std::vector<int64_t> up((size_t)n + 1, 0);
+    for (int32_t r = 0; r < n; r++)
+        for (int64_t e = st.ap[(size_t)r]; e < st.ap[(size_t)r + 1]; e++) up[(size_t)st.ai[(size_t)e] + 1]++;
+    for (int32_t c = 0; c < n; c++) up[(size_t)c + 1] += up[(size_t)c];
+    std::vector<int32_t> ui((size_t)up[(size_t)n]);
+    {
+        std::vector<int64_t> fill(up.begin(), up.end() - 1);
+        for (int32_t r = 0; r < n; r++)
+            for (int64_t e = st.ap[(size_t)r]; e < st.ap[(size_t)r + 1]; e++)
+                ui[(size_t)fill[(size_t)st.ai[(size_t)e]]++] = r;
+    }
+    // separators, children before parents (the tasks are in postorder)
+    for (const bk_task &J : pl.tasks) {
+        if (J.level == 0 || J.node < 0) continue;
+        const int32_t m = J.hi - J.lo, ns = J.nanc, w = ns + 1;     // ranges: ancestors, then own
+        std::vector<int32_t> cnt((size_t)m, 0), rmin((size_t)m * w, INT32_MAX), rmax((size_t)m * w, -1);
+        auto hull = [&](int32_t c, int32_t q, int32_t lo, int32_t hi) {
+            if (hi < lo) return;
+            const size_t k = (size_t)(c - J.lo) * w + q;
+            rmin[k] = std::min(rmin[k], lo);
+            rmax[k] = std::max(rmax[k], hi);
+        };
+        // rows below the separator: a range covering column c reaches it
+        for (int32_t t = J.sp_lo; t < J.lo; t++) {
+            const bk_task &K = task_of(t);
+            const int32_t a = anc_slot(K, J.lo);
+            if (a < 0) continue;
+            const int64_t k0 = off[(size_t)t];
+            const int32_t mn = lmin[(size_t)k0 + a], mx = lmax[(size_t)k0 + a];
+            for (int32_t c = std::max(mn, J.lo); c <= std::min(mx, J.hi - 1); c++) {
+                cnt[(size_t)(c - J.lo)]++;
+                for (int32_t q = 0; q < ns; q++)
+                    hull(c, q, lmin[(size_t)k0 + a + 1 + q], lmax[(size_t)k0 + a + 1 + q]);
+                hull(c, ns, std::max(mn, c + 1), mx);
+            }
+        }
+        for (int32_t c = J.lo; c < J.hi; c++) {
+            // the column's own entries
+            for (int64_t e = up[(size_t)c]; e < up[(size_t)c + 1]; e++) {
+                const int32_t r = ui[(size_t)e];
+                if (r < J.hi) {
+                    hull(c, ns, r, r);
+                } else {
+                    const int32_t q = anc_slot(J, r);
+                    if (q >= 0) hull(c, q, r, r);
+                }
+            }
+            const size_t k = (size_t)(c - J.lo) * w;
+            int64_t lc = 0;
+            for (int32_t q = 0; q <= ns; q++)
+                if (rmax[k + q] >= rmin[k + q]) lc += rmax[k + q] - rmin[k + q] + 1;
+            pl.sLcnt[(size_t)c] = (int32_t)lc;
+            pl.sUcnt[(size_t)c] = cnt[(size_t)(c - J.lo)] + 1;
+            for (int32_t q = 0; q <= ns; q++) {
+                lmin[(size_t)off[(size_t)c] + q] = rmin[k + q];
+                lmax[(size_t)off[(size_t)c] + q] = rmax[k + q];
+            }
+            // the later columns of the node that this column's own range reaches
+            const int32_t mn = rmin[k + ns], mx = rmax[k + ns];
+            for (int32_t c2 = std::max(mn, c + 1); c2 <= mx && c2 < J.hi; c2++) {
+                cnt[(size_t)(c2 - J.lo)]++;
+                for (int32_t q = 0; q < ns; q++) hull(c2, q, rmin[k + q], rmax[k + q]);
+                hull(c2, ns, std::max(mn, c2 + 1), mx);
+            }
+        }
+    }
+    finish_counts(pl);
 }
 
 // The ancestor ranges as sorted tables of BK_MAX_ANC entries (unused ones
@@ -354,9 +498,10 @@ int bk_plan_build(int32_t n, const int32_t *colptr, const int32_t *rowind, const
     pl.max_space = 0;
     for (auto &T : pl.tasks) pl.max_space = std::max(pl.max_space, T.space);
 
-    pl.counts_only = mode == 1;
-    if (mode == 1) {
-        etree_counts(pl);
+    pl.counts_only = mode == 1 || mode == 2;
+    if (pl.counts_only) {
+        if (mode == 1) etree_counts(pl);
+        else interval_counts(pl);
         pl.symbolic_singular = -1;
         bk_plan_layout(pl);
         return BASKER_OK;

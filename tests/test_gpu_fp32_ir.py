@@ -132,7 +132,7 @@ def test_stalled_refinement_falls_back_to_fp64():
 
 def test_precision_option_is_validated():
     prob = I.small_problem(33, "grid", k=10, depth=1)
-    for kw in (dict(precision=3), dict(refactor_switch=4), dict(factor_mode=2), dict(symbolic_mode=2), dict(precision=1, ir_max_iter=0), dict(precision=1, ir_tol=0.0),
+    for kw in (dict(precision=3), dict(refactor_switch=4), dict(factor_mode=2), dict(symbolic_mode=3), dict(precision=1, ir_max_iter=0), dict(precision=1, ir_tol=0.0),
                dict(precision=1, growth_limit=-1.0)):
         with pytest.raises(basker.BaskerError) as e:
             basker.Handle.from_problem(prob, **kw)

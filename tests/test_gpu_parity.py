@@ -202,21 +202,23 @@ def test_factorization_by_the_stored_pattern_path(kind, seed, kw, dominant):
     np.testing.assert_array_equal(h.solve(_dev(b)).cpu().numpy(), o.solve(b))
 
 
+@pytest.mark.parametrize("mode", [1, 2])
 @pytest.mark.parametrize("kind,seed,kw", [
     ("netlist", 95, dict(n_small=60, m_netlist=800, depth=3)),
     ("grid", 96, dict(k=36, depth=3)),
     ("blocks", 97, dict(nblocks=60, size_range=(2, 300))),
 ])
-def test_tree_count_sizing_gives_the_same_factors(kind, seed, kw):
+def test_tree_count_sizing_gives_the_same_factors(kind, seed, kw, mode):
     """options.symbolic_mode 1 sizes L and U by Algorithm 3's elimination-tree
-    counts (no pattern stored, every factorization a complete pass): the factors,
+    counts, mode 2 by Algorithm 3's interval estimates for the separators (no
+    pattern stored, every factorization a complete pass): the factors,
     refactorizations and solves are the oracle's."""
     prob = I.small_problem(seed, kind, **kw)
     o, s = _oracle(prob)
     f = o.factors()
-    h = basker.Handle.from_problem(prob, symbolic_mode=1)
+    h = basker.Handle.from_problem(prob, symbolic_mode=mode)
     inf = h.info()
-    l1, u1 = basker.symbolic_counts(prob, 1)
+    l1, u1 = basker.symbolic_counts(prob, mode)
     assert inf["nnz_l_sym"] == l1.sum() and inf["nnz_u_sym"] == u1.sum()
     h.factor(_dev(prob.values))
     assert_same_factors(h, f)
