@@ -638,16 +638,12 @@ SERVE_PATTERNS = 48
 
 
 def _serving_pattern(spec):
-    """One serving pattern: a netlist circuit as in the n = 2,000 circuit workload
-    (40% of the rows in BTF blocks of U{1,2} rows around one ND-ordered netlist
-    block), each small block coupled into a random later block."""
+    """One serving pattern: a netlist block as in the n = 2,000 circuit workload,
+    BTF blocks omitted, ND depth by size (2..5)."""
     from paper_1601_05725_gb300 import inputs
     seed, m = spec
-    n_small = int(round(0.4 * m))
-    m_net = m - n_small
-    depth = int(np.clip(round(np.log2(m_net / 1500.0)), 2, 8))
-    return inputs.netlist_problem(seed, n_small=n_small, small_sizes=(1, 2), m_netlist=m_net, depth=depth,
-                                  coupling_to="random", name=f"serve_{seed}")
+    depth = int(np.clip(round(np.log2(m / 2000.0)), 2, 5))
+    return inputs.netlist_problem(seed, n_small=0, m_netlist=m, depth=depth, name=f"serve_{seed}")
 
 
 def serving_patterns(npat: int = SERVE_PATTERNS):
