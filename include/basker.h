@@ -81,7 +81,9 @@ typedef struct {
                                      column recomputation until they have taken as long
                                      as the handle's last complete factorization, the rest
                                      then one complete Algorithm 1 pass with the previous
-                                     pivots preferred; 1: rounds only; 2: the complete
+                                     pivots preferred (that pass at once when more than
+                                     max(16, n/200) pivots were rejected); 1: rounds
+                                     only; 2: the complete
                                      pass at once; 3: when every ND separator fits the
                                      dense elimination, the repair pass (one block of
                                      threads per ND leaf or BTF block walks its columns

@@ -44,6 +44,7 @@ struct basker_s {
     int32_t epoch = 0, solve_epoch = 0, refno = 0;
     bool factored = false, ws_dirty = false, schedule_valid = true, order_is_symbolic = true;
     double gp_wall_ms = 0.0;     // wall time of the last complete Algorithm 1 pass (host clock)
+    double round_us_per_col = 0.0;   // a refactorization round's wall time per column it processed
     bool sep_dense = false;      // refactorizations recompute every separator densely
     // the repair pass (sep_dense): the tasks it serves (every task without
     // descendants), its dynamic shared memory and its persistent blocks
@@ -429,9 +430,14 @@ int setup_device(basker_t h)
     d.wsd_slice = pl.wsd_slice;
     d.wsd_warps = pl.wsd_warps;
     d.dd_words = pl.dd_words;
-    TRY(dalloc(h, &d.wsd, (size_t)(pl.wsd_slice * pl.wsd_warps), true));
+    TRY(dalloc(h, &d.wsd, (size_t)pl.wsd_bytes, true));
     d.sx_warps = bk_static_blocks() * 4;
-    d.sx_stride = ((int64_t)pl.max_space + 31) & ~(int64_t)31;
+    // x over the space of the tasks the stored-pattern pass computes (it leaves the
+    // separators that the dense elimination recomputes)
+    int32_t sx_space = 1;
+    for (const bk_task &T : pl.tasks)
+        if (!T.dense) sx_space = std::max(sx_space, T.space);
+    d.sx_stride = ((int64_t)sx_space + 31) & ~(int64_t)31;
     TRY(dalloc(h, &d.sx, (size_t)(d.sx_stride * d.sx_warps), true));
     d.nblocks = pl.nblocks;
     TRY(upload(h, (int32_t **)&d.block_ptr, pl.block_ptr));
@@ -528,6 +534,8 @@ int setup_device(basker_t h)
 
 // launch_redo's answer when the rest of a refactorization is cheaper as one complete pass
 constexpr int BK_SWITCH_TO_FULL = -2;
+// rounds of at least this many columns give the cost per column the switch predicts with
+constexpr size_t BK_ROUND_LARGE = 100000;
 
 int reset_status(basker_t h, cudaStream_t s)
 {
@@ -536,7 +544,7 @@ int reset_status(basker_t h, cudaStream_t s)
     CU(cudaMemsetAsync(&h->d.status->first_fail, 0xff, sizeof(unsigned long long), s));
     if (h->ws_dirty) {
         CU(cudaMemsetAsync(h->d.ws, 0, (size_t)std::max<int64_t>(h->pl.ws_bytes, 256), s));
-        CU(cudaMemsetAsync(h->d.wsd, 0, (size_t)(h->pl.wsd_slice * h->pl.wsd_warps), s));
+        CU(cudaMemsetAsync(h->d.wsd, 0, (size_t)h->pl.wsd_bytes, s));
         CU(cudaMemsetAsync(h->d.sx, 0, sizeof(double) * (size_t)(h->d.sx_stride * h->d.sx_warps), s));
         h->ws_dirty = false;
     }
@@ -584,19 +592,42 @@ int regrow(basker_t h)
     return BASKER_OK;
 }
 
-// The descendant phase of separator columns cols[0..ncols) in a refactorization:
-// first on their stored patterns (verified on the device), then the reach kernel
-// over the columns that failed (their list and count stay on the device).
-int launch_desc_refactor(basker_t h, const int32_t *cols, int32_t ncols, cudaStream_t s)
+// The handle's device view with the column-per-warp workspace cut into the
+// slices of ND level l (one workspace serves the levels in turn).
+bk_dev level_dev(basker_t h, size_t l)
+{
+    bk_dev d = h->d;
+    if (l < h->pl.level_slice.size()) {
+        d.wsd_slice = h->pl.level_slice[l];
+        d.wsd_warps = h->pl.level_warps[l];
+    }
+    return d;
+}
+
+// The descendant phase of separator columns cols[0..ncols) of ND level `level` in
+// a refactorization: first on their stored patterns (verified on the device),
+// then the reach kernel over the columns that failed (their list and count stay
+// on the device).
+int launch_desc_refactor(basker_t h, const int32_t *cols, int32_t ncols, cudaStream_t s, size_t level)
 {
     if (ncols <= 0) return BASKER_OK;
+    const bk_dev dl = level_dev(h, level);
     CU(cudaMemsetAsync(h->d.counter + 5, 0, sizeof(int32_t), s));
     CU(cudaMemsetAsync(h->d.counter + 7, 0, sizeof(int32_t), s));
     CU(cudaMemsetAsync(h->d.counter + 3, 0, sizeof(int32_t), s));
+    if (!h->df_smem) {
+        // separators too large for the stored-pattern kernel: every column by the reach
+        tbeg(h, KT_DESC, s, 1);
+        bk_launch_gp_desc(dl, cols, ncols, h->d.counter + 3, s);
+        CU(cudaGetLastError());
+        tend(h, s);
+        h->launches++;
+        return BASKER_OK;
+    }
     tbeg(h, KT_DESC, s, 2);
-    bk_launch_desc_fast(h->d, cols, ncols, h->d.counter + 5, h->df_redo, h->d.counter + 7, h->df_smem, s);
+    bk_launch_desc_fast(dl, cols, ncols, h->d.counter + 5, h->df_redo, h->d.counter + 7, h->df_smem, s);
     CU(cudaGetLastError());
-    bk_launch_gp_desc(h->d, h->df_redo, ncols, h->d.counter + 3, s, h->d.counter + 7);
+    bk_launch_gp_desc(dl, h->df_redo, ncols, h->d.counter + 3, s, h->d.counter + 7);
     CU(cudaGetLastError());
     tend(h, s);
     h->launches += 2;
@@ -612,7 +643,7 @@ int launch_full_gp(basker_t h, cudaStream_t s, int pref_mode)
         if (l > 0 && h->lv_ncols[l] > 0) {
             CU(cudaMemsetAsync(h->d.counter + 3, 0, sizeof(int32_t), s));
             tbeg(h, KT_DESC, s, 1);
-            bk_launch_gp_desc(h->d, h->lv_cols[l], h->lv_ncols[l], h->d.counter + 3, s);
+            bk_launch_gp_desc(level_dev(h, l), h->lv_cols[l], h->lv_ncols[l], h->d.counter + 3, s);
             CU(cudaGetLastError());
             tend(h, s);
             h->launches++;
@@ -714,7 +745,7 @@ int launch_redo(basker_t h, cudaStream_t s)
                 TRY(stage_upload(h, s, h->rd_cols, cols, 0));
                 TRY(stage_upload(h, s, h->rd_tasks, dense[0], (size_t)pl.n));
                 TRY(stage_upload(h, s, h->rd_tasks + dense[0].size(), dense[1], (size_t)pl.n + dense[0].size()));
-                TRY(launch_desc_refactor(h, h->rd_cols, (int32_t)cols.size(), s));
+                TRY(launch_desc_refactor(h, h->rd_cols, (int32_t)cols.size(), s, l));
                 for (int g = 0; g < 2; g++) {
                     if (dense[g].empty()) continue;
                     tbeg(h, KT_DENSE, s, 1);
@@ -737,6 +768,18 @@ int launch_redo(basker_t h, cudaStream_t s)
             std::vector<int32_t> cols;
             for (int32_t t : active)
                 for (int32_t c = start[(size_t)t]; c < pl.tasks[(size_t)t].hi; c++) cols.push_back(c);
+            // a large round that would, at the cost per column of the large rounds
+            // seen so far, take the rounds past a complete pass: the complete pass now
+            // instead (small rounds are dominated by their fixed costs: not predicted)
+            const double limit0 = h->gp_wall_ms > 0.0 ? h->gp_wall_ms : 20.0 * h->static_factor_ms;
+            const double spent = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+            if ((h->opt.refactor_switch == 0 || h->opt.refactor_switch == 3) && limit0 > 0.0 &&
+                h->round_us_per_col > 0.0 && cols.size() >= BK_ROUND_LARGE &&
+                spent + 1e-3 * h->round_us_per_col * (double)cols.size() > limit0) {
+                h->info.last_repivot_columns = redone;
+                return BK_SWITCH_TO_FULL;
+            }
+            const auto tr = std::chrono::steady_clock::now();
             CU(cudaStreamSynchronize(s));       // the staging buffer is reused
             std::memcpy(h->h_stage, start.data(), nt * 4);
             std::memcpy(h->h_stage + nt, flags.data(), nt * 4);
@@ -747,7 +790,7 @@ int launch_redo(basker_t h, cudaStream_t s)
             CU(cudaMemsetAsync(h->d.counter + 3, 0, sizeof(int32_t), s));
             h->epoch++;
             tbeg(h, KT_SPEC, s, 1);
-            bk_launch_dd(h->d, h->rd_cols, (int32_t)cols.size(), h->d.counter + 3, tau, h->epoch,
+            bk_launch_dd(level_dev(h, l), h->rd_cols, (int32_t)cols.size(), h->d.counter + 3, tau, h->epoch,
                          h->opt.wait_budget_cycles, h->refno, s, h->tune_dd);
             CU(cudaGetLastError());
             tend(h, s);
@@ -758,6 +801,11 @@ int launch_redo(basker_t h, cudaStream_t s)
             CU(cudaMemcpyAsync(h->h_task_fail, h->d.task_fail, sizeof(int32_t) * nt, cudaMemcpyDeviceToHost, s));
             const int st = read_status(h, s);
             if (st != BASKER_OK) return st;
+            if (cols.size() >= BK_ROUND_LARGE) {
+                const double us = 1e3 * std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tr).count() /
+                                  (double)cols.size();
+                h->round_us_per_col = h->round_us_per_col > 0.0 ? 0.5 * (h->round_us_per_col + us) : us;
+            }
             std::vector<int32_t> next;
             for (int32_t t : active) {
                 const bk_task &T = pl.tasks[(size_t)t];
@@ -811,7 +859,7 @@ int launch_repair_path(basker_t h, cudaStream_t s)
     tend(h, s);
     h->launches++;
     for (size_t l = 1; l < h->lv_tasks.size(); l++) {
-        TRY(launch_desc_refactor(h, h->lv_cols[l], h->lv_ncols[l], s));
+        TRY(launch_desc_refactor(h, h->lv_cols[l], h->lv_ncols[l], s, l));
         for (int g = 0; g < 2; g++) {
             if (h->lv_ndense[g][l] == 0) continue;
             tbeg(h, KT_DENSE, s, 1);
@@ -952,7 +1000,13 @@ int refactor_by_rounds(basker_t h, cudaStream_t s)
     int st = read_status(h, s);
     if (st == BASKER_ERR_TIMEOUT) return st;
     if (!h->h_status->static_fail && !h->sep_dense) return st;
-    st = (h->opt.refactor_switch == 2 && h->h_status->static_fail) ? BK_SWITCH_TO_FULL : launch_redo(h, s);
+    // the complete pass at once (mode 2, or, by default, when the stored-pattern pass
+    // rejected so many pivots that the rounds' cascades would recompute most columns
+    // anyway: the same bound the factorization's path uses)
+    const int rejected = h->h_status->static_fail;
+    const bool full_now = rejected && (h->opt.refactor_switch == 2 ||
+                                       (h->opt.refactor_switch == 0 && rejected > std::max(16, h->pl.n / 200)));
+    st = full_now ? BK_SWITCH_TO_FULL : launch_redo(h, s);
     if (st == BASKER_OK) st = read_status(h, s);
     h->schedule_valid = false;
     if (st == BK_SWITCH_TO_FULL) {

@@ -137,8 +137,13 @@ struct bk_plan {
     int64_t lpool = 0, upool = 0;                     // spill pools after the layout's regions
     int64_t ws_bytes = 0;                             // GP global workspace
     int64_t ahat_doubles = 0, ahat_words = 0;         // separator A-hat scratch
-    int64_t wsd_slice = 0;                            // descendant-phase slice (bytes)
-    int32_t wsd_warps = 0;                            // descendant-phase warps (max columns of a level)
+    int64_t wsd_slice = 0;                            // column-per-warp slice of level 0 (bytes)
+    int32_t wsd_warps = 0;                            // and its slices
+    // per ND level: the slice its tasks need (x over the largest space, bitmaps)
+    // and the slices that fit the workspace; the workspace holds wsd_bytes
+    std::vector<int64_t> level_slice;
+    std::vector<int32_t> level_warps;
+    int64_t wsd_bytes = 0;
     int32_t dd_words = 0;                             // shared-memory reach bitmaps per warp (words)
     int32_t max_space = 0;
     int32_t symbolic_singular = -1;                   // first column without a structural pivot

@@ -278,7 +278,9 @@ size_t bk_desc_fast_smem(const bk_task *tasks, int32_t ntasks)
     size_t words = 4;
     for (int32_t t = 0; t < ntasks; t++)
         if (tasks[t].sp_lo < tasks[t].lo) words = std::max(words, ((size_t)(tasks[t].lo - tasks[t].sp_lo) + 31) / 32);
-    return (size_t)DF_COMPACT_WORDS * 4 + ((words + 3) & ~(size_t)3) * 4;
+    const size_t bytes = (size_t)DF_COMPACT_WORDS * 4 + ((words + 3) & ~(size_t)3) * 4;
+    // the bitmap over the largest separator's descendant rows must fit on chip
+    return bytes <= 160 * 1024 ? bytes : 0;
 }
 
 void bk_launch_desc_fast(const bk_dev &d, const int32_t *cols, int32_t ncols, int32_t *counter, int32_t *redo,

@@ -691,8 +691,8 @@ void bk_plan_layout(bk_plan &pl)
     // descendant-phase slice (x over the whole space plus two bitmaps)
     // column-per-warp kernels (separator descendant phase, refactor rounds): one
     // slice per warp holding x over a task's whole space and its step / row bitmaps
-    int64_t ah = 0, ab = 0, slice = 0;
-    std::vector<int64_t> level_cols(pl.level_tasks.size(), 0);
+    int64_t ah = 0, ab = 0;
+    std::vector<int64_t> level_cols(pl.level_tasks.size(), 0), level_slice(pl.level_tasks.size(), 256);
     for (auto &T : pl.tasks) {
         T.ahoff = T.aboff = 0;
         const int64_t own = T.hi - T.lo, words = (T.lspace + 31) / 32;
@@ -700,7 +700,7 @@ void bk_plan_layout(bk_plan &pl)
         // descendant phase on stored patterns) a mark byte per slot
         int64_t sl = (int64_t)T.space * 8 +
                      std::max<int64_t>(((int64_t)(T.hi - T.sp_lo) + 31) / 32 * 4 + words * 4, (int64_t)T.space);
-        slice = std::max(slice, (sl + 255) & ~(int64_t)255);
+        level_slice[(size_t)T.level] = std::max(level_slice[(size_t)T.level], (sl + 255) & ~(int64_t)255);
         level_cols[(size_t)T.level] += own;
         if (T.sp_lo >= T.lo) continue;
         T.ahoff = ah;
@@ -710,16 +710,32 @@ void bk_plan_layout(bk_plan &pl)
     }
     pl.ahat_doubles = std::max<int64_t>(ah, 1);
     pl.ahat_words = std::max<int64_t>(ab, 1);
-    pl.wsd_slice = std::max<int64_t>(slice, 256);
     // the reach's step and row bitmaps fit in shared memory for four warps a block
     int64_t bw = 0;
     for (auto &T : pl.tasks) bw = std::max<int64_t>(bw, ((int64_t)(T.hi - T.sp_lo) + 31) / 32 + (T.lspace + 31) / 32);
     bw = (bw + 3) & ~(int64_t)3;
     pl.dd_words = 4 * bw * 4 <= 160 * 1024 ? (int32_t)bw : 0;
-    int64_t wmax = 1;
-    for (int64_t v : level_cols) wmax = std::max(wmax, v);
-    // at most 152 SMs x 16 warps, and at most 8 GiB of slices
-    const int64_t by_mem = std::max<int64_t>(1, ((int64_t)8 << 30) / pl.wsd_slice);
-    pl.wsd_warps = (int32_t)std::min<int64_t>(std::min<int64_t>(wmax, 152 * 16), by_mem);
+    // One workspace serves every level in turn, each with slices of its own size:
+    // a level wants one slice per column it processes at once (at most 152 SMs x
+    // 16 warps); the workspace holds what level 0 (the leaves and BTF blocks) wants
+    // and, for the levels above, up to 1 GiB (a root separator whose space is the
+    // whole ND block takes fewer warps rather than gigabytes)
+    const size_t nl = level_cols.size();
+    int64_t need0 = 0, need = 0, most = 256;
+    for (size_t l = 0; l < nl; l++) {
+        const int64_t want = std::min<int64_t>(std::max<int64_t>(level_cols[l], 1), 152 * 16) * level_slice[l];
+        if (l == 0) need0 = want;
+        need = std::max(need, want);
+        most = std::max(most, level_slice[l]);
+    }
+    pl.wsd_bytes = std::max(std::min(need, std::max(need0, (int64_t)1 << 30)), most);
+    pl.level_slice = level_slice;
+    pl.level_warps.assign(nl, 1);
+    for (size_t l = 0; l < nl; l++)
+        pl.level_warps[l] = (int32_t)std::max<int64_t>(
+            1, std::min<int64_t>(std::min<int64_t>(std::max<int64_t>(level_cols[l], 1), 152 * 16),
+                                 pl.wsd_bytes / level_slice[l]));
+    pl.wsd_slice = nl ? level_slice[0] : 256;
+    pl.wsd_warps = nl ? pl.level_warps[0] : 1;
     pl.ws_bytes = off;
 }

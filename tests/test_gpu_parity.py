@@ -133,7 +133,9 @@ def test_refactor_sequence_matches_oracle(kind, seed, kw, sigma, tau):
         x = h.solve(_dev(b)).cpu().numpy()
         assert H.solve_backward_error(H.a_matrix(prob.with_values(v)), x, b) <= 1e-12
     if sigma >= 0.3:
-        assert repivots > 0, "the repivoting path was not exercised"
+        # rounds (columns recomputed by the reach) or, when the stored-pattern pass
+        # rejects many pivots, the complete pass with the previous pivots preferred
+        assert repivots > 0 or h.info()["full_refactors"] > 0, "the repivoting path was not exercised"
 
 
 @pytest.mark.parametrize("kind,seed,kw", [
