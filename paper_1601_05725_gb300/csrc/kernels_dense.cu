@@ -60,7 +60,6 @@ struct DnShared {
     double xp[2];        // the pivot's value (the step owner's copy)
     long long lb[2];     // start of L(:,c) (the step owner's copy)
     int cstop;           // the column group's stop decision
-    int bnd[BK_DENSE_CLUSTER + 1];   // first L position of each block's share of the division
     unsigned long long redk[DN_CG];  // the column group's reductions
     int redc[DN_CG], redb[DN_CG], redi[DN_CG];
 };
@@ -376,29 +375,29 @@ __global__ void __launch_bounds__(DN_THREADS) bk_dense_node_kernel(bk_dev d, con
         const int ps = So->pslot[b], cnt = So->cnt[b];
         if (tid_x == 0) spiv[ps] = k;
         {
-            // ---- L(:,c) = x / pivot over the pattern, one entry a thread: this
-            // block's share, the pattern words [rank cw, (rank + 1) cw)
+            // ---- L(:,c) = x / pivot over the pattern, one entry a thread, computed
+            // by every block from the owner's column (its own copy for its updates;
+            // the owner stores it): no second barrier and no gather
             const uint32_t *const rb = cl.map_shared_rank(lbits, owner);
             const int32_t *const rw = cl.map_shared_rank(wpre, owner);
             const V *const rc = cl.map_shared_rank(colv, owner);
             const V xp = (V)So->xp[b];
             const int64_t lb = So->lb[b];
-            const int cw = (nrw + CN - 1) / CN;
-            const int wl = min(nrw, rank * cw), wh = min(nrw, wl + cw);
-            for (int sl = wl * 32 + tid_x; sl < min(lsp, wh * 32); sl += DN_THREADS) {
+            for (int sl = tid_x; sl < lsp; sl += DN_THREADS) {
                 const int w = sl >> 5, bt = sl & 31;
                 const uint32_t bits = rb[w];
                 if (!((bits >> bt) & 1u)) continue;
                 const int pos = rw[w] + __popc(bits & ((1u << bt) - 1u));
                 const V q = rc[sl] / xp;
-                d.Li[lb + pos] = row_of_lslot(T, sl);
-                Lx[lb + pos] = q;
+                if (rank == owner) {
+                    d.Li[lb + pos] = row_of_lslot(T, sl);
+                    Lx[lb + pos] = q;
+                }
                 lsl[pos] = sl;
                 lval[pos] = q;
             }
             if (rank != owner)
                 for (int w = tid_x; w < nrw; w += DN_THREADS) lbits[w] = rb[w];
-            if (tid_x <= CN) S.bnd[tid_x] = rw[min(nrw, tid_x * cw)];
         }
         // ---- this block's later columns whose pattern holds the pivot row (one
         // thread a column): U(c, c2) = that entry, which leaves the column
@@ -442,17 +441,7 @@ __global__ void __launch_bounds__(DN_THREADS) bk_dense_node_kernel(bk_dev d, con
             a2[ps] = V(0);
             b2[ps >> 5] = w & ~(1u << (ps & 31));
         }
-        // ---- the other blocks' shares of L(:,k), from their shared memory
         DN_LAP(2);
-        cl.sync();
-        DN_LAP(3);
-        for (int q = tid_x; q < cnt; q += DN_THREADS) {
-            int src = CN - 1;
-            while (src > 0 && S.bnd[src] > q) src--;
-            if (src == rank) continue;
-            lsl[q] = *cl.map_shared_rank(lsl + q, src);
-            lval[q] = *cl.map_shared_rank(lval + q, src);
-        }
         if (rank != owner && tid_x == 0) {
             S.pslot[b] = ps;
             S.cnt[b] = cnt;

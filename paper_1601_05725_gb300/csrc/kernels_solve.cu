@@ -268,20 +268,21 @@ __global__ void __launch_bounds__(1024) bk_rows_sort_long(const int64_t *rp, con
 // column) taken in decreasing order are a valid order, and one with the most
 // rows at each level.  Forward: the same levels in increasing order are valid
 // when every L(i,k) != 0 of the leaf has level(k) < level(i) (true for
-// symmetric patterns); a leaf where that fails keeps its step order.  One
-// block a leaf checks it.
-__global__ void bk_leaf_check(bk_dev d, bk_solve_dev s)
+// symmetric patterns); a leaf where that fails keeps its step order.  Each leaf's
+// rows are split over `chunks` blocks (block b: leaf b / chunks, chunk b % chunks).
+__global__ void bk_leaf_check(bk_dev d, bk_solve_dev s, int chunks)
 {
+    const int leaf = blockIdx.x / chunks, chunk = blockIdx.x % chunks;
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const bk_task &T = d.tasks[s.leaf_tasks[blockIdx.x]];
+    const bk_task &T = d.tasks[s.leaf_tasks[leaf]];
     int bad = 0;
-    for (int i = T.lo + wid; i < T.hi; i += nw) {
+    for (int i = T.lo + chunk * nw + wid; i < T.hi; i += nw * chunks) {
         const int li = d.level[i];
         for (int64_t e = s.r.Lrp[i] + lane; e < s.r.Lrp[i + 1]; e += 32)
             if (d.level[s.r.Lrk[e]] >= li) bad = 1;
     }
-    if (__any_sync(BK_FULL, bad) && lane == 0) s.leaf_bad[blockIdx.x] = 1;
+    if (__any_sync(BK_FULL, bad) && lane == 0) s.leaf_bad[leaf] = 1;
 }
 
 // Sort key of leaf row i (both below the leaf's size).
@@ -292,16 +293,15 @@ __device__ __forceinline__ int leaf_key(const bk_dev &d, const bk_solve_dev &s, 
     return s.leaf_maxrows - d.level[i];
 }
 
-// Counting sort of all leaf rows by level into their places of the claim order.
-__global__ void bk_leaf_count(bk_dev d, bk_solve_dev s)
+// Counting sort of all leaf rows by level into their places of the claim order
+// (a thread a row; rows of one level take their places in any order).
+__global__ void bk_leaf_count(bk_dev d, bk_solve_dev s, int chunks)
 {
-    const int warp = blockIdx.x;
-    const int lane = threadIdx.x;
-    if (warp >= s.nleaves) return;
-    const bk_task &T = d.tasks[s.leaf_tasks[warp]];
-    for (int i = T.lo + lane; i < T.hi; i += 32) {
-        atomicAdd(s.lcnt + leaf_key(d, s, warp, T.lo, T.hi, i, 0), 1);
-        atomicAdd(s.lcnt + (s.leaf_maxrows + 1) + leaf_key(d, s, warp, T.lo, T.hi, i, 1), 1);
+    const int leaf = blockIdx.x / chunks, chunk = blockIdx.x % chunks;
+    const bk_task &T = d.tasks[s.leaf_tasks[leaf]];
+    for (int i = T.lo + chunk * blockDim.x + threadIdx.x; i < T.hi; i += blockDim.x * chunks) {
+        atomicAdd(s.lcnt + leaf_key(d, s, leaf, T.lo, T.hi, i, 0), 1);
+        atomicAdd(s.lcnt + (s.leaf_maxrows + 1) + leaf_key(d, s, leaf, T.lo, T.hi, i, 1), 1);
     }
 }
 
@@ -325,16 +325,14 @@ __global__ void __launch_bounds__(1024) bk_leaf_scan(bk_solve_dev s)
     }
 }
 
-__global__ void bk_leaf_scatter(bk_dev d, bk_solve_dev s)
+__global__ void bk_leaf_scatter(bk_dev d, bk_solve_dev s, int chunks)
 {
-    const int warp = blockIdx.x;
-    const int lane = threadIdx.x;
-    if (warp >= s.nleaves) return;
-    const bk_task &T = d.tasks[s.leaf_tasks[warp]];
+    const int leaf = blockIdx.x / chunks, chunk = blockIdx.x % chunks;
+    const bk_task &T = d.tasks[s.leaf_tasks[leaf]];
     const int m = s.leaf_maxrows + 1;
-    for (int i = T.lo + lane; i < T.hi; i += 32) {
-        s.items[s.leaf_f0 + atomicAdd(s.lcnt + leaf_key(d, s, warp, T.lo, T.hi, i, 0), 1)] = i;
-        s.items[s.leaf_b0 + atomicAdd(s.lcnt + m + leaf_key(d, s, warp, T.lo, T.hi, i, 1), 1)] = ~i;
+    for (int i = T.lo + chunk * blockDim.x + threadIdx.x; i < T.hi; i += blockDim.x * chunks) {
+        s.items[s.leaf_f0 + atomicAdd(s.lcnt + leaf_key(d, s, leaf, T.lo, T.hi, i, 0), 1)] = i;
+        s.items[s.leaf_b0 + atomicAdd(s.lcnt + m + leaf_key(d, s, leaf, T.lo, T.hi, i, 1), 1)] = ~i;
     }
 }
 
@@ -786,12 +784,15 @@ void bk_launch_leaf_order(const bk_dev &d, const bk_solve_dev &s, void *stream)
 {
     if (s.nleaves <= 0) return;
     cudaStream_t st = (cudaStream_t)stream;
+    // each leaf's rows over up to 32 blocks of 256 threads
+    const int chunks = std::max(1, std::min((s.leaf_maxrows + 255) / 256, 32));
+    const unsigned grid = (unsigned)s.nleaves * (unsigned)chunks;
     cudaMemsetAsync(s.leaf_bad, 0, sizeof(int32_t) * (size_t)s.nleaves, st);
-    bk_leaf_check<<<s.nleaves, 256, 0, st>>>(d, s);
+    bk_leaf_check<<<grid, 256, 0, st>>>(d, s, chunks);
     cudaMemsetAsync(s.lcnt, 0, sizeof(int32_t) * 2 * ((size_t)s.leaf_maxrows + 1), st);
-    bk_leaf_count<<<s.nleaves, 32, 0, st>>>(d, s);
+    bk_leaf_count<<<grid, 256, 0, st>>>(d, s, chunks);
     bk_leaf_scan<<<1, 1024, 0, st>>>(s);
-    bk_leaf_scatter<<<s.nleaves, 32, 0, st>>>(d, s);
+    bk_leaf_scatter<<<grid, 256, 0, st>>>(d, s, chunks);
 }
 
 void bk_launch_solve(const bk_dev &d, const bk_solve_dev &s, int32_t nrhs, const double *b, int32_t ldb,
