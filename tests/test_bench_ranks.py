@@ -99,3 +99,37 @@ def test_block_parallel_oracle_partition_matches_the_whole():
         np.testing.assert_array_equal(xs, xw[prob.Q[cols]])
     t = bench._par_worker((sub, sv, sb, 0, 2))
     assert len(t) == 2 and min(t) > 0
+
+
+def test_chain_depths_equal_brute_force_longest_paths():
+    """The latency floor's link counts: the longest dependency chains of the
+    oracle's factors, against a longest-path search written out over the DAGs
+    (forward rows: L(i,k) != 0 puts row k before row i; columns: U(i,k) != 0 puts
+    step i before column k)."""
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import bench
+    import oracle
+    from paper_1601_05725_gb300 import inputs as I
+    prob = I.grid_problem(4, k=14, depth=2)
+    o = oracle.OracleLU(prob)
+    assert o.factor() == "OK"
+    f = o.factors()
+    dep = bench._chain_depths(prob, f.L, f.U)
+    n = prob.n
+    L, U = f.L.tocoo(), f.U.tocoo()
+
+    def longest(edges):
+        preds = [[] for _ in range(n)]
+        for a, b in edges:
+            preds[b].append(a)
+        depth = [0] * n
+        for v in range(n):                 # steps are a topological order
+            depth[v] = 1 + max((depth[u] for u in preds[v]), default=0)
+        return max(depth)
+    assert dep["forward_rows"] == longest([(k, i) for i, k in zip(L.row, L.col)])
+    assert dep["columns"] == longest([(i, k) for i, k in zip(U.row, U.col) if i != k])
+    heights = bench._nd_tree(prob)
+    assert list(heights) == [0, 0, 1, 0, 0, 1, 2]
+    ptr = np.asarray(prob.nd_node_ptr)
+    assert dep["separator_steps"] == int(ptr[3] - ptr[2] if ptr[3] - ptr[2] > ptr[6] - ptr[5] else ptr[6] - ptr[5]) + int(ptr[7] - ptr[6])
