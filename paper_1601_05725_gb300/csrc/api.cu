@@ -231,7 +231,9 @@ int alloc_factors(basker_t h)
     h->d.lpool_end = pl.lcap + pl.lpool;
     h->d.upool_end = pl.ucap + pl.upool;
     h->arena_ver++;                   // captured launches hold the old arrays
-    TRY(dalloc(h, &h->d.Li, (size_t)h->d.lpool_end));
+    // L's arrays carry 16 bytes of slack: the rounds copy columns in 16-byte
+    // pieces from the boundary below a column to the one above its end
+    TRY(dalloc(h, &h->d.Li, (size_t)h->d.lpool_end + 4));
     // the factors by rows (for the solve) have the same capacities
     bk_rows &r = h->sd.r;
     dfree(h, r.Lrk); dfree(h, r.Lrx); dfree(h, r.Urk); dfree(h, r.Urx); dfree(h, r.tk); dfree(h, r.tx);
@@ -245,7 +247,7 @@ int alloc_factors(basker_t h)
     TRY(dalloc(h, &r.tk, (size_t)std::max(h->d.lpool_end, h->d.upool_end)));
     TRY(dalloc(h, &r.Ls, (size_t)h->d.lpool_end));
     TRY(dalloc(h, &r.tx, (size_t)std::max(h->d.lpool_end, h->d.upool_end)));
-    TRY(dalloc(h, &h->d.Lx, (size_t)h->d.lpool_end));
+    TRY(dalloc(h, &h->d.Lx, (size_t)h->d.lpool_end + 4));
     TRY(dalloc(h, &h->d.Ui, (size_t)h->d.upool_end));
     TRY(dalloc(h, &h->d.Ux, (size_t)h->d.upool_end));
     TRY(upload(h, &h->d.Lbeg, pl.sLbeg));
@@ -678,6 +680,36 @@ int stage_upload(basker_t h, cudaStream_t s, int32_t *dst, const std::vector<int
     return BASKER_OK;
 }
 
+// The columns of a round in claim order: each active task's columns from its
+// start column on, ascending within the task (a column's steps in its own task
+// come before it, so every wait is on a column already claimed), the tasks
+// interleaved in proportion to their lengths, so that every task advances
+// through its columns at the same rate.  Claimed in task order instead, the
+// columns near the top of the first tasks' elimination trees hold the warps
+// while they wait for their chains, and the later tasks start late.  Column i of
+// a task of L columns goes to position floor((2i + 1) N / 2L) of N buckets (N
+// columns in all), which grows with i: a counting sort over the buckets keeps
+// each task's order.
+void round_columns(const bk_plan &pl, const std::vector<int32_t> &active, const std::vector<int32_t> &start,
+                   std::vector<int32_t> &cols)
+{
+    int64_t N = 0;
+    for (int32_t t : active) N += pl.tasks[(size_t)t].hi - start[(size_t)t];
+    cols.assign((size_t)N, 0);
+    if (N == 0) return;
+    std::vector<int32_t> at((size_t)N + 1, 0);
+    auto bucket = [N](int64_t i, int64_t L) { return (size_t)(((2 * i + 1) * N) / (2 * L)); };
+    for (int32_t t : active) {
+        const int64_t L = pl.tasks[(size_t)t].hi - start[(size_t)t];
+        for (int64_t i = 0; i < L; i++) at[bucket(i, L) + 1]++;
+    }
+    for (size_t b = 0; b < (size_t)N; b++) at[b + 1] += at[b];
+    for (int32_t t : active) {
+        const int64_t L = pl.tasks[(size_t)t].hi - start[(size_t)t];
+        for (int64_t i = 0; i < L; i++) cols[(size_t)at[bucket(i, L)]++] = start[(size_t)t] + (int32_t)i;
+    }
+}
+
 // After a stored-pattern pass that rejected some preferred pivots (first
 // rejection per task in h_task_fail): level by level up the ND tree, rounds of the
 // dirty-dataflow kernel.  A task with a rejected column f starts a round at f
@@ -766,8 +798,7 @@ int launch_redo(basker_t h, cudaStream_t s)
         for (int round = 0; !active.empty(); round++) {
             if (round > 4 * (int)pl.n + 8) return BASKER_ERR_INVALID_ARG;   // cannot happen: each round resolves a column
             std::vector<int32_t> cols;
-            for (int32_t t : active)
-                for (int32_t c = start[(size_t)t]; c < pl.tasks[(size_t)t].hi; c++) cols.push_back(c);
+            round_columns(pl, active, start, cols);
             // a large round that would, at the cost per column of the large rounds
             // seen so far, take the rounds past a complete pass: the complete pass now
             // instead (small rounds are dominated by their fixed costs: not predicted)

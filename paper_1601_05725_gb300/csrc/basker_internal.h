@@ -162,6 +162,11 @@ void bk_plan_regrow(bk_plan &plan, const int32_t *over); // after an overflow (p
 size_t bk_task_smem_bytes(const bk_task &t);
 // kernels_dense.cu: the in-node phase of a separator as one dense elimination
 #define BK_DENSE_SMEM (200 * 1024)
+// refactorization rounds: a waited-for step's L column staged in shared memory,
+// up to BK_DD_SCAP entries (rows, values with 16 entries of slack for the
+// 16-byte boundaries, and what each row adds), per warp
+#define BK_DD_SCAP 512
+#define BK_DD_STAGE_BYTES ((BK_DD_SCAP + 16) * 12 + BK_DD_SCAP * 4)
 size_t bk_dense_node_smem(const bk_task &t);
 bool bk_dense_node_eligible(const bk_task &t);
 // separators of at least BK_DENSE_CLUSTER_MIN columns run on a cluster of

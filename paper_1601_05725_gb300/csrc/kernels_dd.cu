@@ -34,6 +34,15 @@
 
 using namespace bk;
 
+// Per-column phase clocks of the reach path, kept only in trace builds: the
+// cycles from the last wait to the end of the step loop, of the pivot selection,
+// of the L write and of the epilogue, and the cycles spent waiting.
+#ifdef BK_TRACE
+#define DD_CLK(v) v = clock64()
+#else
+#define DD_CLK(v)
+#endif
+
 namespace {
 
 __device__ __forceinline__ void set_bit(volatile uint32_t *bm, int i)
@@ -76,24 +85,40 @@ __device__ __forceinline__ bool lane_wait(const bk_dev &d, const int *flag, int 
 // Row slots of the pattern, listed in ascending order: one segment of set bits
 // of rb starting at word wcur (advanced past the words listed).  A segment holds
 // whole groups of 32 words, at most RLIST slots; 32 words hold at most RLIST.
+// A lane lists the bits of its own word when they are few; words with more than
+// LIST_DENSE bits (the runs of consecutive rows a separator brings) are listed by
+// the whole warp, one word at a time, one bit a lane.  Either way a slot's
+// position is its word's offset plus its rank in the word.
 constexpr int RLIST = 1024;
 constexpr int RL_PF = 8;
+constexpr int LIST_DENSE = 8;
 
 __device__ __forceinline__ int build_list(const volatile uint32_t *rb, int nrw, int &wcur, int *list, int lane)
 {
     int filled = 0;
+    const uint32_t below = (1u << lane) - 1u;
     while (wcur < nrw) {
         const int w = wcur + lane;
-        uint32_t bits = w < nrw ? rb[w] : 0u;
+        const uint32_t bits = w < nrw ? rb[w] : 0u;
         const int cnt = __popc(bits);
         const int pre = warp_exscan(cnt, lane);
         const int tot = __shfl_sync(BK_FULL, pre + cnt, 31);
         if (filled + tot > RLIST) break;
-        int q = filled + pre;
-        while (bits) {
-            const int b = __ffs(bits) - 1;
-            bits &= bits - 1;
+        const int q0 = filled + pre;
+        uint32_t mine = cnt > LIST_DENSE ? 0u : bits;
+        int q = q0;
+        while (mine) {
+            const int b = __ffs(mine) - 1;
+            mine &= mine - 1;
             list[q++] = (w << 5) + b;
+        }
+        uint32_t dense = __ballot_sync(BK_FULL, cnt > LIST_DENSE);
+        while (dense) {
+            const int src = __ffs(dense) - 1;
+            dense &= dense - 1;
+            const uint32_t bw = __shfl_sync(BK_FULL, bits, src);
+            const int qb = __shfl_sync(BK_FULL, q0, src);
+            if ((bw >> lane) & 1u) list[qb + __popc(bw & below)] = ((wcur + src) << 5) + lane;
         }
         filled += tot;
         wcur += 32;
@@ -128,11 +153,25 @@ __device__ __forceinline__ void read_step(const bk_dev &d, const bk_task &T, RSt
         dn = lane == 0 ? (ld_acquire(d.done + j) == epoch) : 0;
         dn = __shfl_sync(BK_FULL, dn, 0);
     }
+    // after the wait, L(:,j)'s entries are read where the extent read before the
+    // wait put them, together with the extent itself (one round trip instead of
+    // two); entries the final extent places elsewhere are read again
+    int rg[RSTEP_PF];
+    V lg[RSTEP_PF];
+    const int64_t jl_g = st.jl;
+    const int jc_g = after_wait ? st.jc : 0;
+#pragma unroll
+    for (int u = 0; u < RSTEP_PF; u++) {
+        const int q = lane + 32 * u;
+        rg[u] = q < jc_g ? __ldcg(d.Li + jl_g + q) : -1;
+        lg[u] = q < jc_g ? __ldcg(vals<V>(d.Lx) + jl_g + q) : V(0);
+    }
     st.sp = slot_of(T, base, __ldcg(d.prow + j));
     st.jl = __ldcg(d.Lbeg + j);
     st.jc = __ldcg(d.Lcnt + j);
     st.full = dn != 0;
     st.why = 0;
+    const bool moved = st.jl != jl_g;
 #pragma unroll
     for (int u = 0; u < RSTEP_PF; u++) {
         const int q = lane + 32 * u;
@@ -140,8 +179,9 @@ __device__ __forceinline__ void read_step(const bk_dev &d, const bk_task &T, RSt
         st.bit[u] = -1;
         st.l[u] = 0.0;
         if (!dn || q >= st.jc) continue;
-        const int r = __ldcg(d.Li + st.jl + q);
-        st.l[u] = __ldcg(vals<V>(d.Lx) + st.jl + q);
+        const bool have = !moved && q < jc_g;
+        const int r = have ? rg[u] : __ldcg(d.Li + st.jl + q);
+        st.l[u] = have ? lg[u] : __ldcg(vals<V>(d.Lx) + st.jl + q);
         const int s = slot_of(T, base, r);
         if (s < 0) { st.why = 65; continue; }
         st.s[u] = s;
@@ -157,6 +197,101 @@ __device__ __forceinline__ void read_step(const bk_dev &d, const bk_task &T, RSt
     }
 }
 
+// A step waited for: L(:,j) copied into the warp's staging area in shared
+// memory (16-byte copies at L2 only, from the 16-byte boundary below the column;
+// the arrays carry 16 bytes of padding), started where the extent read before
+// the wait puts it while the extent itself is read again; then the rows' slots
+// and, for rows of the node, the steps that pivot them, RS_PF loads a lane in
+// flight.  Each entry leaves its slot in srow and what it adds in sadd (a step
+// bit >= 0, a row bit encoded -2 - bit, or -1).  Returns the number of entries,
+// or -1 when L(:,j) has more than BK_DD_SCAP entries (read the usual way).
+constexpr int RS_PF = 8;
+
+__device__ __forceinline__ void dd_cp16(void *dst, const void *src)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(src) : "memory");
+}
+__device__ __forceinline__ void dd_cp_wait()
+{
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
+template <typename T>
+__device__ __forceinline__ int stage_range(T *dst, const T *src, int64_t e0, int cnt, int lane)
+{
+    constexpr int per = 16 / (int)sizeof(T);
+    const int64_t a0 = e0 & ~(int64_t)(per - 1);
+    const int off = (int)(e0 - a0);
+    const int chunks = (off + cnt + per - 1) / per;
+    for (int k = lane; k < chunks; k += 32) dd_cp16(dst + k * per, src + a0 + (int64_t)k * per);
+    return off;
+}
+
+template <typename V>
+__device__ __forceinline__ int stage_step(const bk_dev &d, const bk_task &T, RStep<V> &st, int j, int c, int lane,
+                                          int ndesc, int *srow, V *sval, int *sadd, int &ro, int &vo, int &why)
+{
+    const int base = T.sp_lo;
+    const V *const Lx = vals<V>(d.Lx);
+    if (st.jc > BK_DD_SCAP) return -1;
+    // the extent read before the wait is a guess (its two words may come from
+    // either side of a move of the column): copied only inside the arrays
+    const bool guess = st.jl >= 0 && st.jc >= 0 && st.jl + st.jc <= d.lpool_end;
+    if (guess) {
+        ro = stage_range(srow, d.Li, st.jl, st.jc, lane);
+        vo = stage_range(sval, Lx, st.jl, st.jc, lane);
+    }
+    const int pr = __ldcg(d.prow + j);
+    const int64_t jl = __ldcg(d.Lbeg + j);
+    const int jc = __ldcg(d.Lcnt + j);
+    dd_cp_wait();
+    if (!guess || jl != st.jl || jc > st.jc) {
+        st.jl = jl;
+        st.jc = jc;
+        if (jc > BK_DD_SCAP || jl < 0 || jl + jc > d.lpool_end) return -1;
+        __syncwarp();
+        ro = stage_range(srow, d.Li, jl, jc, lane);
+        vo = stage_range(sval, Lx, jl, jc, lane);
+        dd_cp_wait();
+    }
+    st.jl = jl;
+    st.jc = jc;
+    st.sp = slot_of(T, base, pr);
+    __syncwarp();
+    for (int q0 = 0; q0 < jc; q0 += 32 * RS_PF) {
+        int rr[RS_PF], sl[RS_PF], pp[RS_PF];
+#pragma unroll
+        for (int u = 0; u < RS_PF; u++) {
+            const int q = q0 + lane + 32 * u;
+            rr[u] = q < jc ? srow[ro + q] : -1;
+            sl[u] = rr[u] >= 0 ? slot_of(T, base, rr[u]) : -1;
+            pp[u] = (sl[u] >= 0 && sl[u] < T.hi - base) ? __ldcg(d.pinv + rr[u]) : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < RS_PF; u++) {
+            const int q = q0 + lane + 32 * u;
+            if (q >= jc) continue;
+            int add = -1;
+            if (sl[u] < 0) {
+                if (!why) why = 65;
+            } else if (pp[u] >= 0 && pp[u] < c) {
+                if (pp[u] > j) add = pp[u] - base;
+                else if (!why) why = 66;
+            } else if (sl[u] >= ndesc) {
+                add = -2 - (sl[u] - ndesc);
+            } else if (!why) {
+                why = 67;
+            }
+            srow[ro + q] = sl[u];
+            sadd[q] = add;
+        }
+    }
+    __syncwarp();
+    return jc;
+}
+
 template <typename V>
 __global__ void __launch_bounds__(128) bk_dd_kernel(bk_dev d, const int32_t *__restrict__ cols, int32_t ncols,
                                                     int32_t *counter, double tau, int32_t epoch, long long budget,
@@ -167,7 +302,7 @@ __global__ void __launch_bounds__(128) bk_dd_kernel(bk_dev d, const int32_t *__r
     V *const Ux = vals<V>(d.Ux);
     __shared__ bk_task Ts[4];
     __shared__ int rlist[4 * RLIST];
-    extern __shared__ uint32_t dd_bits[];
+    extern __shared__ __align__(16) uint32_t dd_bits[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int gw = blockIdx.x * 4 + wib;
@@ -177,6 +312,12 @@ __global__ void __launch_bounds__(128) bk_dd_kernel(bk_dev d, const int32_t *__r
     // the reach's bitmaps, when they fit in shared memory; zero between columns
     uint32_t *wbits = dd_bits + (int64_t)wib * d.dd_words;
     for (int i = lane; i < d.dd_words; i += 32) wbits[i] = 0u;
+    // the staging area of a waited-for step (rows, values, what each row adds)
+    unsigned char *const stg = reinterpret_cast<unsigned char *>(dd_bits + 4 * (int64_t)d.dd_words) +
+                               (int64_t)wib * BK_DD_STAGE_BYTES;
+    int *const srow = reinterpret_cast<int *>(stg);
+    V *const sval = reinterpret_cast<V *>(stg + (BK_DD_SCAP + 16) * 4);
+    int *const sadd = reinterpret_cast<int *>(stg + (BK_DD_SCAP + 16) * 12);
     __syncwarp();
     int cur_task = -1;
     for (;;) {
@@ -336,12 +477,18 @@ __global__ void __launch_bounds__(128) bk_dd_kernel(bk_dev d, const int32_t *__r
         // current one is predicted (the lowest set bit once the current one is
         // cleared) and its data read while the current step is applied; a step
         // that the current one adds below the prediction is read when it is found.
+#ifdef BK_TRACE
+        long long ck_wait = 0, ck_last = 0, ck_a = 0, ck_b = 0, ck_c = 0, ck_stg = 0, ck_app = 0;
+        int steps_after = 0;
+#endif
+        DD_CLK(ck_last);
         int w0 = 0;
         int jb = next_step_bit(sb, nsw, w0, lane);
         RStep<V> cur, nxt;
         if (jb >= 0) read_step(d, T, cur, base + jb, c, s0, epoch, lane, ndesc);
         for (int iter = 0; jb >= 0; iter++) {
             const int j = base + jb;
+            int nstaged = -1, so_r = 0, so_v = 0;
             if (iter > nsteps || j >= c) { if (!why) why = 63; break; }
             if (lane == 0) atomicAnd(const_cast<uint32_t *>(sb) + (jb >> 5), ~(1u << (jb & 31)));
             __syncwarp();
@@ -349,9 +496,29 @@ __global__ void __launch_bounds__(128) bk_dd_kernel(bk_dev d, const int32_t *__r
             const int jbp = next_step_bit(sb, nsw, wp, lane);
             if (jbp >= 0 && base + jbp < c) read_step(d, T, nxt, base + jbp, c, s0, epoch, lane, ndesc);
             if (!cur.full) {
+#ifdef BK_TRACE
+                const long long cw0 = clock64();
+#endif
                 int ok = lane == 0 ? (int)lane_wait(d, d.done + j, epoch, budget) : 1;
                 if (!__shfl_sync(BK_FULL, ok, 0)) return;
-                read_step(d, T, cur, j, c, s0, epoch, lane, ndesc, true);
+                DD_CLK(ck_last);
+#ifdef BK_TRACE
+                ck_wait += ck_last - cw0;
+#endif
+                nstaged = stage_step(d, T, cur, j, c, lane, ndesc, srow, sval, sadd, so_r, so_v, why);
+#ifdef BK_TRACE
+                ck_stg = clock64() - ck_last;
+                steps_after = 0;
+#endif
+                if (nstaged < 0) {
+                    read_step(d, T, cur, j, c, s0, epoch, lane, ndesc, true);
+                } else {
+                    cur.full = true;
+                    cur.why = 0;
+                    cur.jc = 0;          // the entries are applied from the staging area
+#pragma unroll
+                    for (int u = 0; u < RSTEP_PF; u++) cur.s[u] = -1;
+                }
             }
             const int sp = cur.sp;
             if (sp < 0) { if (!why) why = 64; break; }
@@ -396,22 +563,68 @@ __global__ void __launch_bounds__(128) bk_dd_kernel(bk_dev d, const int32_t *__r
                 else if (cur.bit[u] <= -2) set_bit(rb, -2 - cur.bit[u]);
             }
             if (cur.why && !why) why = cur.why;
-            for (int q = 32 * RSTEP_PF + lane; q < cur.jc; q += 32) {
-                const int r = __ldcg(d.Li + cur.jl + q);
-                const V l = __ldcg(Lx + cur.jl + q);
-                const int s1 = slot_of(T, base, r);
-                if (s1 < 0) { if (!why) why = 65; continue; }
-                x[s1] = fma(-l, m, x[s1]);
-                const int p = s1 < T.hi - base ? __ldcg(d.pinv + r) : -1;
-                if (p >= 0 && p < c) {
-                    if (p > j) set_bit(sb, p - base);
-                    else if (!why) why = 66;
-                } else if (s1 >= ndesc) {
-                    set_bit(rb, s1 - ndesc);
-                } else if (!why) {
-                    why = 67;
+            // entries past the read-ahead window, RSTEP_PF a lane at a time: their
+            // rows, values, x and pinv loads issued together (the rows of L(:,j)
+            // are distinct, so the batch's updates do not alias)
+            for (int q0 = 32 * RSTEP_PF; q0 < cur.jc; q0 += 32 * RSTEP_PF) {
+                int rq[RSTEP_PF], sq[RSTEP_PF], pq[RSTEP_PF];
+                V lq[RSTEP_PF], xq[RSTEP_PF];
+#pragma unroll
+                for (int u = 0; u < RSTEP_PF; u++) {
+                    const int q = q0 + lane + 32 * u;
+                    rq[u] = q < cur.jc ? __ldcg(d.Li + cur.jl + q) : -1;
+                    lq[u] = q < cur.jc ? __ldcg(Lx + cur.jl + q) : V(0);
+                }
+#pragma unroll
+                for (int u = 0; u < RSTEP_PF; u++) {
+                    sq[u] = rq[u] >= 0 ? slot_of(T, base, rq[u]) : -1;
+                    if (rq[u] >= 0 && sq[u] < 0 && !why) why = 65;
+                    pq[u] = (sq[u] >= 0 && sq[u] < T.hi - base) ? __ldcg(d.pinv + rq[u]) : -1;
+                    xq[u] = sq[u] >= 0 ? x[sq[u]] : V(0);
+                }
+#pragma unroll
+                for (int u = 0; u < RSTEP_PF; u++) {
+                    if (sq[u] < 0) continue;
+                    x[sq[u]] = fma(-lq[u], m, xq[u]);
+                    const int p = pq[u];
+                    if (p >= 0 && p < c) {
+                        if (p > j) set_bit(sb, p - base);
+                        else if (!why) why = 66;
+                    } else if (sq[u] >= ndesc) {
+                        set_bit(rb, sq[u] - ndesc);
+                    } else if (!why) {
+                        why = 67;
+                    }
                 }
             }
+            // the staged entries
+#ifdef BK_TRACE
+            const long long ck_ap0 = clock64();
+            steps_after++;
+#endif
+            for (int q0 = 0; q0 < nstaged; q0 += 32 * RSTEP_PF) {
+                int sq[RSTEP_PF], aq[RSTEP_PF];
+                V lq[RSTEP_PF], xq[RSTEP_PF];
+#pragma unroll
+                for (int u = 0; u < RSTEP_PF; u++) {
+                    const int q = q0 + lane + 32 * u;
+                    sq[u] = q < nstaged ? srow[so_r + q] : -1;
+                    lq[u] = q < nstaged ? sval[so_v + q] : V(0);
+                    aq[u] = q < nstaged ? sadd[q] : -1;
+                }
+#pragma unroll
+                for (int u = 0; u < RSTEP_PF; u++) xq[u] = sq[u] >= 0 ? x[sq[u]] : V(0);
+#pragma unroll
+                for (int u = 0; u < RSTEP_PF; u++) {
+                    if (sq[u] < 0) continue;
+                    x[sq[u]] = fma(-lq[u], m, xq[u]);
+                    if (aq[u] >= 0) set_bit(sb, aq[u]);
+                    else if (aq[u] <= -2) set_bit(rb, -2 - aq[u]);
+                }
+            }
+#ifdef BK_TRACE
+            if (nstaged >= 0) ck_app = clock64() - ck_ap0;
+#endif
             if (lane == 0 && oldu != j) same = false;
             nu++;
             __syncwarp();
@@ -422,89 +635,20 @@ __global__ void __launch_bounds__(128) bk_dd_kernel(bk_dev d, const int32_t *__r
             }
         }
         why = warp_max_i(why);
+        DD_CLK(ck_a);
         // Algorithm 1's pivot selection among the node's unpivoted rows.  The
         // pattern's row slots are listed in ascending order, a segment of at most
         // RLIST at a time, and their values read eight per lane at once.
         int *list = rlist + wib * RLIST;
         unsigned long long km = 0;          // largest own magnitude, as a key
-        int ncand = 0, nrows = 0;
-        for (int wcur = 0; wcur < nrw;) {
-            const int filled = build_list(rb, nrw, wcur, list, lane);
-            nrows += filled;
-            for (int i0 = 0; i0 < filled; i0 += 32 * RL_PF) {
-                int ls[RL_PF];
-                V v[RL_PF];
-#pragma unroll
-                for (int u = 0; u < RL_PF; u++) {
-                    const int i = i0 + lane + 32 * u;
-                    ls[u] = i < filled ? list[i] : -1;
-                    v[u] = ls[u] >= 0 ? x[ndesc + ls[u]] : 0.0;
-                }
-#pragma unroll
-                for (int u = 0; u < RL_PF; u++) {
-                    if (ls[u] < 0) continue;
-                    if (!isfinite(v[u])) bad = true;
-                    if (ls[u] < nown) {
-                        ncand++;
-                        km = key_max(km, mag_key(v[u]));
-                    }
-                }
-            }
-            __syncwarp();
-        }
-        km = warp_max_key(km);
-        const V amax = key_value<V>(km);
-        ncand = warp_sum(ncand);
-        bad = __any_sync(BK_FULL, bad);
+        int ncand = 0, nrows = 0, nseg = 0;
         const int pcur = __ldcg(d.prow + c);
-        const int pref = resolve ? d.pref[c] : pcur;
         auto in_pattern = [&](int r) -> bool {
             const int ls = r - T.lo;
             return (unsigned)ls < (unsigned)nown && ((rb[ls >> 5] >> (ls & 31)) & 1u);
         };
-        int piv = -1;
-        bool ok = false;
-        if (!bad && ncand > 0 && amax > 0.0) {
-            if (in_pattern(pref) && (double)fabs(x[ndesc + pref - T.lo]) >= tau * (double)amax) {
-                piv = pref;
-                ok = true;
-            } else if (resolve) {
-                // the lowest own row reaching the maximum
-                int best = INT_MAX;
-                const int nw_own = (nown + 31) >> 5;
-                for (int wcur = 0; wcur < nw_own && best == INT_MAX;) {
-                    const int filled = build_list(rb, nw_own, wcur, list, lane);
-                    for (int i0 = 0; i0 < filled; i0 += 32 * RL_PF) {
-                        int ls[RL_PF];
-                        V v[RL_PF];
-#pragma unroll
-                        for (int u = 0; u < RL_PF; u++) {
-                            const int i = i0 + lane + 32 * u;
-                            ls[u] = i < filled ? list[i] : -1;
-                            v[u] = ls[u] >= 0 ? x[ndesc + ls[u]] : 0.0;
-                        }
-#pragma unroll
-                        for (int u = 0; u < RL_PF; u++)
-                            if (ls[u] >= 0 && ls[u] < nown && mag_key(v[u]) == km) best = min(best, ls[u]);
-                    }
-                    best = warp_min(best);
-                    __syncwarp();
-                }
-                piv = T.lo + best;
-                ok = true;
-            }
-        }
-        if (resolve && piv < 0) {
-            // no acceptable pivot at an exact column: the matrix is singular here
-            if (lane == 0) report_fail(d.status, c, bad ? BK_CODE_NAN : BK_CODE_SINGULAR);
-        }
-        if (piv < 0) piv = pcur;                     // keep the speculation consistent
-        const int pls = piv - T.lo;
-        const bool pin = in_pattern(piv);
-        const V xp = pin ? x[ndesc + pls] : 0.0;
-        // L(:,c) = x / pivot over the pattern's unpivoted rows; clear the state
-        {
-            const int cnt_all = nrows - (pin ? 1 : 0);
+        // L(:,c) goes to its region, or to a larger one from the pool
+        auto place_l = [&](int cnt_all) {
             if (!overflow && lb + cnt_all > le) {
                 const int64_t cap = max((long long)cnt_all,
                                         min((long long)(2 * (int64_t)cnt_all + 16),
@@ -524,27 +668,48 @@ __global__ void __launch_bounds__(128) bk_dd_kernel(bk_dev d, const int32_t *__r
                 }
             }
             if (lb + cnt_all > le) overflow = true;
-        }
-        int64_t lpos = lb;
-        int rank0 = 0;
-        for (int wcur = 0; wcur < nrw;) {
-            const int filled = build_list(rb, nrw, wcur, list, lane);
-            for (int i0 = 0; i0 < filled; i0 += 32 * RL_PF) {
+        };
+        int wfirst = 0;
+        const int filled0 = build_list(rb, nrw, wfirst, list, lane);
+        int piv = -1;
+        bool ok = false;
+        int pls = 0;
+        bool pin = false;
+        V xp = V(0);
+        if (!resolve && wfirst >= nrw) {
+            // every column but the round's resolve column keeps its pivot row, so
+            // with the pattern listed in one segment the selection's check and the
+            // L write share one pass over the values
+            nrows = filled0;
+            piv = pcur;
+            pls = piv - T.lo;
+            pin = in_pattern(piv);
+            xp = pin ? x[ndesc + pls] : V(0);
+            DD_CLK(ck_b);
+            place_l(nrows - (pin ? 1 : 0));
+            for (int i0 = 0; i0 < nrows; i0 += 32 * RL_PF) {
                 int ls[RL_PF], oldr[RL_PF];
                 int64_t qq[RL_PF];
                 V v[RL_PF];
 #pragma unroll
                 for (int u = 0; u < RL_PF; u++) {
                     const int i = i0 + lane + 32 * u;
-                    ls[u] = i < filled ? list[i] : -1;
-                    if (ls[u] == pls && pin) ls[u] = -2;          // the pivot row: cleared below
-                    qq[u] = lb + rank0 + i - ((pin && ls[u] > pls) ? 1 : 0);
-                    v[u] = ls[u] >= 0 ? x[ndesc + ls[u]] : 0.0;
-                    oldr[u] = (ls[u] >= 0 && !overflow && lb == old_lb && qq[u] - lb < old_lc) ? d.Li[qq[u]] : -1;
+                    ls[u] = i < nrows ? list[i] : -1;
+                    const bool isp = pin && ls[u] == pls;
+                    qq[u] = lb + i - ((pin && ls[u] > pls) ? 1 : 0);
+                    v[u] = ls[u] >= 0 ? x[ndesc + ls[u]] : V(0);
+                    oldr[u] = (ls[u] >= 0 && !isp && !overflow && lb == old_lb && qq[u] - lb < old_lc) ? d.Li[qq[u]]
+                                                                                                      : -1;
                 }
 #pragma unroll
                 for (int u = 0; u < RL_PF; u++) {
                     if (ls[u] < 0) continue;
+                    if (!isfinite(v[u])) bad = true;
+                    if (ls[u] < nown) {
+                        ncand++;
+                        km = key_max(km, mag_key(v[u]));
+                    }
+                    if (pin && ls[u] == pls) continue;            // the pivot row: cleared below
                     if (!overflow) {
                         const int r = row_of_lslot(T, ls[u]);
                         if (oldr[u] != r) same = false;
@@ -554,9 +719,127 @@ __global__ void __launch_bounds__(128) bk_dd_kernel(bk_dev d, const int32_t *__r
                     x[ndesc + ls[u]] = 0.0;
                 }
             }
-            rank0 += filled;
             __syncwarp();
+            km = warp_max_key(km);
+            const V amax = key_value<V>(km);
+            ncand = warp_sum(ncand);
+            bad = __any_sync(BK_FULL, bad);
+            ok = !bad && ncand > 0 && amax > 0.0 && pin && (double)fabs(xp) >= tau * (double)amax;
+        } else {
+            int wcur = wfirst, filled = filled0;
+            for (;;) {
+                nrows += filled;
+                nseg++;
+                for (int i0 = 0; i0 < filled; i0 += 32 * RL_PF) {
+                    int ls[RL_PF];
+                    V v[RL_PF];
+#pragma unroll
+                    for (int u = 0; u < RL_PF; u++) {
+                        const int i = i0 + lane + 32 * u;
+                        ls[u] = i < filled ? list[i] : -1;
+                        v[u] = ls[u] >= 0 ? x[ndesc + ls[u]] : 0.0;
+                    }
+#pragma unroll
+                    for (int u = 0; u < RL_PF; u++) {
+                        if (ls[u] < 0) continue;
+                        if (!isfinite(v[u])) bad = true;
+                        if (ls[u] < nown) {
+                            ncand++;
+                            km = key_max(km, mag_key(v[u]));
+                        }
+                    }
+                }
+                __syncwarp();
+                if (wcur >= nrw) break;
+                filled = build_list(rb, nrw, wcur, list, lane);
+            }
+            km = warp_max_key(km);
+            const V amax = key_value<V>(km);
+            ncand = warp_sum(ncand);
+            bad = __any_sync(BK_FULL, bad);
+            const int pref = resolve ? d.pref[c] : pcur;
+            if (!bad && ncand > 0 && amax > 0.0) {
+                if (in_pattern(pref) && (double)fabs(x[ndesc + pref - T.lo]) >= tau * (double)amax) {
+                    piv = pref;
+                    ok = true;
+                } else if (resolve) {
+                    // the lowest own row reaching the maximum (the list is rebuilt over
+                    // the own rows: the L write below lists the pattern again)
+                    nseg = 0;
+                    int best = INT_MAX;
+                    const int nw_own = (nown + 31) >> 5;
+                    for (int wc = 0; wc < nw_own && best == INT_MAX;) {
+                        const int fo = build_list(rb, nw_own, wc, list, lane);
+                        for (int i0 = 0; i0 < fo; i0 += 32 * RL_PF) {
+                            int ls[RL_PF];
+                            V v[RL_PF];
+#pragma unroll
+                            for (int u = 0; u < RL_PF; u++) {
+                                const int i = i0 + lane + 32 * u;
+                                ls[u] = i < fo ? list[i] : -1;
+                                v[u] = ls[u] >= 0 ? x[ndesc + ls[u]] : 0.0;
+                            }
+#pragma unroll
+                            for (int u = 0; u < RL_PF; u++)
+                                if (ls[u] >= 0 && ls[u] < nown && mag_key(v[u]) == km) best = min(best, ls[u]);
+                        }
+                        best = warp_min(best);
+                        __syncwarp();
+                    }
+                    piv = T.lo + best;
+                    ok = true;
+                }
+            }
+            if (resolve && piv < 0) {
+                // no acceptable pivot at an exact column: the matrix is singular here
+                if (lane == 0) report_fail(d.status, c, bad ? BK_CODE_NAN : BK_CODE_SINGULAR);
+            }
+            if (piv < 0) piv = pcur;                     // keep the speculation consistent
+            DD_CLK(ck_b);
+            pls = piv - T.lo;
+            pin = in_pattern(piv);
+            xp = pin ? x[ndesc + pls] : 0.0;
+            // L(:,c) = x / pivot over the pattern's unpivoted rows; clear the state
+            place_l(nrows - (pin ? 1 : 0));
+            int rank0 = 0;
+            // a pattern listed in one segment by the selection above is still listed
+            const bool listed = nseg == 1;
+            for (int wc = 0; wc < nrw;) {
+                int fl2 = nrows;
+                if (listed) wc = nrw;
+                else fl2 = build_list(rb, nrw, wc, list, lane);
+                for (int i0 = 0; i0 < fl2; i0 += 32 * RL_PF) {
+                    int ls[RL_PF], oldr[RL_PF];
+                    int64_t qq[RL_PF];
+                    V v[RL_PF];
+#pragma unroll
+                    for (int u = 0; u < RL_PF; u++) {
+                        const int i = i0 + lane + 32 * u;
+                        ls[u] = i < fl2 ? list[i] : -1;
+                        if (ls[u] == pls && pin) ls[u] = -2;          // the pivot row: cleared below
+                        qq[u] = lb + rank0 + i - ((pin && ls[u] > pls) ? 1 : 0);
+                        v[u] = ls[u] >= 0 ? x[ndesc + ls[u]] : 0.0;
+                        oldr[u] = (ls[u] >= 0 && !overflow && lb == old_lb && qq[u] - lb < old_lc) ? d.Li[qq[u]]
+                                                                                                  : -1;
+                    }
+#pragma unroll
+                    for (int u = 0; u < RL_PF; u++) {
+                        if (ls[u] < 0) continue;
+                        if (!overflow) {
+                            const int r = row_of_lslot(T, ls[u]);
+                            if (oldr[u] != r) same = false;
+                            d.Li[qq[u]] = r;
+                            Lx[qq[u]] = v[u] / xp;
+                        }
+                        x[ndesc + ls[u]] = 0.0;
+                    }
+                }
+                rank0 += fl2;
+                __syncwarp();
+            }
         }
+        int64_t lpos = lb;
+        DD_CLK(ck_c);
         lpos = lb + nrows - (pin ? 1 : 0);
         for (int w = lane; w < nrw; w += 32) rb[w] = 0u;
         overflow = __any_sync(BK_FULL, overflow);
@@ -595,6 +878,16 @@ __global__ void __launch_bounds__(128) bk_dd_kernel(bk_dev d, const int32_t *__r
             __threadfence();
             st_release(d.done + c, epoch);
             BK_TREC(d.trace, BK_TR_ROUND, resolve ? 3 : 2, c, t0);
+#ifdef BK_TRACE
+            const long long ck_d = clock64();
+            bk_trace_raw(d.trace, BK_TR_PHASE, 50, c, (unsigned long long)(ck_a - ck_last),
+                         (unsigned long long)(ck_b - ck_a));
+            bk_trace_raw(d.trace, BK_TR_PHASE, 51, c, (unsigned long long)(ck_c - ck_b),
+                         (unsigned long long)(ck_d - ck_c));
+            bk_trace_raw(d.trace, BK_TR_PHASE, 52, c, (unsigned long long)ck_wait, (unsigned long long)nu);
+            bk_trace_raw(d.trace, BK_TR_PHASE, 53, c, (unsigned long long)ck_stg,
+                         (unsigned long long)ck_app | ((unsigned long long)steps_after << 40));
+#endif
         }
         __syncwarp();
         if (why) return;      // the workspace slice may hold stale values; the host clears it
@@ -608,7 +901,7 @@ void bk_launch_dd(const bk_dev &d, const int32_t *cols, int32_t ncols, int32_t *
 {
     if (ncols <= 0) return;
     int warps = std::min<int>(ncols, max_warps > 0 ? std::min<int>(max_warps, d.wsd_warps) : d.wsd_warps);
-    const size_t smem = (size_t)4 * d.dd_words * sizeof(uint32_t);
+    const size_t smem = (size_t)4 * d.dd_words * sizeof(uint32_t) + (size_t)4 * BK_DD_STAGE_BYTES;
     const int grid = (warps + 3) / 4;
     // the limit is a property of the kernel shared by every handle and thread:
     // raise it once to the largest footprint the plan allows (160 KB)

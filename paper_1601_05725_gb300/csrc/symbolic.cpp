@@ -711,10 +711,11 @@ void bk_plan_layout(bk_plan &pl)
     pl.ahat_doubles = std::max<int64_t>(ah, 1);
     pl.ahat_words = std::max<int64_t>(ab, 1);
     // the reach's step and row bitmaps fit in shared memory for four warps a block
+    // (beside the rounds' staging areas)
     int64_t bw = 0;
     for (auto &T : pl.tasks) bw = std::max<int64_t>(bw, ((int64_t)(T.hi - T.sp_lo) + 31) / 32 + (T.lspace + 31) / 32);
     bw = (bw + 3) & ~(int64_t)3;
-    pl.dd_words = 4 * bw * 4 <= 160 * 1024 ? (int32_t)bw : 0;
+    pl.dd_words = 4 * bw * 4 + 4 * BK_DD_STAGE_BYTES <= 160 * 1024 ? (int32_t)bw : 0;
     // One workspace serves every level in turn, each with slices of its own size:
     // a level wants one slice per column it processes at once (at most 152 SMs x
     // 16 warps); the workspace holds what level 0 (the leaves and BTF blocks) wants
