@@ -54,7 +54,7 @@ struct basker_s {
     // the separators' descendant phase on stored patterns: the columns left to the
     // reach kernel (listed on the device) and the fast kernel's shared memory
     int32_t *df_redo = nullptr;
-    size_t df_smem = 0;
+    std::vector<bk_desc_par> df_par;     // the descendant phase's on-chip sizes per ND level
     // the arena as the symbolic pass left it (natural pivots, symbolic pattern and
     // schedule): a factorization first tries the stored-pattern path from it
     int32_t *sym_Li = nullptr, *sym_Ui = nullptr, *sym_n = nullptr;   // sym_n: 8 arrays of n ints
@@ -489,7 +489,8 @@ int setup_device(basker_t h)
     TRY(dalloc(h, &h->rd_c0, (size_t)std::max<size_t>(pl.tasks.size(), 1)));
     TRY(dalloc(h, &h->rd_cols, (size_t)std::max(n, 1)));
     TRY(dalloc(h, &h->df_redo, (size_t)std::max(n, 1)));
-    h->df_smem = bk_desc_fast_smem(pl.tasks.data(), (int32_t)pl.tasks.size());
+    h->df_par.clear();
+    for (size_t l = 0; l < pl.level_tasks.size(); l++) h->df_par.push_back(bk_desc_fast_params(pl, (int32_t)l));
     CU(cudaMallocHost((void **)&h->h_stage, sizeof(int32_t) * ((size_t)n + 4 * pl.tasks.size() + 16)));
     CU(cudaMallocHost((void **)&h->h_status, sizeof(bk_status)));
     CU(cudaMallocHost((void **)&h->h_task_fail, sizeof(int32_t) * std::max<size_t>(pl.tasks.size(), 1)));
@@ -617,7 +618,8 @@ int launch_desc_refactor(basker_t h, const int32_t *cols, int32_t ncols, cudaStr
     CU(cudaMemsetAsync(h->d.counter + 5, 0, sizeof(int32_t), s));
     CU(cudaMemsetAsync(h->d.counter + 7, 0, sizeof(int32_t), s));
     CU(cudaMemsetAsync(h->d.counter + 3, 0, sizeof(int32_t), s));
-    if (!h->df_smem) {
+    const bk_desc_par par = level < h->df_par.size() ? h->df_par[level] : bk_desc_par{};
+    if (!par.smem) {
         // separators too large for the stored-pattern kernel: every column by the reach
         tbeg(h, KT_DESC, s, 1);
         bk_launch_gp_desc(dl, cols, ncols, h->d.counter + 3, s);
@@ -627,7 +629,7 @@ int launch_desc_refactor(basker_t h, const int32_t *cols, int32_t ncols, cudaStr
         return BASKER_OK;
     }
     tbeg(h, KT_DESC, s, 2);
-    bk_launch_desc_fast(dl, cols, ncols, h->d.counter + 5, h->df_redo, h->d.counter + 7, h->df_smem, s);
+    bk_launch_desc_fast(dl, cols, ncols, h->d.counter + 5, h->df_redo, h->d.counter + 7, par, s);
     CU(cudaGetLastError());
     bk_launch_gp_desc(dl, h->df_redo, ncols, h->d.counter + 3, s, h->d.counter + 7);
     CU(cudaGetLastError());

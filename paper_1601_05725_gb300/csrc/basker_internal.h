@@ -188,9 +188,17 @@ void bk_launch_gp_desc(const bk_dev &d, const int32_t *cols, int32_t ncols, int3
                        void *stream, const int32_t *ncols_dev = nullptr);
 // kernels_desc.cu: the descendant phase on the stored patterns, verified; the
 // columns that fail are listed in redo[0 .. *nredo) for bk_launch_gp_desc
-size_t bk_desc_fast_smem(const bk_task *tasks, int32_t ntasks);
+// sizes of the descendant phase's on-chip layout for one ND level
+struct bk_desc_par {
+    int32_t hmask;      // slot table entries - 1 (a power of two minus one)
+    int32_t xs, xl;     // stored steps and L-space rows of a column kept on chip, at most
+    int32_t prs_words;  // words of the bitmap over the largest descendant space
+    int32_t cap;        // L entries per staging buffer (512 or 1024)
+    size_t smem;        // dynamic shared memory (0: the bitmap does not fit; reach kernel only)
+};
+bk_desc_par bk_desc_fast_params(const bk_plan &pl, int32_t level);
 void bk_launch_desc_fast(const bk_dev &d, const int32_t *cols, int32_t ncols, int32_t *counter, int32_t *redo,
-                         int32_t *nredo, size_t smem, void *stream);
+                         int32_t *nredo, const bk_desc_par &par, void *stream);
 void bk_launch_dd(const bk_dev &d, const int32_t *cols, int32_t ncols, int32_t *counter, double tau,
                   int32_t epoch, long long budget, int32_t refno, void *stream, int max_warps = 0);
 void bk_launch_static(const bk_dev &d, int32_t ncols, double tau, int32_t epoch,

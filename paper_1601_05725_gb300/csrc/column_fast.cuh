@@ -27,13 +27,13 @@ namespace bk {
 constexpr int FC_SEG = 128;    // steps whose metadata sit in shared memory at once
 constexpr int FC_CAP = 1024;   // L entries per buffer (two buffers)
 
-template <typename V>
+template <typename V, int CAP = FC_CAP>
 struct FcSmem {
     int32_t j[FC_SEG], sp[FC_SEG], jc[FC_SEG], off[FC_SEG + 1];
     int64_t jl[FC_SEG];
     V u[FC_SEG];               // U(j,c) of the segment's steps, written out after it
-    int32_t bi[2][FC_CAP];
-    V bv[2][FC_CAP];
+    int32_t bi[2][CAP];
+    V bv[2][CAP];
 };
 
 __device__ __forceinline__ void fc_cp4(void *dst, const void *src)
@@ -228,26 +228,33 @@ __device__ __forceinline__ bool fc_nonfinite(float v) { return (__float_as_int(v
 // not the reach; the caller falls back).  map (if not null): x and mark are
 // indexed by a compact index instead of the slot: map.find(slot) for slots below
 // nallow (-1: not there, vfail), map.shift + slot for the others.
+// An open-addressing table from slot to position: each entry packs the slot
+// (above FC_POS_BITS) and the position (below); -1 is empty.
+constexpr int FC_POS_BITS = 11;
+constexpr int FC_POS_MASK = (1 << FC_POS_BITS) - 1;
+
+__device__ __forceinline__ int fc_hash(int s, int mask) { return (int)(((unsigned)s * 2654435761u) >> 7) & mask; }
+
 struct FcMap {
-    const int32_t *keys, *vals;
+    const int32_t *tab;
     int mask, shift;
     __device__ __forceinline__ int find(int s) const
     {
-        int h = (int)(((unsigned)s * 2654435761u) >> 7) & mask;
+        int h = fc_hash(s, mask);
         for (int probe = 0; probe <= mask; probe++) {
-            const int k = keys[h];
-            if (k == s) return vals[h];
+            const int k = tab[h];
             if (k < 0) return -1;
+            if ((k >> FC_POS_BITS) == s) return k & FC_POS_MASK;
             h = (h + 1) & mask;
         }
         return -1;
     }
 };
 
-template <typename V, bool MARK, int NT>
+template <typename V, bool MARK, int NT, int CAP = FC_CAP>
 __device__ __forceinline__ bool column_fast_update_cta(const bk_dev &d, const bk_task &T, int base,
                                                        const int32_t *Ulist, int ns, V *Uout, V *x,
-                                                       FcSmem<V> &S, unsigned char *mark, int *red, int tid,
+                                                       FcSmem<V, CAP> &S, unsigned char *mark, int *red, int tid,
                                                        bool &bad, const uint32_t *allow = nullptr, int nallow = 0,
                                                        bool *vfail = nullptr, const FcMap *map = nullptr)
 {
@@ -307,13 +314,13 @@ __device__ __forceinline__ bool column_fast_update_cta(const bk_dev &d, const bk
         // the batch starting at step bs: as many steps as fit one buffer (at least
         // one); the steps that fit form a prefix, so their count decides
         auto batch_end = [&](int bs) {
-            const bool fits = tid >= bs && tid < nseg && S.off[tid + 1] - S.off[bs] <= FC_CAP;
+            const bool fits = tid >= bs && tid < nseg && S.off[tid + 1] - S.off[bs] <= CAP;
             return bs + max(1, __syncthreads_count(fits));
         };
         // copies of a batch's entries: steps dealt to the warps, entries to the lanes
         auto issue = [&](int bs, int be, int b) {
             const int e0 = S.off[bs];
-            if (S.off[be] - e0 <= FC_CAP) {
+            if (S.off[be] - e0 <= CAP) {
                 for (int t = bs + warp; t < be; t += NT / 32) {
                     const int a = S.off[t], cnt = S.off[t + 1] - a;
                     const int64_t g = S.jl[t];
@@ -337,7 +344,7 @@ __device__ __forceinline__ bool column_fast_update_cta(const bk_dev &d, const bk
             __syncthreads();
             FC_LAP(2);
             const int e0 = S.off[bs], e1 = S.off[be];
-            const bool direct = e1 - e0 > FC_CAP;
+            const bool direct = e1 - e0 > CAP;
             int32_t *const bi = S.bi[buf];
             const V *const bv = S.bv[buf];
             if (!direct) {

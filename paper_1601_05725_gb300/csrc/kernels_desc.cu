@@ -18,15 +18,19 @@
 // as the reach kernel would write them.  A column that fails is cleaned up and
 // listed for the reach kernel (bk_gp_desc_kernel), which runs next.
 //
-// Layout.  Compact (up to DF_MAXS stored steps and DF_MAXL L-space rows): x and
-// a mark byte per entry in shared memory, indexed by the position of a step in
-// the stored list for the descendant rows (found through an open-addressing
-// table from slot to position, built from the stored steps' pivot rows; a
-// descendant row not in the table is not the pivot row of a stored step) and
-// after them by the L-space slot.  Otherwise x and a mark byte per slot in the
-// block's global workspace slice (x over the column's whole space does not fit
-// on chip), with a bitmap over the descendant slots holding the stored steps'
-// pivot rows in shared memory.
+// Layout.  Compact (a column with at most xs stored steps and an L-space of at
+// most xl rows, xs and xl sized per ND level from the symbolic counts of its
+// separator columns): x and a mark byte per entry in shared memory, indexed by
+// the position of a step in the stored list for the descendant rows (found
+// through an open-addressing table from slot to position, built from the stored
+// steps' pivot rows; a descendant row not in the table is not the pivot row of a
+// stored step) and after them by the L-space slot.  Otherwise x and a mark byte
+// per slot in the block's global workspace slice (x over the column's whole
+// space does not fit on chip), with a bitmap over the descendant slots holding
+// the stored steps' pivot rows in shared memory, in the memory the compact
+// layout uses (a block re-initialises it when it switches between the two).
+// The level's sizes keep the block's shared memory small enough for all of a
+// level's columns to be resident at once (one wave).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -42,34 +46,34 @@ using namespace bk;
 namespace {
 
 constexpr int DF_NT = 128;
-constexpr int DF_H = 4096;        // table entries (a power of two)
-constexpr int DF_MAXS = 2048;     // stored steps of a compact column, at most
-constexpr int DF_MAXL = 2048;     // L-space rows of a compact column, at most
-// shared words of the compact layout (table keys and values, x, marks)
-constexpr int DF_COMPACT_WORDS = (2 * DF_H * 4 + (DF_MAXS + DF_MAXL) * (8 + 1) + 15) / 16 * 4;
+constexpr int DF_MAXS = 1 << FC_POS_BITS;   // stored steps of a compact column, at most
+constexpr int DF_MAXL = 2048;               // L-space rows of a compact column, at most
+// L entries per staging buffer: the larger buffers where the level's columns
+// still fit on the SMs at once (bk_desc_par::cap picks the kernel)
+constexpr int DF_CAP_SMALL = 512, DF_CAP_LARGE = 1024;
 
-template <typename V>
-__global__ void __launch_bounds__(DF_NT, 1) bk_desc_fast_kernel(bk_dev d, const int32_t *__restrict__ cols,
-                                                                 int32_t ncols, int32_t *counter, int32_t *redo,
-                                                                 int32_t *nredo, int32_t prs_words)
+template <typename V, int DF_CAP>
+__global__ void __launch_bounds__(DF_NT) bk_desc_fast_kernel(bk_dev d, const int32_t *__restrict__ cols,
+                                                             int32_t ncols, int32_t *counter, int32_t *redo,
+                                                             int32_t *nredo, bk_desc_par par)
 {
     const V *const Bx = vals<V>(d.Bx);
     V *const Ux = vals<V>(d.Ux);
     V *const Ahat = vals<V>(d.ahat);
-    // compact: table keys, table values, x, marks; otherwise the prow(S) bitmap
+    // compact: the slot table, x, marks; otherwise the prow(S) bitmap (same memory)
     extern __shared__ __align__(16) uint32_t df_smem[];
     __shared__ bk_task T;
-    __shared__ FcSmem<V> fcs;
+    __shared__ FcSmem<V, DF_CAP> fcs;
     __shared__ int red[DF_NT / 32 + 1];
     __shared__ int ctl[2];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    int32_t *const hkeys = reinterpret_cast<int32_t *>(df_smem);
-    int32_t *const hvals = hkeys + DF_H;
-    V *const xc = reinterpret_cast<V *>(hvals + DF_H);
-    unsigned char *const mc = reinterpret_cast<unsigned char *>(xc + DF_MAXS + DF_MAXL);
-    uint32_t *const prs = df_smem + DF_COMPACT_WORDS;
-    for (int i = tid; i < DF_H; i += DF_NT) hkeys[i] = -1;
-    for (int i = tid; i < prs_words; i += DF_NT) prs[i] = 0u;
+    const int H = par.hmask + 1;
+    int32_t *const tab = reinterpret_cast<int32_t *>(df_smem);
+    V *const xc = reinterpret_cast<V *>(df_smem + H);
+    unsigned char *const mc = reinterpret_cast<unsigned char *>(xc + par.xs + par.xl);
+    uint32_t *const prs = df_smem;
+    for (int i = tid; i < H; i += DF_NT) tab[i] = -1;
+    bool table_ready = true;         // the memory holds an empty table (else a zero bitmap)
     int cur_task = -1;
     for (;;) {
         if (tid == 0) ctl[0] = atomicAdd(counter, 1);
@@ -94,21 +98,28 @@ __global__ void __launch_bounds__(DF_NT, 1) bk_desc_fast_kernel(bk_dev d, const 
         const int64_t ub = d.Ubeg[c];
         const int ns = d.dcnt[c];
         const int e1 = d.Bp[c + 1];
-        if (ns >= 0 && ns <= DF_MAXS && ns <= d.Ucnt[c] - 1 && lsp <= DF_MAXL) {
+        if (ns >= 0 && ns <= par.xs && ns <= d.Ucnt[c] - 1 && lsp <= par.xl && ndesc < (1 << (31 - FC_POS_BITS))) {
             // ---- compact: x on chip
+            if (!table_ready) {
+                __syncthreads();
+                for (int i = tid; i < H; i += DF_NT) tab[i] = -1;
+                table_ready = true;
+                __syncthreads();
+            }
             bool ok = true, broken = false;
             for (int q = tid; q < ns; q += DF_NT) {
                 const int j = __ldcg(d.Ui + ub + q);
                 const int sl = __ldcg(d.prow + j) - base;     // a descendant row's slot
                 if (j < base || j >= T.lo || (unsigned)sl >= (unsigned)ndesc) { ok = false; continue; }
-                int h = (int)(((unsigned)sl * 2654435761u) >> 7) & (DF_H - 1);
-                for (int probe = 0; probe < DF_H; probe++) {
-                    const int old = atomicCAS(hkeys + h, -1, sl);
-                    if (old == -1 || old == sl) {
-                        hvals[h] = q;
+                int h = fc_hash(sl, par.hmask);
+                for (int probe = 0; probe < H; probe++) {
+                    const int old = atomicCAS(tab + h, -1, (sl << FC_POS_BITS) | q);
+                    if (old == -1) break;
+                    if ((old >> FC_POS_BITS) == sl) {      // two stored steps, one pivot row
+                        ok = false;
                         break;
                     }
-                    h = (h + 1) & (DF_H - 1);
+                    h = (h + 1) & par.hmask;
                 }
             }
             for (int i = tid; i < ns + lsp; i += DF_NT) {
@@ -116,7 +127,7 @@ __global__ void __launch_bounds__(DF_NT, 1) bk_desc_fast_kernel(bk_dev d, const 
                 mc[i] = 0;
             }
             ok = __syncthreads_and(ok);
-            const FcMap map{hkeys, hvals, DF_H - 1, ns - ndesc};
+            const FcMap map{tab, par.hmask, ns - ndesc};
             if (ok) {
                 for (int e = d.dstart[c] + tid; e < e1; e += DF_NT) {
                     const int sl = slot_of(T, base, d.Bi[e]);
@@ -130,8 +141,8 @@ __global__ void __launch_bounds__(DF_NT, 1) bk_desc_fast_kernel(bk_dev d, const 
             }
             bool bad = false, vfail = false;
             if (ok && !__syncthreads_or(broken)) {
-                if (!column_fast_update_cta<V, true, DF_NT>(d, T, base, d.Ui + ub, ns, Ux + ub, xc, fcs, mc, red,
-                                                            tid, bad, nullptr, ndesc, &vfail, &map))
+                if (!column_fast_update_cta<V, true, DF_NT, DF_CAP>(d, T, base, d.Ui + ub, ns, Ux + ub, xc, fcs, mc,
+                                                                    red, tid, bad, nullptr, ndesc, &vfail, &map))
                     broken = true;
                 ok = !__syncthreads_or(vfail);
                 if (ok)
@@ -162,10 +173,17 @@ __global__ void __launch_bounds__(DF_NT, 1) bk_desc_fast_kernel(bk_dev d, const 
             }
             // the table back to empty
             __syncthreads();
-            for (int i = tid; i < DF_H; i += DF_NT) hkeys[i] = -1;
+            for (int i = tid; i < H; i += DF_NT) tab[i] = -1;
             __syncthreads();
             if (tid == 0) BK_TREC(d.trace, BK_TR_DESC, (ok && !broken) ? 3 : 4, c, t0);
             continue;
+        }
+        if (table_ready) {
+            // the bitmap over the descendant slots starts empty
+            __syncthreads();
+            for (int i = tid; i < par.prs_words; i += DF_NT) prs[i] = 0u;
+            table_ready = false;
+            __syncthreads();
         }
         bool ok = ns >= 0 && ns <= d.Ucnt[c] - 1;
         // the stored steps must be descendants; their pivot rows form prs
@@ -190,8 +208,8 @@ __global__ void __launch_bounds__(DF_NT, 1) bk_desc_fast_kernel(bk_dev d, const 
         }
         bool bad = false, vfail = false;
         if (ok && !__syncthreads_or(broken)) {
-            if (!column_fast_update_cta<V, true, DF_NT>(d, T, base, d.Ui + ub, ns, Ux + ub, x, fcs, mark, red, tid,
-                                                        bad, prs, ndesc, &vfail))
+            if (!column_fast_update_cta<V, true, DF_NT, DF_CAP>(d, T, base, d.Ui + ub, ns, Ux + ub, x, fcs, mark, red,
+                                                                tid, bad, prs, ndesc, &vfail))
                 broken = true;
             ok = !__syncthreads_or(vfail);
             // every stored step's pivot row was touched
@@ -273,31 +291,72 @@ __global__ void __launch_bounds__(DF_NT, 1) bk_desc_fast_kernel(bk_dev d, const 
 
 }  // namespace
 
-size_t bk_desc_fast_smem(const bk_task *tasks, int32_t ntasks)
+// The compact layout's sizes for the separator columns of ND level `level`: xs
+// stored steps (1.5x the largest symbolic U count of the level's columns, as
+// pivoting moves patterns), a table of at least 1.5 xs entries, xl the largest
+// L-space; the shared memory is the larger of that layout and the bitmap over
+// the largest descendant space.  smem 0: the level's descendant phase cannot
+// keep the bitmap on chip (every column goes to the reach kernel).
+bk_desc_par bk_desc_fast_params(const bk_plan &pl, int32_t level)
 {
-    size_t words = 4;
-    for (int32_t t = 0; t < ntasks; t++)
-        if (tasks[t].sp_lo < tasks[t].lo) words = std::max(words, ((size_t)(tasks[t].lo - tasks[t].sp_lo) + 31) / 32);
-    const size_t bytes = (size_t)DF_COMPACT_WORDS * 4 + ((words + 3) & ~(size_t)3) * 4;
-    // the bitmap over the largest separator's descendant rows must fit on chip
-    return bytes <= 160 * 1024 ? bytes : 0;
+    bk_desc_par p{};
+    int64_t umax = 0, xl = 0, words = 4;
+    for (const bk_task &T : pl.tasks) {
+        if (T.level != level || T.sp_lo >= T.lo) continue;
+        for (int32_t c = T.lo; c < T.hi; c++)
+            umax = std::max<int64_t>(umax, c < (int32_t)pl.sUcnt.size() ? pl.sUcnt[(size_t)c] : (int64_t)(c - T.sp_lo + 1));
+        xl = std::max<int64_t>(xl, T.lspace);
+        words = std::max<int64_t>(words, ((int64_t)(T.lo - T.sp_lo) + 31) / 32);
+    }
+    int64_t xs = std::min<int64_t>(DF_MAXS, ((umax * 3 / 2) + 63) & ~(int64_t)31);
+    if (xl > DF_MAXL) xs = xl = 0;                 // no column of the level fits on chip
+    int64_t H = 256;
+    while (H < xs + xs / 2) H *= 2;
+    const size_t compact = (((size_t)H * 4 + (size_t)(xs + xl) * (sizeof(double) + 1)) + 15) & ~(size_t)15;
+    const size_t bitmap = (((size_t)words + 3) & ~(size_t)3) * 4;
+    p.hmask = (int32_t)H - 1;
+    p.xs = (int32_t)xs;
+    p.xl = (int32_t)xl;
+    p.prs_words = (int32_t)(((size_t)words + 3) & ~(size_t)3);
+    const size_t bytes = std::max(compact, bitmap);
+    p.smem = bytes <= 160 * 1024 ? bytes : 0;
+    // the larger staging buffers when the blocks the level's columns need on each
+    // SM still fit its shared memory with them (static part: the buffers, 24 bytes
+    // an entry, plus about 5 KB; 1 KB reserved a block)
+    int64_t ncols = 0;
+    for (const bk_task &T : pl.tasks)
+        if (T.level == level && T.sp_lo < T.lo) ncols += T.hi - T.lo;
+    const int64_t per_sm = std::max<int64_t>(1, (ncols + 151) / 152);
+    const size_t big = p.smem + (size_t)DF_CAP_LARGE * 24 + 6 * 1024 + 1024;
+    p.cap = (size_t)per_sm * big <= 228 * 1024 ? DF_CAP_LARGE : DF_CAP_SMALL;
+    return p;
 }
 
 void bk_launch_desc_fast(const bk_dev &d, const int32_t *cols, int32_t ncols, int32_t *counter, int32_t *redo,
-                         int32_t *nredo, size_t smem, void *stream)
+                         int32_t *nredo, const bk_desc_par &par, void *stream)
 {
     if (ncols <= 0) return;
     static std::once_flag once;
     std::call_once(once, [] {
-        cudaFuncSetAttribute(bk_desc_fast_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-        cudaFuncSetAttribute(bk_desc_fast_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+        const int lim = 160 * 1024;
+        cudaFuncSetAttribute(bk_desc_fast_kernel<double, DF_CAP_SMALL>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        cudaFuncSetAttribute(bk_desc_fast_kernel<float, DF_CAP_SMALL>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        cudaFuncSetAttribute(bk_desc_fast_kernel<double, DF_CAP_LARGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        cudaFuncSetAttribute(bk_desc_fast_kernel<float, DF_CAP_LARGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     });
-    const int grid = std::max(1, std::min<int>({ncols, d.wsd_warps, 152 * 4}));
+    // every column of the level resident at once where the shared memory allows
+    const int grid = std::max(1, std::min<int>({ncols, d.wsd_warps, 152 * 8}));
     cudaStream_t s = (cudaStream_t)stream;
-    if (d.prec)
-        bk_desc_fast_kernel<float><<<grid, DF_NT, smem, s>>>(d, cols, ncols, counter, redo, nredo,
-                                                             (int32_t)(smem / 4) - DF_COMPACT_WORDS);
-    else
-        bk_desc_fast_kernel<double><<<grid, DF_NT, smem, s>>>(d, cols, ncols, counter, redo, nredo,
-                                                              (int32_t)(smem / 4) - DF_COMPACT_WORDS);
+    const bool large = par.cap >= DF_CAP_LARGE;
+    if (d.prec) {
+        if (large)
+            bk_desc_fast_kernel<float, DF_CAP_LARGE><<<grid, DF_NT, par.smem, s>>>(d, cols, ncols, counter, redo, nredo, par);
+        else
+            bk_desc_fast_kernel<float, DF_CAP_SMALL><<<grid, DF_NT, par.smem, s>>>(d, cols, ncols, counter, redo, nredo, par);
+    } else {
+        if (large)
+            bk_desc_fast_kernel<double, DF_CAP_LARGE><<<grid, DF_NT, par.smem, s>>>(d, cols, ncols, counter, redo, nredo, par);
+        else
+            bk_desc_fast_kernel<double, DF_CAP_SMALL><<<grid, DF_NT, par.smem, s>>>(d, cols, ncols, counter, redo, nredo, par);
+    }
 }
