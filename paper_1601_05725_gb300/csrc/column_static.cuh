@@ -16,16 +16,19 @@ namespace bk {
 __device__ __forceinline__ bool flag_wait(const bk_dev &d, const int *flag, int epoch, long long budget, int lane)
 {
     int ok = 1;
-    if (lane == 0 && ld_acquire(flag) != epoch) {
-        const long long t0 = clock64();
-        while (ld_acquire(flag) != epoch) {
-            if (*reinterpret_cast<const volatile int *>(&d.status->timeout) || clock64() - t0 > budget) {
-                atomicExch(&d.status->timeout, 1);
-                ok = 0;
-                break;
+    if (lane == 0) {
+        if (ld_relaxed(flag) != epoch) {
+            const long long t0 = clock64();
+            while (ld_relaxed(flag) != epoch) {
+                if (*reinterpret_cast<const volatile int *>(&d.status->timeout) || clock64() - t0 > budget) {
+                    atomicExch(&d.status->timeout, 1);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
             }
-            __nanosleep(64);
         }
+        if (ok) fence_acquire();
     }
     return __shfl_sync(BK_FULL, ok, 0) != 0;
 }
@@ -113,7 +116,8 @@ __device__ __forceinline__ bool pattern_column(const bk_dev &d, const bk_task &T
         if (lane < nin) {
             j_l = d.Ui[ub + k0 + lane];
             const bool must = wait_all || (j_l >= wait_lo && d.col_task[j_l] == tid);
-            done_l = !must || ld_acquire(d.done + j_l) == epoch;
+            done_l = !must || ld_relaxed(d.done + j_l) == epoch;
+            if (must && done_l) fence_acquire();
             if (pchg && must && done_l && __ldcg(pchg + j_l) == epoch) changed = true;
             sp_l = slot_of(T, base, __ldcg(d.prow + j_l));
             jl_l = __ldcg(d.Lbeg + j_l);

@@ -125,6 +125,20 @@ __device__ __forceinline__ int ld_acquire(const int *p)
     return v;
 }
 
+// Waits poll a flag with relaxed loads and, once it holds the value waited for,
+// take one fence: a relaxed load followed by fence.acq_rel is an acquire pattern,
+// so the reads after the wait are ordered after the writes released before the
+// flag, while the polls themselves order nothing (one fence a wait, not one
+// acquire a poll).
+__device__ __forceinline__ int ld_relaxed(const int *p)
+{
+    int v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void fence_acquire() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
 __device__ __forceinline__ void st_release(int *p, int v)
 {
     asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");

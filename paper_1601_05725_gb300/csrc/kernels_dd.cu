@@ -70,15 +70,17 @@ __device__ __forceinline__ int next_step_bit(const volatile uint32_t *bm, int nw
 // warp already gave up).
 __device__ __forceinline__ bool lane_wait(const bk_dev &d, const int *flag, int epoch, long long budget)
 {
-    if (ld_acquire(flag) == epoch) return true;
-    const long long t0 = clock64();
-    while (ld_acquire(flag) != epoch) {
-        if (*reinterpret_cast<const volatile int *>(&d.status->timeout) || clock64() - t0 > budget) {
-            atomicExch(&d.status->timeout, 1);
-            return false;
+    if (ld_relaxed(flag) != epoch) {
+        const long long t0 = clock64();
+        while (ld_relaxed(flag) != epoch) {
+            if (*reinterpret_cast<const volatile int *>(&d.status->timeout) || clock64() - t0 > budget) {
+                atomicExch(&d.status->timeout, 1);
+                return false;
+            }
+            __nanosleep(32);
         }
-        __nanosleep(32);
     }
+    fence_acquire();
     return true;
 }
 
@@ -150,7 +152,11 @@ __device__ __forceinline__ void read_step(const bk_dev &d, const bk_task &T, RSt
     const bool inround = j >= s0 && j < T.hi;
     int dn = 1;
     if (inround && !after_wait) {
-        dn = lane == 0 ? (ld_acquire(d.done + j) == epoch) : 0;
+        dn = 0;
+        if (lane == 0 && ld_relaxed(d.done + j) == epoch) {
+            fence_acquire();
+            dn = 1;
+        }
         dn = __shfl_sync(BK_FULL, dn, 0);
     }
     // after the wait, L(:,j)'s entries are read where the extent read before the
@@ -393,7 +399,8 @@ __global__ void __launch_bounds__(128) bk_dd_kernel(bk_dev d, const int32_t *__r
                         bool done = false;
                         int v = 0;
                         if ((todo >> lane) & 1u) {
-                            done = ld_acquire(d.done + j) == epoch;
+                            done = ld_relaxed(d.done + j) == epoch;
+                            if (done) fence_acquire();
                             if (done) v = __ldcg(d.pchg_ep + j) == epoch ? 2 : (__ldcg(d.dirty_ep + j) == epoch ? 1 : 0);
                         }
                         verdict = warp_max_i(v);

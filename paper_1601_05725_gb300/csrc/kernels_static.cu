@@ -113,9 +113,9 @@ __global__ void __launch_bounds__(128) bk_levels_kernel(bk_dev d, int32_t epoch,
         for (int q = lane; q < uc - 1; q += 32) {
             const int j = d.Ui[ub + q];
             const int *flag = d.done + j;
-            if (ld_acquire(flag) != epoch) {
+            if (ld_relaxed(flag) != epoch) {
                 const long long t0 = clock64();
-                while (ld_acquire(flag) != epoch) {
+                while (ld_relaxed(flag) != epoch) {
                     if (*reinterpret_cast<const volatile int *>(&d.status->timeout) || clock64() - t0 > budget) {
                         atomicExch(&d.status->timeout, 1);
                         ok = 0;
@@ -125,6 +125,7 @@ __global__ void __launch_bounds__(128) bk_levels_kernel(bk_dev d, int32_t epoch,
                 }
             }
             if (!ok) break;
+            fence_acquire();
             lv = max(lv, __ldcg(d.level + j) + 1);
         }
         if (__any_sync(BK_FULL, !ok)) return;
