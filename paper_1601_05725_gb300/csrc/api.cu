@@ -604,6 +604,7 @@ bk_dev level_dev(basker_t h, size_t l)
         d.wsd_slice = h->pl.level_slice[l];
         d.wsd_warps = h->pl.level_warps[l];
     }
+    if (l < h->pl.level_dd_words.size()) d.dd_words = h->pl.level_dd_words[l];
     return d;
 }
 

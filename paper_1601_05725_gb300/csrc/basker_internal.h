@@ -145,6 +145,7 @@ struct bk_plan {
     std::vector<int32_t> level_warps;
     int64_t wsd_bytes = 0;
     int32_t dd_words = 0;                             // shared-memory reach bitmaps per warp (words)
+    std::vector<int32_t> level_dd_words;              // the same for the tasks of each ND level
     int32_t max_space = 0;
     int32_t symbolic_singular = -1;                   // first column without a structural pivot
     bool counts_only = false;                         // Algorithm 3's counts: no pattern, no schedule
@@ -166,7 +167,10 @@ size_t bk_task_smem_bytes(const bk_task &t);
 // up to BK_DD_SCAP entries (rows, values with 16 entries of slack for the
 // 16-byte boundaries, and what each row adds), per warp
 #define BK_DD_SCAP 512
-#define BK_DD_STAGE_BYTES ((BK_DD_SCAP + 16) * 12 + BK_DD_SCAP * 4)
+// per warp: rows, values, what each row adds, the x values under the rows, the
+// column's own previous L rows (compared with the new ones), the rows prestaged
+// before a wait and the rows' slots
+#define BK_DD_STAGE_BYTES ((BK_DD_SCAP + 16) * 12 + BK_DD_SCAP * 12 + (BK_DD_SCAP + 16) * 8 + BK_DD_SCAP * 4)
 size_t bk_dense_node_smem(const bk_task &t);
 bool bk_dense_node_eligible(const bk_task &t);
 // separators of at least BK_DENSE_CLUSTER_MIN columns run on a cluster of

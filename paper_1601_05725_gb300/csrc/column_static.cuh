@@ -13,11 +13,16 @@
 
 namespace bk {
 
-__device__ __forceinline__ bool flag_wait(const bk_dev &d, const int *flag, int epoch, long long budget, int lane)
+// Bounded wait of lane 0 on a flag, the warp told the outcome.  dist: how many
+// columns the waiting column lies past the one it waits for; the farther, the
+// less often it polls (a chain's head is polled by every column still to come).
+__device__ __forceinline__ bool flag_wait(const bk_dev &d, const int *flag, int epoch, long long budget, int lane,
+                                          int dist = 1)
 {
     int ok = 1;
     if (lane == 0) {
         if (ld_relaxed(flag) != epoch) {
+            const unsigned nap = (unsigned)min(max(dist, 1), 32) * 32u;
             const long long t0 = clock64();
             while (ld_relaxed(flag) != epoch) {
                 if (*reinterpret_cast<const volatile int *>(&d.status->timeout) || clock64() - t0 > budget) {
@@ -25,7 +30,7 @@ __device__ __forceinline__ bool flag_wait(const bk_dev &d, const int *flag, int 
                     ok = 0;
                     break;
                 }
-                __nanosleep(64);
+                __nanosleep(nap);
             }
         }
         if (ok) fence_acquire();
@@ -159,7 +164,7 @@ __device__ __forceinline__ bool pattern_column(const bk_dev &d, const bk_task &T
                 xv[u] = ss[u] >= 0 ? x[ss[u]] : 0.0;
             }
             if ((pending >> t) & 1u) {
-                if (!flag_wait(d, d.done + j, epoch, budget, lane)) return false;
+                if (!flag_wait(d, d.done + j, epoch, budget, lane, c - j)) return false;
                 if (pchg && __ldcg(pchg + j) == epoch) {
                     clear_stored(d, T, x, c, lane);
                     *aborted = true;

@@ -67,17 +67,22 @@ __device__ __forceinline__ int next_step_bit(const volatile uint32_t *bm, int nw
 }
 
 // Bounded wait of one lane on a flag; false if the budget ran out (or another
-// warp already gave up).
-__device__ __forceinline__ bool lane_wait(const bk_dev &d, const int *flag, int epoch, long long budget)
+// warp already gave up).  dist: how many columns the waiting column lies past
+// the one it waits for.  Along a chain of columns, every column still to come
+// polls the flag of the chain's head; the far ones poll it less often (their
+// wait is about dist links long), which keeps the head's flag from being the
+// point every waiter's requests queue at.
+__device__ __forceinline__ bool lane_wait(const bk_dev &d, const int *flag, int epoch, long long budget, int dist = 1)
 {
     if (ld_relaxed(flag) != epoch) {
+        const unsigned nap = (unsigned)min(max(dist, 1), 32) * 32u;
         const long long t0 = clock64();
         while (ld_relaxed(flag) != epoch) {
             if (*reinterpret_cast<const volatile int *>(&d.status->timeout) || clock64() - t0 > budget) {
                 atomicExch(&d.status->timeout, 1);
                 return false;
             }
-            __nanosleep(32);
+            __nanosleep(nap);
         }
     }
     fence_acquire();
@@ -102,6 +107,10 @@ __device__ __forceinline__ int build_list(const volatile uint32_t *rb, int nrw, 
     while (wcur < nrw) {
         const int w = wcur + lane;
         const uint32_t bits = w < nrw ? rb[w] : 0u;
+        if (!__any_sync(BK_FULL, bits != 0u)) {      // 32 empty words: nothing to list
+            wcur += 32;
+            continue;
+        }
         const int cnt = __popc(bits);
         const int pre = warp_exscan(cnt, lane);
         const int tot = __shfl_sync(BK_FULL, pre + cnt, 31);
@@ -207,9 +216,10 @@ __device__ __forceinline__ void read_step(const bk_dev &d, const bk_task &T, RSt
 // memory (16-byte copies at L2 only, from the 16-byte boundary below the column;
 // the arrays carry 16 bytes of padding), started where the extent read before
 // the wait puts it while the extent itself is read again; then the rows' slots
-// and, for rows of the node, the steps that pivot them, RS_PF loads a lane in
-// flight.  Each entry leaves its slot in srow and what it adds in sadd (a step
-// bit >= 0, a row bit encoded -2 - bit, or -1).  Returns the number of entries,
+// and, for rows of the node, the steps that pivot them, read with the x values
+// under the rows, RS_PF entries a lane in flight.  Each entry leaves its slot in
+// srow, what it adds in sadd (a step bit >= 0, a row bit encoded -2 - bit, or -1)
+// and x at its slot in sxv.  Returns the number of entries,
 // or -1 when L(:,j) has more than BK_DD_SCAP entries (read the usual way).
 constexpr int RS_PF = 8;
 
@@ -235,9 +245,76 @@ __device__ __forceinline__ int stage_range(T *dst, const T *src, int64_t e0, int
     return off;
 }
 
+// The rows rows[ro + q], q < n, of L(:,j): each one's slot (sslot), what it
+// adds to the reach (sadd) and x at its slot (sxv), RS_PF rows a lane at a time
+// (their pivot steps and x values read together).
+template <typename V>
+__device__ __forceinline__ void classify_rows(const bk_dev &d, const bk_task &T, int j, int c, int ndesc, const V *x,
+                                              const int *rows, int ro, int n, int *sslot, int *sadd, V *sxv,
+                                              int &why, int lane)
+{
+    const int base = T.sp_lo;
+    for (int q0 = 0; q0 < n; q0 += 32 * RS_PF) {
+        int rr[RS_PF], sl[RS_PF], pp[RS_PF];
+        V xv[RS_PF];
+#pragma unroll
+        for (int u = 0; u < RS_PF; u++) {
+            const int q = q0 + lane + 32 * u;
+            rr[u] = q < n ? rows[ro + q] : -1;
+            sl[u] = rr[u] >= 0 ? slot_of(T, base, rr[u]) : -1;
+            pp[u] = (sl[u] >= 0 && sl[u] < T.hi - base) ? __ldcg(d.pinv + rr[u]) : -1;
+            xv[u] = sl[u] >= 0 ? x[sl[u]] : V(0);
+        }
+#pragma unroll
+        for (int u = 0; u < RS_PF; u++) {
+            const int q = q0 + lane + 32 * u;
+            if (q >= n) continue;
+            int add = -1;
+            if (sl[u] < 0) {
+                if (!why) why = 65;
+            } else if (pp[u] >= 0 && pp[u] < c) {
+                if (pp[u] > j) add = pp[u] - base;
+                else if (!why) why = 66;
+            } else if (sl[u] >= ndesc) {
+                add = -2 - (sl[u] - ndesc);
+            } else if (!why) {
+                why = 67;
+            }
+            sslot[q] = sl[u];
+            sadd[q] = add;
+            sxv[q] = xv[u];
+        }
+    }
+    __syncwarp();
+}
+
+// Before waiting for step j: its rows where the extent read earlier puts them
+// (a guess: the step may still change them) into sgr, classified into sslot,
+// sadd and sxv while the wait goes on.  x is final for step j already (every
+// earlier step is applied).  Returns the offset of the first row in sgr, or -1
+// when the guess is not usable.
+template <typename V>
+__device__ __forceinline__ int prestage_step(const bk_dev &d, const bk_task &T, const RStep<V> &st, int j, int c,
+                                             int ndesc, const V *x, int *sgr, int *sslot, int *sadd, V *sxv,
+                                             int &why_pre, int lane)
+{
+    if (st.jc < 0 || st.jc > BK_DD_SCAP || st.jl < 0 || st.jl + st.jc > d.lpool_end) return -1;
+    const int go = stage_range(sgr, d.Li, st.jl, st.jc, lane);
+    dd_cp_wait();
+    __syncwarp();
+    classify_rows(d, T, j, c, ndesc, x, sgr, go, st.jc, sslot, sadd, sxv, why_pre, lane);
+    return go;
+}
+
+// After the wait: L(:,j)'s rows and values copied again, with its extent read
+// again (one round trip); when the extent is the guessed one and the rows are
+// the prestaged rows, their classification stands; otherwise the rows are
+// classified now.  Returns the number of entries, or -1 when L(:,j) has more
+// than BK_DD_SCAP entries (read the usual way).
 template <typename V>
 __device__ __forceinline__ int stage_step(const bk_dev &d, const bk_task &T, RStep<V> &st, int j, int c, int lane,
-                                          int ndesc, int *srow, V *sval, int *sadd, int &ro, int &vo, int &why)
+                                          int ndesc, const V *x, int *srow, V *sval, int *sadd, V *sxv, int *sslot,
+                                          const int *sgr, int go, int why_pre, int &vo, int &why)
 {
     const int base = T.sp_lo;
     const V *const Lx = vals<V>(d.Lx);
@@ -245,6 +322,7 @@ __device__ __forceinline__ int stage_step(const bk_dev &d, const bk_task &T, RSt
     // the extent read before the wait is a guess (its two words may come from
     // either side of a move of the column): copied only inside the arrays
     const bool guess = st.jl >= 0 && st.jc >= 0 && st.jl + st.jc <= d.lpool_end;
+    int ro = 0;
     if (guess) {
         ro = stage_range(srow, d.Li, st.jl, st.jc, lane);
         vo = stage_range(sval, Lx, st.jl, st.jc, lane);
@@ -253,6 +331,7 @@ __device__ __forceinline__ int stage_step(const bk_dev &d, const bk_task &T, RSt
     const int64_t jl = __ldcg(d.Lbeg + j);
     const int jc = __ldcg(d.Lcnt + j);
     dd_cp_wait();
+    const bool kept = go >= 0 && guess && jl == st.jl && jc == st.jc;
     if (!guess || jl != st.jl || jc > st.jc) {
         st.jl = jl;
         st.jc = jc;
@@ -266,35 +345,15 @@ __device__ __forceinline__ int stage_step(const bk_dev &d, const bk_task &T, RSt
     st.jc = jc;
     st.sp = slot_of(T, base, pr);
     __syncwarp();
-    for (int q0 = 0; q0 < jc; q0 += 32 * RS_PF) {
-        int rr[RS_PF], sl[RS_PF], pp[RS_PF];
-#pragma unroll
-        for (int u = 0; u < RS_PF; u++) {
-            const int q = q0 + lane + 32 * u;
-            rr[u] = q < jc ? srow[ro + q] : -1;
-            sl[u] = rr[u] >= 0 ? slot_of(T, base, rr[u]) : -1;
-            pp[u] = (sl[u] >= 0 && sl[u] < T.hi - base) ? __ldcg(d.pinv + rr[u]) : -1;
-        }
-#pragma unroll
-        for (int u = 0; u < RS_PF; u++) {
-            const int q = q0 + lane + 32 * u;
-            if (q >= jc) continue;
-            int add = -1;
-            if (sl[u] < 0) {
-                if (!why) why = 65;
-            } else if (pp[u] >= 0 && pp[u] < c) {
-                if (pp[u] > j) add = pp[u] - base;
-                else if (!why) why = 66;
-            } else if (sl[u] >= ndesc) {
-                add = -2 - (sl[u] - ndesc);
-            } else if (!why) {
-                why = 67;
-            }
-            srow[ro + q] = sl[u];
-            sadd[q] = add;
-        }
+    bool same = kept;
+    if (kept)
+        for (int q = lane; q < jc; q += 32)
+            if (srow[ro + q] != sgr[go + q]) same = false;
+    if (__all_sync(BK_FULL, same)) {
+        if (!why) why = why_pre;
+        return jc;
     }
-    __syncwarp();
+    classify_rows(d, T, j, c, ndesc, x, srow, ro, jc, sslot, sadd, sxv, why, lane);
     return jc;
 }
 
@@ -324,6 +383,11 @@ __global__ void __launch_bounds__(128) bk_dd_kernel(bk_dev d, const int32_t *__r
     int *const srow = reinterpret_cast<int *>(stg);
     V *const sval = reinterpret_cast<V *>(stg + (BK_DD_SCAP + 16) * 4);
     int *const sadd = reinterpret_cast<int *>(stg + (BK_DD_SCAP + 16) * 12);
+    V *const sxv = reinterpret_cast<V *>(stg + (BK_DD_SCAP + 16) * 12 + BK_DD_SCAP * 4);
+    int *const sold = reinterpret_cast<int *>(stg + (BK_DD_SCAP + 16) * 12 + BK_DD_SCAP * 12);
+    int *const sgr = sold + (BK_DD_SCAP + 16);
+    int *const sslot = sgr + (BK_DD_SCAP + 16);
+
     __syncwarp();
     int cur_task = -1;
     for (;;) {
@@ -347,7 +411,7 @@ __global__ void __launch_bounds__(128) bk_dd_kernel(bk_dev d, const int32_t *__r
         const bool resolve = (fl & BK_DD_RESOLVE) && c == s0;
         // the resolve column's touched rows must be visible before deciding
         if ((fl & BK_DD_RESOLVE) && c > s0) {
-            int ok = lane == 0 ? (int)lane_wait(d, d.done + s0, epoch, budget) : 1;
+            int ok = lane == 0 ? (int)lane_wait(d, d.done + s0, epoch, budget, c - s0) : 1;
             if (!__shfl_sync(BK_FULL, ok, 0)) return;
         }
         int64_t ub = d.Ubeg[c], ue = d.Uend[c];
@@ -409,7 +473,7 @@ __global__ void __launch_bounds__(128) bk_dd_kernel(bk_dev d, const int32_t *__r
                         if (todo) {
                             const int first = __ffs(todo) - 1;
                             const int jw = __shfl_sync(BK_FULL, j, first);
-                            int okw = lane == 0 ? (int)lane_wait(d, d.done + jw, epoch, budget) : 1;
+                            int okw = lane == 0 ? (int)lane_wait(d, d.done + jw, epoch, budget, c - jw) : 1;
                             if (!__shfl_sync(BK_FULL, okw, 0)) return;
                         }
                     }
@@ -467,6 +531,14 @@ __global__ void __launch_bounds__(128) bk_dd_kernel(bk_dev d, const int32_t *__r
         const int old_uc = d.Ucnt[c], old_lc = d.Lcnt[c];
         const int64_t old_ub = ub, old_lb = lb;
         bool same = true;
+        // the column's previous L rows, copied on chip while the steps run (the L
+        // write compares the new rows with them)
+        int so_old = -1;
+        if (old_lc <= BK_DD_SCAP && old_lb >= 0 && old_lb + old_lc <= d.lpool_end) {
+            so_old = stage_range(sold, d.Li, old_lb, old_lc, lane);
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        }
+        auto old_row = [&](int64_t q) -> int { return so_old >= 0 ? sold[so_old + (int)(q - old_lb)] : d.Li[q]; };
 
         const int e1 = d.Bp[c + 1];
         for (int e = d.dstart[c] + lane; e < e1; e += 32) {
@@ -495,7 +567,7 @@ __global__ void __launch_bounds__(128) bk_dd_kernel(bk_dev d, const int32_t *__r
         if (jb >= 0) read_step(d, T, cur, base + jb, c, s0, epoch, lane, ndesc);
         for (int iter = 0; jb >= 0; iter++) {
             const int j = base + jb;
-            int nstaged = -1, so_r = 0, so_v = 0;
+            int nstaged = -1, so_v = 0;
             if (iter > nsteps || j >= c) { if (!why) why = 63; break; }
             if (lane == 0) atomicAnd(const_cast<uint32_t *>(sb) + (jb >> 5), ~(1u << (jb & 31)));
             __syncwarp();
@@ -506,13 +578,27 @@ __global__ void __launch_bounds__(128) bk_dd_kernel(bk_dev d, const int32_t *__r
 #ifdef BK_TRACE
                 const long long cw0 = clock64();
 #endif
-                int ok = lane == 0 ? (int)lane_wait(d, d.done + j, epoch, budget) : 1;
-                if (!__shfl_sync(BK_FULL, ok, 0)) return;
+                // a step still being computed: its rows prestaged while it runs
+                int set = 0;
+                if (lane == 0) set = ld_relaxed(d.done + j) == epoch;
+                set = __shfl_sync(BK_FULL, set, 0);
+                int go = -1, why_pre = 0;
+                if (!set) go = prestage_step(d, T, cur, j, c, ndesc, x, sgr, sslot, sadd, sxv, why_pre, lane);
+                int ok = 1;
+                if (lane == 0) {
+                    if (set) fence_acquire();
+                    else ok = (int)lane_wait(d, d.done + j, epoch, budget, c - j);
+                }
+                if (!__shfl_sync(BK_FULL, ok, 0)) {
+                    asm volatile("cp.async.wait_group 0;" ::: "memory");   // no copy left in flight
+                    return;
+                }
                 DD_CLK(ck_last);
 #ifdef BK_TRACE
                 ck_wait += ck_last - cw0;
 #endif
-                nstaged = stage_step(d, T, cur, j, c, lane, ndesc, srow, sval, sadd, so_r, so_v, why);
+                nstaged = stage_step(d, T, cur, j, c, lane, ndesc, x, srow, sval, sadd, sxv, sslot, sgr, go, why_pre,
+                                     so_v, why);
 #ifdef BK_TRACE
                 ck_stg = clock64() - ck_last;
                 steps_after = 0;
@@ -615,12 +701,11 @@ __global__ void __launch_bounds__(128) bk_dd_kernel(bk_dev d, const int32_t *__r
 #pragma unroll
                 for (int u = 0; u < RSTEP_PF; u++) {
                     const int q = q0 + lane + 32 * u;
-                    sq[u] = q < nstaged ? srow[so_r + q] : -1;
+                    sq[u] = q < nstaged ? sslot[q] : -1;
                     lq[u] = q < nstaged ? sval[so_v + q] : V(0);
                     aq[u] = q < nstaged ? sadd[q] : -1;
+                    xq[u] = q < nstaged ? sxv[q] : V(0);
                 }
-#pragma unroll
-                for (int u = 0; u < RSTEP_PF; u++) xq[u] = sq[u] >= 0 ? x[sq[u]] : V(0);
 #pragma unroll
                 for (int u = 0; u < RSTEP_PF; u++) {
                     if (sq[u] < 0) continue;
@@ -676,6 +761,7 @@ __global__ void __launch_bounds__(128) bk_dd_kernel(bk_dev d, const int32_t *__r
             }
             if (lb + cnt_all > le) overflow = true;
         };
+        if (so_old >= 0) asm volatile("cp.async.wait_group 0;" ::: "memory");
         int wfirst = 0;
         const int filled0 = build_list(rb, nrw, wfirst, list, lane);
         int piv = -1;
@@ -705,7 +791,7 @@ __global__ void __launch_bounds__(128) bk_dd_kernel(bk_dev d, const int32_t *__r
                     const bool isp = pin && ls[u] == pls;
                     qq[u] = lb + i - ((pin && ls[u] > pls) ? 1 : 0);
                     v[u] = ls[u] >= 0 ? x[ndesc + ls[u]] : V(0);
-                    oldr[u] = (ls[u] >= 0 && !isp && !overflow && lb == old_lb && qq[u] - lb < old_lc) ? d.Li[qq[u]]
+                    oldr[u] = (ls[u] >= 0 && !isp && !overflow && lb == old_lb && qq[u] - lb < old_lc) ? old_row(qq[u])
                                                                                                       : -1;
                 }
 #pragma unroll
@@ -826,7 +912,7 @@ __global__ void __launch_bounds__(128) bk_dd_kernel(bk_dev d, const int32_t *__r
                         if (ls[u] == pls && pin) ls[u] = -2;          // the pivot row: cleared below
                         qq[u] = lb + rank0 + i - ((pin && ls[u] > pls) ? 1 : 0);
                         v[u] = ls[u] >= 0 ? x[ndesc + ls[u]] : 0.0;
-                        oldr[u] = (ls[u] >= 0 && !overflow && lb == old_lb && qq[u] - lb < old_lc) ? d.Li[qq[u]]
+                        oldr[u] = (ls[u] >= 0 && !overflow && lb == old_lb && qq[u] - lb < old_lc) ? old_row(qq[u])
                                                                                                   : -1;
                     }
 #pragma unroll
@@ -882,7 +968,8 @@ __global__ void __launch_bounds__(128) bk_dd_kernel(bk_dev d, const int32_t *__r
                 d.pchg_ep[c] = epoch;
                 d.pchg_ref[c] = refno;
             }
-            __threadfence();
+            // the release orders this lane's writes and, through the warp barrier
+            // above, the other lanes' L entries before the flag
             st_release(d.done + c, epoch);
             BK_TREC(d.trace, BK_TR_ROUND, resolve ? 3 : 2, c, t0);
 #ifdef BK_TRACE

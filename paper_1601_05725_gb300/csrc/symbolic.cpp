@@ -711,11 +711,20 @@ void bk_plan_layout(bk_plan &pl)
     pl.ahat_doubles = std::max<int64_t>(ah, 1);
     pl.ahat_words = std::max<int64_t>(ab, 1);
     // the reach's step and row bitmaps fit in shared memory for four warps a block
-    // (beside the rounds' staging areas)
+    // (beside the rounds' staging areas), per ND level: the rounds of a level
+    // launch with its own tasks' bitmaps
+    auto fits = [](int64_t w) { return 4 * w * 4 + 4 * BK_DD_STAGE_BYTES <= 160 * 1024; };
     int64_t bw = 0;
-    for (auto &T : pl.tasks) bw = std::max<int64_t>(bw, ((int64_t)(T.hi - T.sp_lo) + 31) / 32 + (T.lspace + 31) / 32);
-    bw = (bw + 3) & ~(int64_t)3;
-    pl.dd_words = 4 * bw * 4 + 4 * BK_DD_STAGE_BYTES <= 160 * 1024 ? (int32_t)bw : 0;
+    pl.level_dd_words.assign(pl.level_tasks.size(), 0);
+    for (auto &T : pl.tasks) {
+        const int64_t w = (((int64_t)(T.hi - T.sp_lo) + 31) / 32 + (T.lspace + 31) / 32 + 3) & ~(int64_t)3;
+        bw = std::max(bw, w);
+        int32_t &lw = pl.level_dd_words[(size_t)T.level];
+        lw = (int32_t)std::max<int64_t>(lw, w);
+    }
+    pl.dd_words = fits(bw) ? (int32_t)bw : 0;
+    for (auto &lw : pl.level_dd_words)
+        if (!fits(lw)) lw = 0;
     // One workspace serves every level in turn, each with slices of its own size:
     // a level wants one slice per column it processes at once (at most 152 SMs x
     // 16 warps); the workspace holds what level 0 (the leaves and BTF blocks) wants
