@@ -362,9 +362,11 @@ def _measure(h, dvals, drhs, K, W, dev, flush, dist, world):
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
 # ncu capture of the kernel as it stands, by kernel kind and value width.  A kind
 # without a capture of its current code reports null.
-TRAFFIC = {("powergrid_316x316", "solve", 8): 102.8e6, ("powergrid_316x316", "dense_node", 8): 2.3e6}
+TRAFFIC = {("powergrid_316x316", "solve", 8): 102.8e6, ("powergrid_316x316", "refactor_rounds", 8): 19.2e6,
+           ("powergrid_316x316", "dense_node", 8): 2.3e6}
 # sm__pipe_fp64_cycles_active (pct of peak) from the same captures
-FP64_PIPE = {("powergrid_316x316", "solve", 8): 16.5, ("powergrid_316x316", "dense_node", 8): 24.1}
+FP64_PIPE = {("powergrid_316x316", "solve", 8): 16.5, ("powergrid_316x316", "refactor_rounds", 8): 1.4,
+             ("powergrid_316x316", "dense_node", 8): 24.1}
 
 
 def _roofline(prob, info1, K, nnz_lu, vbytes, hbm):
