@@ -398,7 +398,45 @@ __global__ void __launch_bounds__(32) bk_gp_task_kernel(bk_dev d, const int32_t 
 // ---------------------------------------------------------------------------
 // Descendant phase of separator columns (one warp per column, persistent).
 // Column space: subtree rows [sp_lo, hi) then ancestors (base = sp_lo); the step
-// bitmap covers descendant steps [sp_lo, lo) only.
+// bitmap covers descendant steps [sp_lo, lo) only.  The bitmaps sit in shared
+// memory when the level's fit (d.dd_words words a warp), else in the slice.
+// Every descendant step is final before this kernel, so the step after the
+// current one (the lowest set bit once the current one is cleared) has its pivot
+// slot, the extent of its L column and its first DSTEP_PF * 32 entries (rows'
+// slots, values, the rows' pivot steps) read while the current step is applied;
+// a step that the current one adds below that prediction is read when found.
+constexpr int DSTEP_PF = 4;
+template <typename V>
+struct DStep {
+    int sp, jc;
+    int64_t jl;
+    int s[DSTEP_PF], p[DSTEP_PF];
+    V l[DSTEP_PF];
+};
+
+template <typename V>
+__device__ __forceinline__ void read_dstep(const bk_dev &d, const bk_task &T, DStep<V> &st, int j, int ndesc,
+                                           int lane)
+{
+    const int base = T.sp_lo;
+    const V *const Lx = vals<V>(d.Lx);
+    st.sp = d.prow[j] - base;
+    st.jl = d.Lbeg[j];
+    st.jc = d.Lcnt[j];
+    int r[DSTEP_PF];
+#pragma unroll
+    for (int u = 0; u < DSTEP_PF; u++) {
+        const int q = lane + 32 * u;
+        r[u] = q < st.jc ? d.Li[st.jl + q] : -1;
+        st.l[u] = q < st.jc ? Lx[st.jl + q] : V(0);
+    }
+#pragma unroll
+    for (int u = 0; u < DSTEP_PF; u++) {
+        st.s[u] = r[u] >= 0 ? slot_of(T, base, r[u]) : -2;
+        st.p[u] = (st.s[u] >= 0 && st.s[u] < ndesc) ? d.pinv[r[u]] : -1;
+    }
+}
+
 template <typename V>
 __global__ void __launch_bounds__(128) bk_gp_desc_kernel(bk_dev d, const int32_t *__restrict__ cols,
                                                          int32_t ncols, int32_t *counter,
@@ -410,12 +448,16 @@ __global__ void __launch_bounds__(128) bk_gp_desc_kernel(bk_dev d, const int32_t
     V *const Ux = vals<V>(d.Ux);
     V *const Ahat = vals<V>(d.ahat);
     __shared__ bk_task Ts[4];
+    extern __shared__ uint32_t gd_bits[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int gw = blockIdx.x * 4 + wib;
     if (gw >= d.wsd_warps) return;
     bk_task &T = Ts[wib];
     unsigned char *slice = d.wsd + (int64_t)gw * d.wsd_slice;
+    uint32_t *const wbits = gd_bits + (int64_t)wib * d.dd_words;
+    for (int i = lane; i < d.dd_words; i += 32) wbits[i] = 0u;
+    __syncwarp();
     int cur_task = -1;
     for (;;) {
         int k = 0;
@@ -436,7 +478,7 @@ __global__ void __launch_bounds__(128) bk_gp_desc_kernel(bk_dev d, const int32_t
         const int nsw = (ndesc + 31) >> 5;
         const int nrw = (lsp + 31) >> 5;
         V *x = reinterpret_cast<V *>(slice);
-        volatile uint32_t *sb = reinterpret_cast<uint32_t *>(x + T.space);
+        volatile uint32_t *sb = d.dd_words ? wbits : reinterpret_cast<uint32_t *>(x + T.space);
         volatile uint32_t *rb = sb + nsw;
         int64_t ub = d.Ubeg[c], ue = d.Uend[c];
         bool bad = false;
@@ -459,18 +501,24 @@ __global__ void __launch_bounds__(128) bk_gp_desc_kernel(bk_dev d, const int32_t
         __syncwarp();
         int w0 = 0;
         bool overflow = false, broken = false;
-        for (int iter = 0;; iter++) {
-            const int jb = next_step_bit(sb, nsw, w0, lane);
-            if (jb < 0) break;
+        int jb = next_step_bit(sb, nsw, w0, lane);
+        DStep<V> cur, nxt;
+        if (jb >= 0) read_dstep(d, T, cur, base + jb, ndesc, lane);
+        for (int iter = 0; jb >= 0; iter++) {
             const int j = base + jb;
-            const int sp = d.prow[j] - base;       // descendant row: slot = row - sp_lo
+            const int sp = cur.sp;                 // descendant row: slot = row - sp_lo
             if (iter > ndesc || (unsigned)sp >= (unsigned)ndesc) { broken = true; break; }
-            const V m = x[sp];
+            if (lane == 0) atomicAnd(const_cast<uint32_t *>(sb) + (jb >> 5), ~(1u << (jb & 31)));
             __syncwarp();
-            if (lane == 0) {
-                atomicAnd(const_cast<uint32_t *>(sb) + (jb >> 5), ~(1u << (jb & 31)));
-                x[sp] = 0.0;
-            }
+            int wp = w0;
+            const int jbp = next_step_bit(sb, nsw, wp, lane);
+            if (jbp >= 0) read_dstep(d, T, nxt, base + jbp, ndesc, lane);
+            const V m = x[sp];
+            V xv[DSTEP_PF];
+#pragma unroll
+            for (int u = 0; u < DSTEP_PF; u++) xv[u] = cur.s[u] >= 0 ? x[cur.s[u]] : V(0);
+            __syncwarp();
+            if (lane == 0) x[sp] = 0.0;
             if (!isfinite(m)) bad = true;
             if (!overflow && ub + nu + 2 > ue) {
                 const int64_t cap = grown_ucap(nu, (int64_t)(c - T.sp_lo) + 1);
@@ -498,12 +546,25 @@ __global__ void __launch_bounds__(128) bk_gp_desc_kernel(bk_dev d, const int32_t
                 Ux[ub + nu] = m;
             }
             nu++;
-            const int64_t jl = d.Lbeg[j];
-            const int jc = d.Lcnt[j];
-            // L(:,j) applied eight entries per lane at a time: all loads first
-            for (int q0 = lane; q0 < jc; q0 += 32 * DESC_PF) {
+            // the read-ahead entries, then the rest of L(:,j) eight a lane at a time
+#pragma unroll
+            for (int u = 0; u < DSTEP_PF; u++) {
+                const int s = cur.s[u];
+                if (s == -2) continue;
+                if (s < 0) { report_internal(d.status, c, 18); continue; }
+                x[s] = fma(-cur.l[u], m, xv[u]);
+                if (s < ndesc) {
+                    if (cur.p[u] > j && cur.p[u] < T.lo) set_bit(sb, cur.p[u] - base);
+                    else report_internal(d.status, c, 19);
+                } else {
+                    set_bit(rb, s - ndesc);
+                }
+            }
+            const int64_t jl = cur.jl;
+            const int jc = cur.jc;
+            for (int q0 = 32 * DSTEP_PF + lane; q0 < jc; q0 += 32 * DESC_PF) {
                 int rr[DESC_PF], ss[DESC_PF], pp[DESC_PF];
-                V ll[DESC_PF], xv[DESC_PF];
+                V ll[DESC_PF], xw[DESC_PF];
 #pragma unroll
                 for (int u = 0; u < DESC_PF; u++) {
                     const int q = q0 + 32 * u;
@@ -513,7 +574,7 @@ __global__ void __launch_bounds__(128) bk_gp_desc_kernel(bk_dev d, const int32_t
 #pragma unroll
                 for (int u = 0; u < DESC_PF; u++) {
                     ss[u] = rr[u] >= 0 ? slot_of(T, base, rr[u]) : -2;
-                    xv[u] = ss[u] >= 0 ? x[ss[u]] : V(0);
+                    xw[u] = ss[u] >= 0 ? x[ss[u]] : V(0);
                     pp[u] = (ss[u] >= 0 && ss[u] < ndesc) ? d.pinv[rr[u]] : -1;
                 }
 #pragma unroll
@@ -521,7 +582,7 @@ __global__ void __launch_bounds__(128) bk_gp_desc_kernel(bk_dev d, const int32_t
                     const int s = ss[u];
                     if (s == -2) continue;
                     if (s < 0) { report_internal(d.status, c, 18); continue; }
-                    x[s] = fma(-ll[u], m, xv[u]);
+                    x[s] = fma(-ll[u], m, xw[u]);
                     if (s < ndesc) {
                         if (pp[u] > j && pp[u] < T.lo) set_bit(sb, pp[u] - base);
                         else report_internal(d.status, c, 19);
@@ -531,6 +592,11 @@ __global__ void __launch_bounds__(128) bk_gp_desc_kernel(bk_dev d, const int32_t
                 }
             }
             __syncwarp();
+            jb = next_step_bit(sb, nsw, w0, lane);
+            if (jb >= 0) {
+                if (jb == jbp) cur = nxt;
+                else read_dstep(d, T, cur, base + jb, ndesc, lane);
+            }
         }
         // A-hat(:,c) on the separator's and ancestors' rows, and its pattern
         V *ah = Ahat + T.ahoff + (int64_t)(c - T.lo) * lsp;
@@ -600,11 +666,19 @@ void bk_launch_gp_desc(const bk_dev &d, const int32_t *cols, int32_t ncols, int3
 {
     if (ncols <= 0) return;
     int warps = std::min<int>(ncols, d.wsd_warps);
+    // the level's step and row bitmaps, four warps' worth (d.dd_words is set per
+    // ND level, 0 when they do not fit)
+    const size_t smem = (size_t)4 * d.dd_words * sizeof(uint32_t);
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaFuncSetAttribute(bk_gp_desc_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+        cudaFuncSetAttribute(bk_gp_desc_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    });
     if (d.prec)
-        bk_gp_desc_kernel<float><<<(warps + 3) / 4, 128, 0, (cudaStream_t)stream>>>(d, cols, ncols, counter,
-                                                                                   ncols_dev);
+        bk_gp_desc_kernel<float><<<(warps + 3) / 4, 128, smem, (cudaStream_t)stream>>>(d, cols, ncols, counter,
+                                                                                      ncols_dev);
     else
-        bk_gp_desc_kernel<double><<<(warps + 3) / 4, 128, 0, (cudaStream_t)stream>>>(d, cols, ncols, counter,
-                                                                                    ncols_dev);
+        bk_gp_desc_kernel<double><<<(warps + 3) / 4, 128, smem, (cudaStream_t)stream>>>(d, cols, ncols, counter,
+                                                                                       ncols_dev);
 }
 
