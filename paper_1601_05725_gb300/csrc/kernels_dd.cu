@@ -4,7 +4,8 @@
 // flags the columns whose preferred pivot Algorithm 1's pivot selection would
 // reject.  Within a task (BTF block or ND node) everything before the first such
 // column f is exact.  A round then processes each active task from its start
-// column s (one warp per column, claimed in ascending order, flags per column):
+// column s (one warp per column, claimed in ascending order within a task, the
+// tasks interleaved; flags per column):
 //   * resolve (s = f): column s is recomputed by the reach of Algorithm 1 and
 //     takes the pivot the selection rule gives; its previous and new pivot rows
 //     are marked "touched" in this round;
