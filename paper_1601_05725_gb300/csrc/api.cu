@@ -13,6 +13,7 @@
 #include <new>
 
 #include "basker_internal.h"
+#include "round_order.h"
 #include "refine_internal.h"
 #include "solve_internal.h"
 #include "trace.cuh"
@@ -683,34 +684,15 @@ int stage_upload(basker_t h, cudaStream_t s, int32_t *dst, const std::vector<int
     return BASKER_OK;
 }
 
-// The columns of a round in claim order: each active task's columns from its
-// start column on, ascending within the task (a column's steps in its own task
-// come before it, so every wait is on a column already claimed), the tasks
-// interleaved in proportion to their lengths, so that every task advances
-// through its columns at the same rate.  Claimed in task order instead, the
-// columns near the top of the first tasks' elimination trees hold the warps
-// while they wait for their chains, and the later tasks start late.  Column i of
-// a task of L columns goes to position floor((2i + 1) N / 2L) of N buckets (N
-// columns in all), which grows with i: a counting sort over the buckets keeps
-// each task's order.
+// The columns of a round in claim order (bk_round_order): each active task's
+// columns from its start column on.
 void round_columns(const bk_plan &pl, const std::vector<int32_t> &active, const std::vector<int32_t> &start,
                    std::vector<int32_t> &cols)
 {
-    int64_t N = 0;
-    for (int32_t t : active) N += pl.tasks[(size_t)t].hi - start[(size_t)t];
-    cols.assign((size_t)N, 0);
-    if (N == 0) return;
-    std::vector<int32_t> at((size_t)N + 1, 0);
-    auto bucket = [N](int64_t i, int64_t L) { return (size_t)(((2 * i + 1) * N) / (2 * L)); };
-    for (int32_t t : active) {
-        const int64_t L = pl.tasks[(size_t)t].hi - start[(size_t)t];
-        for (int64_t i = 0; i < L; i++) at[bucket(i, L) + 1]++;
-    }
-    for (size_t b = 0; b < (size_t)N; b++) at[b + 1] += at[b];
-    for (int32_t t : active) {
-        const int64_t L = pl.tasks[(size_t)t].hi - start[(size_t)t];
-        for (int64_t i = 0; i < L; i++) cols[(size_t)at[bucket(i, L)]++] = start[(size_t)t] + (int32_t)i;
-    }
+    std::vector<std::pair<int32_t, int32_t>> ranges;
+    ranges.reserve(active.size());
+    for (int32_t t : active) ranges.emplace_back(start[(size_t)t], pl.tasks[(size_t)t].hi);
+    bk::bk_round_order(ranges, cols);
 }
 
 // After a stored-pattern pass that rejected some preferred pivots (first
